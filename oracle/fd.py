@@ -1,0 +1,210 @@
+"""ctypes wrapper around the C oracle ``fd_oracle.c`` (test infrastructure).
+
+Arrays are NumPy float64, C-contiguous.  A state is shaped
+``(nfields, nz, ny, nx)`` with fields (lnrho, u_x, u_y, u_z[, s]); nfields is
+4 (the paper's isothermal model, entropy_mode 0) or 5 (passive entropy s,
+entropy_mode 1).  Every routine follows one definition of the paper; see the
+header of ``fd_oracle.c`` for the list.
+"""
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build_oracle
+
+_lib = None
+_D = ctypes.c_double
+_L = ctypes.c_long
+_I = ctypes.c_int
+_P = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = ctypes.CDLL(path)
+        L.or_d1_point.restype = _D
+        L.or_d1_point.argtypes = [_P, _D]
+        L.or_d2_point.restype = _D
+        L.or_d2_point.argtypes = [_P, _D]
+        L.or_dmix_point.restype = _D
+        L.or_dmix_point.argtypes = [_P, _D, _D]
+        for name in ("or_grid_d1", "or_grid_d2"):
+            getattr(L, name).argtypes = [_P, _P, _L, _L, _L, _D, _D, _D, _I]
+        L.or_grid_dmix.argtypes = [_P, _P, _L, _L, _L, _D, _D, _D, _I, _I]
+        L.or_rhs.argtypes = [_P, _P, _L, _L, _L, _D, _D, _D, _D, _D, _I, _I]
+        L.or_rk3_coefficients.argtypes = [_P, _P]
+        L.or_substep55.argtypes = [_P, _P, _P, _I, _D, _L, _L, _L, _D, _D, _D, _D, _D, _I]
+        L.or_substep19.argtypes = [_P, _P, _P, _P, _I, _D, _L, _L, _L, _D, _D, _D, _D, _D, _I]
+        L.or_diagnostics.argtypes = [_P, _L, _L, _L, _D, _D, _D, _I, _P]
+        L.or_cfl_dt.restype = _D
+        L.or_cfl_dt.argtypes = [_P, _L, _L, _L, _D, _D, _D, _D, _D, _D, _D]
+        L.or_box_filter.argtypes = [_P, _P, _L, _L, _L, _I, _I]
+        L.or_set_threads.restype = _I
+        L.or_set_threads.argtypes = [_I]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_P)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n):
+    """Set the OpenMP thread count of the substep loops; returns the count."""
+    return lib().or_set_threads(int(n))
+
+
+# ---------------------------------------------------------------- stencils
+
+def d1_point(samples, h):
+    """Eq. 6 applied to 7 samples at offsets -3..3."""
+    s = _f64(samples)
+    assert s.shape == (7,)
+    return lib().or_d1_point(_p(s), h)
+
+
+def d2_point(samples, h):
+    """Eq. 7 (with 1/(180 h^2)) applied to 7 samples at offsets -3..3."""
+    s = _f64(samples)
+    assert s.shape == (7,)
+    return lib().or_d2_point(_p(s), h)
+
+
+def dmix_point(patch, ha, hb):
+    """Eq. 8 applied to a 7x7 patch, patch[ia+3, ib+3] = f(a+ia ha, b+ib hb)."""
+    s = _f64(patch)
+    assert s.shape == (7, 7)
+    return lib().or_dmix_point(_p(s), ha, hb)
+
+
+@dataclass
+class Grid:
+    nx: int
+    ny: int
+    nz: int
+    lx: float = 2 * np.pi
+    ly: float = 2 * np.pi
+    lz: float = 2 * np.pi
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def spacing(self):
+        return (self.lx / self.nx, self.ly / self.ny, self.lz / self.nz)
+
+    def dims(self):
+        return (self.nx, self.ny, self.nz, self.lx, self.ly, self.lz)
+
+
+def grid_d1(f, grid, axis):
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().or_grid_d1(_p(f), _p(out), *grid.dims(), axis)
+    return out
+
+
+def grid_d2(f, grid, axis):
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().or_grid_d2(_p(f), _p(out), *grid.dims(), axis)
+    return out
+
+
+def grid_dmix(f, grid, a, b):
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().or_grid_dmix(_p(f), _p(out), *grid.dims(), a, b)
+    return out
+
+
+# ---------------------------------------------------------------- physics
+
+@dataclass
+class Physics:
+    cs: float = 1.0
+    nu: float = 5e-3
+    entropy_mode: int = 1
+
+    @property
+    def nfields(self):
+        return 5 if self.entropy_mode else 4
+
+
+FORM_55P = 0
+FORM_19P = 1
+
+
+def rhs(state, grid, phys, form=FORM_55P):
+    """d(state)/dt from Eqs. 1-3 (f = 0) in the given stencil form."""
+    st = _f64(state)
+    assert st.shape == (phys.nfields,) + grid.shape
+    out = np.zeros_like(st)
+    lib().or_rhs(_p(st), _p(out), *grid.dims(), phys.cs, phys.nu, phys.entropy_mode, form)
+    return out
+
+
+def rk3_coefficients():
+    a = np.zeros(3)
+    b = np.zeros(3)
+    lib().or_rk3_coefficients(_p(a), _p(b))
+    return a, b
+
+
+def substep(state_in, w, s, dt, grid, phys, form=FORM_55P):
+    """One RK3 substep (s = 0, 1, 2).  Returns (state_out, w_new)."""
+    st = _f64(state_in).copy()
+    wn = _f64(w).copy()
+    out = np.zeros_like(st)
+    if form == FORM_55P:
+        lib().or_substep55(_p(st), _p(wn), _p(out), s, dt, *grid.dims(), phys.cs, phys.nu,
+                           phys.entropy_mode)
+    else:
+        divf = np.zeros(grid.shape)
+        lib().or_substep19(_p(st), _p(wn), _p(out), _p(divf), s, dt, *grid.dims(), phys.cs,
+                           phys.nu, phys.entropy_mode)
+    return out, wn
+
+
+def rk3_step(state, dt, grid, phys, form=FORM_55P, nsteps=1):
+    """Advance `nsteps` full RK3 steps of length dt; returns the new state."""
+    st = _f64(state).copy()
+    w = np.zeros_like(st)
+    for _ in range(nsteps):
+        for s in range(3):
+            st, w = substep(st, w, s, dt, grid, phys, form)
+    return st
+
+
+def diagnostics(state, grid, phys):
+    """FP64 reductions of a state (see ``or_diagnostics``)."""
+    st = _f64(state)
+    out = np.zeros(15)
+    lib().or_diagnostics(_p(st), *grid.dims(), phys.entropy_mode, out.ctypes.data_as(_P))
+    return {
+        "mass": out[0], "ekin": out[1], "umax": out[2], "urms": out[3],
+        "rms": out[4:9].copy(), "maxabs": out[9:14].copy(), "nonfinite": int(out[14]),
+    }
+
+
+def cfl_dt(state, grid, phys, cfl=0.4, cnu=0.25):
+    st = _f64(state)
+    return lib().or_cfl_dt(_p(st), *grid.dims(), phys.cs, phys.nu, cfl, cnu)
+
+
+def box_filter(fine, r=4):
+    """Centred box filter to a grid r times coarser per axis (fields first)."""
+    f = _f64(fine)
+    nf, nz, ny, nx = f.shape
+    out = np.zeros((nf, nz // r, ny // r, nx // r))
+    lib().or_box_filter(_p(f), _p(out), nx, ny, nz, r, nf)
+    return out
