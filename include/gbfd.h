@@ -1,0 +1,169 @@
+/*
+ * gbfd.h -- C ABI of libgbfd, a single-GPU (GB300, sm_103a) solver for the
+ * isothermal compressible hydrodynamics of Pekkila et al. (2017), "Methods
+ * for compressible fluid simulation on GPUs using high-order finite
+ * differences": sixth-order central differences (Eqs. 6-9) for the
+ * right-hand side of Eqs. 1-3, fused with the 2N-storage third-order
+ * Runge-Kutta substep (Eq. 10, Algorithms 2 and 3) on a periodic 3D grid.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a gbfd_status and never aborts the process.  After a
+ *    failure, gbfd_last_error(ctx) holds a one-line reason.
+ *  - Device memory is owned by the caller: gbfd_init receives one
+ *    workspace buffer (size from gbfd_workspace_bytes) and never allocates
+ *    device memory itself.  The context object is host memory owned by the
+ *    library and released by gbfd_destroy.
+ *  - All device work is enqueued asynchronously on the CUDA stream given to
+ *    gbfd_init; only gbfd_get_state to host memory, gbfd_diagnostics,
+ *    gbfd_cfl_dt and gbfd_sync wait for that stream.
+ *  - A state is nfields arrays [nz][ny][nx] (x fastest) of the fields
+ *    (lnrho, u_x, u_y, u_z[, s]), laid out one after the other.  nfields is
+ *    4 for entropy_mode 0 (the paper's isothermal model, no energy variable)
+ *    and 5 for entropy_mode 1 (a passive entropy field, ds/dt = -u.grad s,
+ *    with no feedback on the flow).
+ *  - The grid is periodic in every axis (Sect. 4); point i of an axis sits
+ *    at i L/N (Sect. 2.3).
+ *  - Not thread-safe per context: calls on one context must not overlap.
+ */
+#ifndef GBFD_H
+#define GBFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBFD_ABI_VERSION 1
+
+typedef enum {
+    GBFD_OK = 0,
+    GBFD_ERR_INVALID_ARG = 1, /* a size, pointer or parameter was rejected  */
+    GBFD_ERR_WORKSPACE = 2,   /* workspace too small or not 256-B aligned   */
+    GBFD_ERR_CUDA = 3,        /* a CUDA runtime call failed (see last_error) */
+    GBFD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up          */
+    GBFD_ERR_UNSUPPORTED = 5, /* valid request this build does not provide   */
+    GBFD_ERR_STATE = 6        /* context unusable after an earlier error     */
+} gbfd_status;
+
+/* Arithmetic of the solver (spec precision forms).
+ * FP64: FP64 storage and arithmetic.
+ * FP32: FP32 storage, stencils and update.
+ * FP32_ACC64: FP32 storage and stencils; the RK3 register update
+ *   w <- alpha w + dt rhs and u <- u + beta w of Eq. 10 is done in FP64 in
+ *   registers and rounded to FP32 storage.
+ * FP32_ACC64_W64: as FP32_ACC64, but the 2N register w (u-tilde) is also
+ *   stored in FP64. */
+enum { GBFD_FP64 = 0, GBFD_FP32 = 1, GBFD_FP32_ACC64 = 2, GBFD_FP32_ACC64_W64 = 3 };
+
+/* Stencil form (Sect. 4.1 and 4.2).
+ * 55P: single pass; grad(div u) from Eq. 7 and the bidiagonal Eq. 8.
+ * 19P: two passes (Algorithm 3); pass 1 stores div u, pass 2 adds
+ *      (nu/3) grad(div u) with Eq. 6 applied to the stored divergence. */
+enum { GBFD_55P = 0, GBFD_19P = 1 };
+
+typedef struct {
+    int32_t nx, ny, nz;   /* points per axis; nx % 4 == 0, all >= 8           */
+    int32_t precision;    /* GBFD_FP64 / GBFD_FP32 / GBFD_FP32_ACC64[_W64]     */
+    int32_t form;         /* GBFD_55P / GBFD_19P                               */
+    int32_t entropy_mode; /* 0: 4 fields (isothermal); 1: + passive entropy s */
+    double lx, ly, lz;    /* box lengths L_i (> 0)                             */
+    double cs;            /* isothermal sound speed c_s (>= 0), Eq. 2         */
+    double nu;            /* kinematic viscosity nu (>= 0), Eq. 2             */
+} gbfd_params;
+
+/* FP64 reductions over the current state (grid cell volume dV = prod L_i/N_i):
+ * mass = dV sum exp(lnrho); ekin = dV sum exp(lnrho)|u|^2/2;
+ * umax = max |u| (Euclidean); urms = sqrt(mean |u|^2);
+ * rms[f] = sqrt(mean f^2), maxabs[f] = max |f| per field (0 for an absent
+ * entropy field); nonfinite = 1 when any value of the state is NaN/Inf. */
+typedef struct {
+    double mass, ekin, umax, urms;
+    double rms[5];
+    double maxabs[5];
+    int32_t nonfinite;
+    int32_t nfields;
+} gbfd_diag;
+
+typedef struct gbfd_ctx gbfd_ctx;
+
+/* Bytes of device workspace gbfd_init needs for these parameters (0 when the
+ * parameters are invalid).  Holds two padded state buffers (ping-pong, the
+ * separate in/out arrays of Sect. 4), the 2N register u-tilde, the
+ * divergence field of the 19-point form, a staging area for state copies
+ * and reduction scratch. */
+size_t gbfd_workspace_bytes(const gbfd_params *p);
+
+/* Create a context.  `workspace` is a device pointer (256-byte aligned) to
+ * `workspace_bytes` >= gbfd_workspace_bytes(p) bytes that the caller keeps
+ * alive until gbfd_destroy; `stream` is a cudaStream_t (NULL = legacy default
+ * stream).  The state is zero after init.  Errors: INVALID_ARG (p or out
+ * NULL, bad sizes), WORKSPACE, CUDA. */
+gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_bytes, void *stream,
+                      gbfd_ctx **out);
+
+/* Release the context (not the caller's workspace).  NULL is accepted. */
+gbfd_status gbfd_destroy(gbfd_ctx *ctx);
+
+/* Copy a full state into the solver.  `src` holds nfields*nz*ny*nx values,
+ * FP64 if src_is_fp64 else FP32, in host memory (src_on_device = 0; pinned
+ * memory makes the copy asynchronous) or device memory (src_on_device = 1).
+ * Values are converted to the storage precision.  The host buffer may be
+ * reused once the call's work on the stream has completed. */
+gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, int src_is_fp64);
+
+/* Copy the current state out, same layout as gbfd_set_state.  A host
+ * destination is complete when the call returns (the stream is
+ * synchronised); a device destination is written asynchronously. */
+gbfd_status gbfd_get_state(gbfd_ctx *ctx, void *dst, int dst_on_device, int dst_is_fp64);
+
+/* Advance `nsteps` >= 0 full RK3 steps of length dt (> 0, finite): three
+ * substeps each of Eq. 10 with alpha = (0, -5/9, -153/128) and
+ * beta = (1/3, 15/16, 8/15) (Williamson's 2N-storage RK3; the paper leaves
+ * the coefficients to the chosen scheme and fixes alpha_1 = 0), the
+ * right-hand side of Eqs. 1-3 with the body force f = 0, in the form chosen
+ * at init.  Asynchronous. */
+gbfd_status gbfd_rk3_step(gbfd_ctx *ctx, double dt, int nsteps);
+
+/* One substep s in {0, 1, 2} of Eq. 10 (Algorithm 2 or 3), for tests that
+ * compare single substeps; s = 0 ignores the old u-tilde (alpha_1 = 0).
+ * Asynchronous. */
+gbfd_status gbfd_substep(gbfd_ctx *ctx, int s, double dt);
+
+/* FP64 reductions of the current state (struct above).  Synchronises. */
+gbfd_status gbfd_diagnostics(gbfd_ctx *ctx, gbfd_diag *out);
+
+/* Time step from the current state: dt = min(cfl dmin / (max|u| + c_s),
+ * cnu dmin^2 / nu) with dmin the smallest grid spacing (the paper gives no
+ * rule; this is the helper used by the benchmarks).  Synchronises. */
+gbfd_status gbfd_cfl_dt(gbfd_ctx *ctx, double cfl, double cnu, double *dt_out);
+
+/* Wait for the context's stream and report any device-side error
+ * (bounded waits that gave up -> TIMEOUT; CUDA errors -> CUDA). */
+gbfd_status gbfd_sync(gbfd_ctx *ctx);
+
+/* Tuning options (no counterpart in the paper; used by the tests and the
+ * autotuner).  GBFD_OPT_KERNEL_PATH: 0 = tiled kernels (TMA-staged shared
+ * memory, the default), 1 = simple one-thread-per-point kernels reading
+ * global memory.  GBFD_OPT_TILE_CONFIG: index into the tiled kernels' tile
+ * table, -1 = built-in default.  Out-of-range values -> INVALID_ARG. */
+enum { GBFD_OPT_KERNEL_PATH = 1, GBFD_OPT_TILE_CONFIG = 2 };
+gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value);
+
+/* Number of kernel launches the context has enqueued since init. */
+int64_t gbfd_launch_count(const gbfd_ctx *ctx);
+
+/* One-line description of the last failure on this context ("" if none);
+ * valid until the next call on the context.  ctx may be NULL (reports
+ * failures of gbfd_init). */
+const char *gbfd_last_error(const gbfd_ctx *ctx);
+
+/* Static name of a status code. */
+const char *gbfd_status_string(gbfd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFD_H */

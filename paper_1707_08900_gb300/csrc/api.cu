@@ -1,0 +1,527 @@
+// C-ABI entry points of libgbfd (declared in include/gbfd.h): parameter
+// validation, workspace carving, state copies, the RK3 driver loop of
+// Algorithms 2 and 3, diagnostics.  No device memory is allocated here: all
+// buffers are carved from the caller's workspace.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/gbfd.h"
+#include "kernels.cuh"
+#include "tiled.cuh"
+
+using namespace gbfd;
+
+struct gbfd_ctx {
+    gbfd_params p;
+    int nf;
+    int sbytes;  // storage bytes per value (8 FP64, 4 otherwise)
+    int wbytes;  // u-tilde bytes per value
+    cudaStream_t stream;
+    char *ws;
+    size_t ws_bytes;
+    Layout Ls, Lw, Ld;
+    char *state_region[2];
+    char *w_region;
+    char *div_region;
+    char *staging;
+    double *diag_part;
+    double *diag_out;
+    int *dev_error;  // device-side error word (bounded waits)
+    int ndiag;
+    int cur;         // which state buffer holds the current state
+    int64_t launches;
+    int kernel_path;  // 0 = tiled when supported, 1 = simple
+    int tile_cfg;     // index into the tiled kernel's tile table (-1 = default)
+    TmapCache tmaps;  // encoded TMA descriptors of the two state buffers
+    bool broken;
+    Coef<double> c64;
+    Coef<float> c32;
+    char err[512];
+};
+
+namespace {
+
+thread_local char g_init_err[512];
+
+void set_err(gbfd_ctx *c, const char *fmt, ...)
+{
+    char *buf = c ? c->err : g_init_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+}
+
+gbfd_status cuda_fail(gbfd_ctx *c, cudaError_t e, const char *what)
+{
+    set_err(c, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    if (c && (e == cudaErrorIllegalAddress || e == cudaErrorLaunchFailure ||
+              e == cudaErrorIllegalInstruction || e == cudaErrorMisalignedAddress ||
+              e == cudaErrorHardwareStackError))
+        c->broken = true;
+    return GBFD_ERR_CUDA;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int nfields_of(const gbfd_params *p) { return p->entropy_mode ? 5 : 4; }
+
+bool validate(const gbfd_params *p, char *why, size_t n)
+{
+    if (!p) {
+        snprintf(why, n, "params is NULL");
+        return false;
+    }
+    if (p->nx < 8 || p->ny < 8 || p->nz < 8) {
+        snprintf(why, n, "grid %dx%dx%d: every extent must be >= 8", p->nx, p->ny, p->nz);
+        return false;
+    }
+    if (p->nx % 4) {
+        snprintf(why, n, "nx = %d must be a multiple of 4", p->nx);
+        return false;
+    }
+    if ((long long)p->nx * p->ny * p->nz > (1LL << 33)) {
+        snprintf(why, n, "grid too large");
+        return false;
+    }
+    if (p->precision < GBFD_FP64 || p->precision > GBFD_FP32_ACC64_W64) {
+        snprintf(why, n, "unknown precision %d", p->precision);
+        return false;
+    }
+    if (p->form != GBFD_55P && p->form != GBFD_19P) {
+        snprintf(why, n, "unknown form %d", p->form);
+        return false;
+    }
+    if (p->entropy_mode != 0 && p->entropy_mode != 1) {
+        snprintf(why, n, "entropy_mode must be 0 or 1");
+        return false;
+    }
+    const double v[5] = {p->lx, p->ly, p->lz, p->cs, p->nu};
+    for (int i = 0; i < 5; ++i)
+        if (!std::isfinite(v[i])) {
+            snprintf(why, n, "non-finite box length or physical parameter");
+            return false;
+        }
+    if (p->lx <= 0 || p->ly <= 0 || p->lz <= 0 || p->cs < 0 || p->nu < 0) {
+        snprintf(why, n, "box lengths must be > 0, cs and nu >= 0");
+        return false;
+    }
+    return true;
+}
+
+struct Plan {
+    Layout Ls, Lw, Ld;
+    size_t off_state[2], off_w, off_div, off_staging, off_part, off_out, off_err, total;
+    int ndiag;
+};
+
+Plan make_plan(const gbfd_params *p)
+{
+    Plan pl;
+    const int nf = nfields_of(p);
+    const int sb = p->precision == GBFD_FP64 ? 8 : 4;
+    const int wb = (p->precision == GBFD_FP64 || p->precision == GBFD_FP32_ACC64_W64) ? 8 : 4;
+    pl.Ls = make_layout(p->nx, p->ny, p->nz, sb, nf);
+    pl.Lw = make_layout(p->nx, p->ny, p->nz, wb, nf);
+    pl.Ld = make_layout(p->nx, p->ny, p->nz, sb, 1);
+    pl.ndiag = diag_blocks(pl.Ls);
+    size_t off = 0;
+    for (int i = 0; i < 2; ++i) {
+        pl.off_state[i] = off;
+        off = align256(off + pl.Ls.bytes);
+    }
+    pl.off_w = off;
+    off = align256(off + pl.Lw.bytes);
+    pl.off_div = off;
+    if (p->form == GBFD_19P)
+        off = align256(off + pl.Ld.bytes);
+    pl.off_staging = off;
+    off = align256(off + (size_t)nf * p->nx * p->ny * p->nz * 8);
+    pl.off_part = off;
+    off = align256(off + (size_t)pl.ndiag * 16 * sizeof(double));
+    pl.off_out = off;
+    off = align256(off + 16 * sizeof(double));
+    pl.off_err = off;
+    off = align256(off + 256);
+    pl.total = off;
+    return pl;
+}
+
+StateBufs bufs(gbfd_ctx *c)
+{
+    StateBufs b;
+    b.in = c->state_region[c->cur] + c->Ls.origin;
+    b.out = c->state_region[c->cur ^ 1] + c->Ls.origin;
+    b.w = c->w_region + c->Lw.origin;
+    b.div = c->div_region ? c->div_region + c->Ld.origin : nullptr;
+    b.Ls = c->Ls;
+    b.Lw = c->Lw;
+    return b;
+}
+
+gbfd_status check_ctx(gbfd_ctx *c)
+{
+    if (!c)
+        return GBFD_ERR_INVALID_ARG;
+    if (c->broken) {
+        set_err(c, "context unusable after an earlier device fault");
+        return GBFD_ERR_STATE;
+    }
+    return GBFD_OK;
+}
+
+gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
+{
+    StateBufs b = bufs(c);
+    RKStage st = make_stage(s, dt, c->p.nu);
+    int n = 0;
+    cudaError_t e = cudaSuccess;
+    const bool tiled = c->kernel_path == 0;
+    switch (c->p.precision) {
+    case GBFD_FP64:
+        e = tiled ? launch_substep_tiled<double, double, double>(b, c->c64, st, c->nf, c->p.form,
+                                                                 c->tile_cfg, c->dev_error, &c->tmaps,
+                                                                 c->stream, &n)
+                  : launch_substep_simple<double, double, double>(b, c->c64, st, c->nf, c->p.form,
+                                                                  c->stream, &n);
+        break;
+    case GBFD_FP32:
+        e = tiled ? launch_substep_tiled<float, float, float>(b, c->c32, st, c->nf, c->p.form,
+                                                              c->tile_cfg, c->dev_error, &c->tmaps,
+                                                              c->stream, &n)
+                  : launch_substep_simple<float, float, float>(b, c->c32, st, c->nf, c->p.form,
+                                                               c->stream, &n);
+        break;
+    case GBFD_FP32_ACC64:
+        e = tiled ? launch_substep_tiled<float, float, double>(b, c->c32, st, c->nf, c->p.form,
+                                                               c->tile_cfg, c->dev_error, &c->tmaps,
+                                                               c->stream, &n)
+                  : launch_substep_simple<float, float, double>(b, c->c32, st, c->nf, c->p.form,
+                                                                c->stream, &n);
+        break;
+    default:
+        e = tiled ? launch_substep_tiled<float, double, double>(b, c->c32, st, c->nf, c->p.form,
+                                                                c->tile_cfg, c->dev_error, &c->tmaps,
+                                                                c->stream, &n)
+                  : launch_substep_simple<float, double, double>(b, c->c32, st, c->nf, c->p.form,
+                                                                 c->stream, &n);
+        break;
+    }
+    c->launches += n;
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "substep launch");
+    c->cur ^= 1;
+    return GBFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gbfd_workspace_bytes(const gbfd_params *p)
+{
+    char why[256];
+    if (!validate(p, why, sizeof why))
+        return 0;
+    return make_plan(p).total;
+}
+
+gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_bytes, void *stream,
+                      gbfd_ctx **out)
+{
+    char why[256];
+    if (!out) {
+        set_err(nullptr, "out is NULL");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!validate(p, why, sizeof why)) {
+        set_err(nullptr, "%s", why);
+        return GBFD_ERR_INVALID_ARG;
+    }
+    Plan pl = make_plan(p);
+    if (!workspace || ((uintptr_t)workspace & 255)) {
+        set_err(nullptr, "workspace must be a non-NULL, 256-byte aligned device pointer");
+        return GBFD_ERR_WORKSPACE;
+    }
+    if (workspace_bytes < pl.total) {
+        set_err(nullptr, "workspace has %zu bytes, %zu needed", workspace_bytes, pl.total);
+        return GBFD_ERR_WORKSPACE;
+    }
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, workspace);
+    if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        set_err(nullptr, "workspace is not device memory");
+        return GBFD_ERR_WORKSPACE;
+    }
+    gbfd_ctx *c = new (std::nothrow) gbfd_ctx();
+    if (!c) {
+        set_err(nullptr, "out of host memory");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    c->p = *p;
+    c->nf = nfields_of(p);
+    c->sbytes = pl.Ls.w;
+    c->wbytes = pl.Lw.w;
+    c->stream = (cudaStream_t)stream;
+    c->ws = (char *)workspace;
+    c->ws_bytes = workspace_bytes;
+    c->Ls = pl.Ls;
+    c->Lw = pl.Lw;
+    c->Ld = pl.Ld;
+    c->state_region[0] = c->ws + pl.off_state[0];
+    c->state_region[1] = c->ws + pl.off_state[1];
+    c->w_region = c->ws + pl.off_w;
+    c->div_region = p->form == GBFD_19P ? c->ws + pl.off_div : nullptr;
+    c->staging = c->ws + pl.off_staging;
+    c->diag_part = (double *)(c->ws + pl.off_part);
+    c->diag_out = (double *)(c->ws + pl.off_out);
+    c->dev_error = (int *)(c->ws + pl.off_err);
+    c->ndiag = pl.ndiag;
+    c->cur = 0;
+    c->launches = 0;
+    c->kernel_path = 0;
+    c->tile_cfg = -1;
+    memset(&c->tmaps, 0, sizeof c->tmaps);
+    c->broken = false;
+    const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
+    c->c64 = make_coef<double>(hx, hy, hz, p->cs, p->nu);
+    c->c32 = make_coef<float>(hx, hy, hz, p->cs, p->nu);
+    c->err[0] = 0;
+    // zero state, ghosts, padding and the error word once
+    e = cudaMemsetAsync(c->ws, 0, pl.total, c->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "workspace clear");
+        delete c;
+        return GBFD_ERR_CUDA;
+    }
+    *out = c;
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_destroy(gbfd_ctx *ctx)
+{
+    delete ctx;
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value)
+{
+    gbfd_status s = check_ctx(ctx);
+    if (s != GBFD_OK)
+        return s;
+    switch (key) {
+    case GBFD_OPT_KERNEL_PATH:
+        if (value != 0 && value != 1)
+            break;
+        ctx->kernel_path = (int)value;
+        return GBFD_OK;
+    case GBFD_OPT_TILE_CONFIG:
+        if (value < -1 || value >= tiled_config_count(ctx->sbytes))
+            break;
+        ctx->tile_cfg = (int)value;
+        return GBFD_OK;
+    default:
+        break;
+    }
+    set_err(ctx, "option %d: value %lld rejected", key, (long long)value);
+    return GBFD_ERR_INVALID_ARG;
+}
+
+gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, int src_is_fp64)
+{
+    gbfd_status s = check_ctx(ctx);
+    if (s != GBFD_OK)
+        return s;
+    if (!src) {
+        set_err(ctx, "src is NULL");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const size_t n = (size_t)ctx->nf * ctx->p.nx * ctx->p.ny * ctx->p.nz;
+    const size_t bytes = n * (src_is_fp64 ? 8 : 4);
+    const void *from = src;
+    if (!src_on_device) {
+        cudaError_t e =
+            cudaMemcpyAsync(ctx->staging, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "set_state copy");
+        from = ctx->staging;
+    }
+    int nl = 0;
+    cudaError_t e = launch_scatter(from, src_is_fp64, ctx->state_region[ctx->cur] + ctx->Ls.origin,
+                                   ctx->Ls, ctx->nf, ctx->stream, &nl);
+    ctx->launches += nl;
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "set_state scatter");
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_get_state(gbfd_ctx *ctx, void *dst, int dst_on_device, int dst_is_fp64)
+{
+    gbfd_status s = check_ctx(ctx);
+    if (s != GBFD_OK)
+        return s;
+    if (!dst) {
+        set_err(ctx, "dst is NULL");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const size_t n = (size_t)ctx->nf * ctx->p.nx * ctx->p.ny * ctx->p.nz;
+    const size_t bytes = n * (dst_is_fp64 ? 8 : 4);
+    void *to = dst_on_device ? dst : (void *)ctx->staging;
+    int nl = 0;
+    cudaError_t e = launch_gather(ctx->state_region[ctx->cur] + ctx->Ls.origin, ctx->Ls, to,
+                                  dst_is_fp64, ctx->nf, ctx->stream, &nl);
+    ctx->launches += nl;
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "get_state gather");
+    if (!dst_on_device) {
+        e = cudaMemcpyAsync(dst, ctx->staging, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "get_state copy");
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "get_state sync");
+    }
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_substep(gbfd_ctx *ctx, int s, double dt)
+{
+    gbfd_status st = check_ctx(ctx);
+    if (st != GBFD_OK)
+        return st;
+    if (s < 0 || s > 2 || !(dt > 0) || !std::isfinite(dt)) {
+        set_err(ctx, "substep %d / dt %g rejected", s, dt);
+        return GBFD_ERR_INVALID_ARG;
+    }
+    return do_substep(ctx, s, dt);
+}
+
+gbfd_status gbfd_rk3_step(gbfd_ctx *ctx, double dt, int nsteps)
+{
+    gbfd_status st = check_ctx(ctx);
+    if (st != GBFD_OK)
+        return st;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) {
+        set_err(ctx, "rk3_step: dt %g / nsteps %d rejected", dt, nsteps);
+        return GBFD_ERR_INVALID_ARG;
+    }
+    for (int n = 0; n < nsteps; ++n)
+        for (int s = 0; s < 3; ++s) {
+            st = do_substep(ctx, s, dt);
+            if (st != GBFD_OK)
+                return st;
+        }
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_sync(gbfd_ctx *ctx)
+{
+    gbfd_status st = check_ctx(ctx);
+    if (st != GBFD_OK)
+        return st;
+    int herr = 0;
+    cudaError_t e = cudaMemcpyAsync(&herr, ctx->dev_error, sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "sync");
+    if (herr) {
+        set_err(ctx, "device-side bounded wait gave up (code %d)", herr);
+        cudaMemsetAsync(ctx->dev_error, 0, sizeof(int), ctx->stream);
+        return GBFD_ERR_TIMEOUT;
+    }
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_diagnostics(gbfd_ctx *ctx, gbfd_diag *out)
+{
+    gbfd_status st = check_ctx(ctx);
+    if (st != GBFD_OK)
+        return st;
+    if (!out) {
+        set_err(ctx, "out is NULL");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const double dv = (ctx->p.lx / ctx->p.nx) * (ctx->p.ly / ctx->p.ny) * (ctx->p.lz / ctx->p.nz);
+    int nl = 0;
+    cudaError_t e = launch_diagnostics(ctx->state_region[ctx->cur] + ctx->Ls.origin, ctx->Ls,
+                                       ctx->nf, dv, ctx->diag_part, ctx->ndiag, ctx->diag_out,
+                                       ctx->stream, &nl);
+    ctx->launches += nl;
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "diagnostics launch");
+    double h[16];
+    e = cudaMemcpyAsync(h, ctx->diag_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "diagnostics read");
+    out->mass = h[0];
+    out->ekin = h[1];
+    out->umax = h[2];
+    out->urms = h[3];
+    for (int f = 0; f < 5; ++f) {
+        out->rms[f] = h[4 + f];
+        out->maxabs[f] = h[9 + f];
+    }
+    out->nonfinite = h[14] != 0.0;
+    out->nfields = ctx->nf;
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_cfl_dt(gbfd_ctx *ctx, double cfl, double cnu, double *dt_out)
+{
+    if (!dt_out || !(cfl > 0) || !(cnu > 0)) {
+        if (ctx)
+            set_err(ctx, "cfl_dt: bad arguments");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    gbfd_diag d;
+    gbfd_status st = gbfd_diagnostics(ctx, &d);
+    if (st != GBFD_OK)
+        return st;
+    const double h[3] = {ctx->p.lx / ctx->p.nx, ctx->p.ly / ctx->p.ny, ctx->p.lz / ctx->p.nz};
+    double dmin = h[0] < h[1] ? h[0] : h[1];
+    dmin = dmin < h[2] ? dmin : h[2];
+    double dt = cfl * dmin / (d.umax + ctx->p.cs);
+    if (ctx->p.nu > 0) {
+        const double dtn = cnu * dmin * dmin / ctx->p.nu;
+        dt = dtn < dt ? dtn : dt;
+    }
+    *dt_out = dt;
+    return GBFD_OK;
+}
+
+int64_t gbfd_launch_count(const gbfd_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+const char *gbfd_last_error(const gbfd_ctx *ctx) { return ctx ? ctx->err : g_init_err; }
+
+const char *gbfd_status_string(gbfd_status s)
+{
+    switch (s) {
+    case GBFD_OK:
+        return "GBFD_OK";
+    case GBFD_ERR_INVALID_ARG:
+        return "GBFD_ERR_INVALID_ARG";
+    case GBFD_ERR_WORKSPACE:
+        return "GBFD_ERR_WORKSPACE";
+    case GBFD_ERR_CUDA:
+        return "GBFD_ERR_CUDA";
+    case GBFD_ERR_TIMEOUT:
+        return "GBFD_ERR_TIMEOUT";
+    case GBFD_ERR_UNSUPPORTED:
+        return "GBFD_ERR_UNSUPPORTED";
+    case GBFD_ERR_STATE:
+        return "GBFD_ERR_STATE";
+    }
+    return "unknown";
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// Internal definitions shared by the libgbfd translation units: the padded
+// field layout in HBM, the stencil coefficient tables, the Williamson RK3
+// coefficients and the per-point right-hand side of Eqs. 1-3.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbfd {
+
+// ---------------------------------------------------------------------------
+// Padded field layout.
+//
+// Each field is stored as [z][Y][X] with ghost columns/rows in x and y only:
+// interior point (x, y, z) lives at X = x + GX, Y = y + GY.  The ghosts hold
+// periodic copies (X in [0, GX) is x = nx-GX.., X in [nx+GX, nx+2GX) is
+// x = 0..GX-1; same in y with GY) so that a tile plus its 3-cell halo is one
+// rectangular, in-bounds box for TMA.  z needs no ghosts: a plane is fetched
+// by its wrapped index.  The row pitch P is a multiple of 128 bytes and the
+// origin is offset so that every interior row starts 128-byte aligned
+// (whole-sector warp accesses).  GX = 4 (not 3) keeps the TMA box origin
+// X = x0 16-byte aligned.
+// ---------------------------------------------------------------------------
+constexpr int GX = 4;
+constexpr int GY = 3;
+constexpr int R = 3;  // stencil radius (sixth order, n = 2R)
+
+struct Layout {
+    int nx, ny, nz;
+    int w;              // bytes per value
+    long long P;        // row pitch, elements
+    long long rows;     // rows per plane, ny + 2 GY
+    long long plane;    // P * rows
+    long long fpitch;   // elements between consecutive fields
+    long long origin;   // byte offset of element (f=0,z=0,Y=0,X=0) in the region
+    long long bytes;    // region bytes for `nf` fields
+};
+
+inline Layout make_layout(int nx, int ny, int nz, int w, int nf)
+{
+    Layout L;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = nz;
+    L.w = w;
+    const long long q = 128 / w;  // elements per 128 bytes
+    L.P = ((nx + 2 * GX + q - 1) / q) * q;
+    L.rows = ny + 2 * GY;
+    L.plane = L.P * L.rows;
+    L.fpitch = L.plane * nz;  // P*w is a multiple of 128, so is this
+    L.origin = 128 - GX * w;
+    L.bytes = 128 + (long long)nf * L.fpitch * w;
+    return L;
+}
+
+// Element index of interior point (x, y, z) of field f relative to origin.
+__host__ __device__ inline long long lidx(const Layout &L, int f, int z, int y, int x)
+{
+    return (long long)f * L.fpitch + (long long)z * L.plane + (long long)(y + GY) * L.P + (x + GX);
+}
+
+// ---------------------------------------------------------------------------
+// Stencil coefficients (Eqs. 6-8) with the grid spacing folded in.
+//   D1 f = sum_k d1[a][k-1] (f_{+k} - f_{-k})                      (Eq. 6)
+//   D2 f = d2c[a] f_0 + sum_k d2[a][k-1] (f_{+k} + f_{-k})         (Eq. 7)
+//   Dab f = sum_k mx[p][k-1] (f_{+k,+k} - f_{-k,+k} + f_{-k,-k} - f_{+k,-k})
+//                                                                  (Eq. 8)
+// pair p: 0 = (x,y), 1 = (x,z), 2 = (y,z).
+// ---------------------------------------------------------------------------
+template <class T>
+struct Coef {
+    T d1[3][3];
+    T d2c[3];
+    T d2[3][3];
+    T mx[3][3];
+    T cs2;     // c_s^2
+    T nu;      // nu
+    T nu3;     // nu / 3
+    T nu2;     // 2 nu
+    T nu23;    // (2/3) nu
+};
+
+template <class T>
+inline Coef<T> make_coef(double hx, double hy, double hz, double cs, double nu)
+{
+    Coef<T> c;
+    const double h[3] = {hx, hy, hz};
+    const double d1w[3] = {45.0, -9.0, 1.0};
+    const double d2w[3] = {270.0, -27.0, 2.0};
+    const double mxw[3] = {270.0, -27.0, 2.0};
+    for (int a = 0; a < 3; ++a) {
+        for (int k = 0; k < 3; ++k) {
+            c.d1[a][k] = (T)(d1w[k] / (60.0 * h[a]));
+            c.d2[a][k] = (T)(d2w[k] / (180.0 * h[a] * h[a]));
+        }
+        c.d2c[a] = (T)(-490.0 / (180.0 * h[a] * h[a]));
+    }
+    const double hp[3][2] = {{hx, hy}, {hx, hz}, {hy, hz}};
+    for (int p = 0; p < 3; ++p)
+        for (int k = 0; k < 3; ++k)
+            c.mx[p][k] = (T)(mxw[k] / (720.0 * hp[p][0] * hp[p][1]));
+    c.cs2 = (T)(cs * cs);
+    c.nu = (T)nu;
+    c.nu3 = (T)(nu / 3.0);
+    c.nu2 = (T)(2.0 * nu);
+    c.nu23 = (T)(2.0 * nu / 3.0);
+    return c;
+}
+
+// Williamson (1980) 2N-storage RK3: the paper's Eq. 10 leaves alpha, beta to
+// the chosen scheme and fixes alpha_1 = 0.
+constexpr double RK3_ALPHA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+constexpr double RK3_BETA[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+// ---------------------------------------------------------------------------
+// Right-hand side of Eqs. 1-3 (f = 0) at one point from its derivatives.
+// gu[i][j] = d_j u_i.  lap[i] = sum_j D2_j u_i.  gd[i] = d_i(div u), the
+// grad-div term (left 0 by the 19-point first pass, which adds it in pass 2).
+// ---------------------------------------------------------------------------
+template <class T>
+struct PointDerivs {
+    T u[3];
+    T gl[3];
+    T gu[3][3];
+    T gs[3];
+    T lap[3];
+    T gd[3];
+};
+
+template <class T, int NF>
+__device__ __forceinline__ void rhs_point(const PointDerivs<T> &d, const Coef<T> &c, T *out)
+{
+    const T div = d.gu[0][0] + d.gu[1][1] + d.gu[2][2];
+    // Eq. 1
+    out[0] = -(d.u[0] * d.gl[0] + d.u[1] * d.gl[1] + d.u[2] * d.gl[2]) - div;
+    // Eq. 3 and Eq. 2:  2 (S . grad lnrho)_i
+    //   = sum_j (d_j u_i + d_i u_j) d_j lnrho - (2/3) div d_i lnrho
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T adv = d.u[0] * d.gu[i][0] + d.u[1] * d.gu[i][1] + d.u[2] * d.gu[i][2];
+        T s2 = (d.gu[i][0] + d.gu[0][i]) * d.gl[0] + (d.gu[i][1] + d.gu[1][i]) * d.gl[1] +
+               (d.gu[i][2] + d.gu[2][i]) * d.gl[2];
+        T visc = c.nu * (d.lap[i] + s2) + c.nu3 * d.gd[i] - c.nu23 * div * d.gl[i];
+        out[1 + i] = -adv - c.cs2 * d.gl[i] + visc;
+    }
+    if (NF == 5)
+        out[4] = -(d.u[0] * d.gs[0] + d.u[1] * d.gs[1] + d.u[2] * d.gs[2]);
+}
+
+// Eq. 10 update of one value: w <- alpha w + dt r (the first substep ignores
+// the old w, alpha_1 = 0), u_out <- u + beta w; arithmetic in TA.
+template <class TA, class TW, class TS>
+__device__ __forceinline__ void rk3_update(bool first, TA alpha, TA beta, TA dt, TA r, TS u,
+                                           TW &w, TS &out)
+{
+    TA wn = first ? dt * r : alpha * (TA)w + dt * r;
+    w = (TW)wn;
+    out = (TS)((TA)u + beta * wn);
+}
+
+// Store v at interior (x, y, z) of field f and at its periodic ghost copies.
+template <class T>
+__device__ __forceinline__ void store_ghosted(T *base, const Layout &L, int f, int z, int y, int x,
+                                              T v)
+{
+    const long long i0 = lidx(L, f, z, y, x);
+    base[i0] = v;
+    long long dx = 0, dy = 0;
+    if (x < GX)
+        dx = L.nx;
+    else if (x >= L.nx - GX)
+        dx = -L.nx;
+    if (y < GY)
+        dy = (long long)L.ny * L.P;
+    else if (y >= L.ny - GY)
+        dy = -(long long)L.ny * L.P;
+    if (dx)
+        base[i0 + dx] = v;
+    if (dy) {
+        base[i0 + dy] = v;
+        if (dx)
+            base[i0 + dy + dx] = v;
+    }
+}
+
+// Host-side launch helpers implemented in the kernel translation units.
+struct StateBufs {
+    void *in;    // padded state, storage type
+    void *out;   // padded state, storage type
+    void *w;     // padded 2N register (u-tilde)
+    void *div;   // padded divergence field (19-point form)
+    Layout Ls;   // layout of in/out/div (div uses one field)
+    Layout Lw;   // layout of w
+};
+
+}  // namespace gbfd

@@ -1,0 +1,212 @@
+// State copies into/out of the padded layout and the FP64 diagnostics
+// reductions (mass, kinetic energy, max |u| for the time-step rule, per-field
+// rms and max, non-finite flag).
+#include "kernels.cuh"
+
+namespace gbfd {
+
+namespace {
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Every padded cell (interior and ghost) of every field from the compact
+// source; ghosts take the periodic image.
+template <class TD, class TSrc>
+__global__ void k_scatter(const TSrc *__restrict__ src, TD *__restrict__ dst, Layout L)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Y = blockIdx.y;
+    const int z = blockIdx.z % L.nz;
+    const int f = blockIdx.z / L.nz;
+    if (X >= L.nx + 2 * GX)
+        return;
+    const int x = wrapi(X - GX, L.nx);
+    const int y = wrapi(Y - GY, L.ny);
+    const long long s = (((long long)f * L.nz + z) * L.ny + y) * L.nx + x;
+    dst[(long long)f * L.fpitch + (long long)z * L.plane + (long long)Y * L.P + X] = (TD)src[s];
+}
+
+template <class TS, class TD>
+__global__ void k_gather(const TS *__restrict__ src, TD *__restrict__ dst, Layout L)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z % L.nz;
+    const int f = blockIdx.z / L.nz;
+    if (x >= L.nx)
+        return;
+    const long long d = (((long long)f * L.nz + z) * L.ny + y) * L.nx + x;
+    dst[d] = (TD)src[lidx(L, f, z, y, x)];
+}
+
+template <class TD, class TSrc>
+cudaError_t scatter_t(const TSrc *src, TD *dst, const Layout &L, int nf, cudaStream_t stream)
+{
+    dim3 block(128);
+    dim3 grid((L.nx + 2 * GX + 127) / 128, L.ny + 2 * GY, nf * L.nz);
+    k_scatter<TD, TSrc><<<grid, block, 0, stream>>>(src, dst, L);
+    return cudaGetLastError();
+}
+
+template <class TS, class TD>
+cudaError_t gather_t(const TS *src, TD *dst, const Layout &L, int nf, cudaStream_t stream)
+{
+    dim3 block(128);
+    dim3 grid((L.nx + 127) / 128, L.ny, nf * L.nz);
+    k_gather<TS, TD><<<grid, block, 0, stream>>>(src, dst, L);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reductions
+
+constexpr int DIAG_THREADS = 256;
+constexpr int NQ = 16;  // reduced quantities per block
+
+// q[0] sum rho, q[1] sum rho|u|^2/2, q[2] max|u|^2, q[3] sum |u|^2,
+// q[4..8] sum f^2, q[9..13] max |f|, q[14] non-finite count.
+template <class TS>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(const TS *__restrict__ st,
+                                                                Layout L, int nf,
+                                                                double *__restrict__ part)
+{
+    double q[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i)
+        q[i] = 0.0;
+    const long long nrows = (long long)L.nz * L.ny;
+    for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int z = (int)(r / L.ny), y = (int)(r % L.ny);
+        for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
+            double v[5];
+#pragma unroll
+            for (int f = 0; f < 5; ++f)
+                v[f] = f < nf ? (double)st[lidx(L, f, z, y, x)] : 0.0;
+            const double rho = exp(v[0]);
+            const double uu = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+            q[0] += rho;
+            q[1] += 0.5 * rho * uu;
+            q[2] = fmax(q[2], uu);
+            q[3] += uu;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                q[4 + f] += v[f] * v[f];
+                q[9 + f] = fmax(q[9 + f], fabs(v[f]));
+                if (!isfinite(v[f]))
+                    q[14] += 1.0;
+            }
+        }
+    }
+    // fixed-order block tree reduction
+    __shared__ double sh[DIAG_THREADS];
+    for (int i = 0; i < 15; ++i) {
+        const bool ismax = (i == 2) || (i >= 9 && i <= 13);
+        sh[threadIdx.x] = q[i];
+        __syncthreads();
+        for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double a = sh[threadIdx.x], b = sh[threadIdx.x + s];
+                sh[threadIdx.x] = ismax ? fmax(a, b) : a + b;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            part[(long long)blockIdx.x * NQ + i] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(const double *__restrict__ part,
+                                                              int nblocks, long long npts,
+                                                              double dv, double *__restrict__ out)
+{
+    __shared__ double sh[DIAG_THREADS];
+    __shared__ double res[NQ];
+    for (int i = 0; i < 15; ++i) {
+        const bool ismax = (i == 2) || (i >= 9 && i <= 13);
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += DIAG_THREADS) {
+            const double v = part[(long long)b * NQ + i];
+            a = ismax ? fmax(a, v) : a + v;
+        }
+        sh[threadIdx.x] = a;
+        __syncthreads();
+        for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double x = sh[threadIdx.x], y = sh[threadIdx.x + s];
+                sh[threadIdx.x] = ismax ? fmax(x, y) : x + y;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            res[i] = sh[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double n = (double)npts;
+        out[0] = dv * res[0];
+        out[1] = dv * res[1];
+        out[2] = sqrt(res[2]);
+        out[3] = sqrt(res[3] / n);
+        for (int f = 0; f < 5; ++f) {
+            out[4 + f] = sqrt(res[4 + f] / n);
+            out[9 + f] = res[9 + f];
+        }
+        out[14] = res[14] > 0.0 ? 1.0 : 0.0;
+        out[15] = 0.0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_scatter(const void *src, int src_fp64, void *dst, const Layout &L, int nf,
+                           cudaStream_t stream, int *launches)
+{
+    *launches += 1;
+    if (L.w == 8)
+        return src_fp64 ? scatter_t((const double *)src, (double *)dst, L, nf, stream)
+                        : scatter_t((const float *)src, (double *)dst, L, nf, stream);
+    return src_fp64 ? scatter_t((const double *)src, (float *)dst, L, nf, stream)
+                    : scatter_t((const float *)src, (float *)dst, L, nf, stream);
+}
+
+cudaError_t launch_gather(const void *src, const Layout &L, void *dst, int dst_fp64, int nf,
+                          cudaStream_t stream, int *launches)
+{
+    *launches += 1;
+    if (L.w == 8)
+        return dst_fp64 ? gather_t((const double *)src, (double *)dst, L, nf, stream)
+                        : gather_t((const double *)src, (float *)dst, L, nf, stream);
+    return dst_fp64 ? gather_t((const float *)src, (double *)dst, L, nf, stream)
+                    : gather_t((const float *)src, (float *)dst, L, nf, stream);
+}
+
+int diag_blocks(const Layout &L)
+{
+    const long long rows = (long long)L.nz * L.ny;
+    return (int)(rows < 1216 ? rows : 1216);  // 8 blocks per SM on 152 SMs
+}
+
+cudaError_t launch_diagnostics(const void *state, const Layout &L, int nf, double dv,
+                               double *partials, int nblocks, double *out, cudaStream_t stream,
+                               int *launches)
+{
+    if (L.w == 8)
+        k_diag_partial<double><<<nblocks, DIAG_THREADS, 0, stream>>>((const double *)state, L, nf,
+                                                                     partials);
+    else
+        k_diag_partial<float><<<nblocks, DIAG_THREADS, 0, stream>>>((const float *)state, L, nf,
+                                                                    partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    k_diag_final<<<1, DIAG_THREADS, 0, stream>>>(partials, nblocks,
+                                                 (long long)L.nx * L.ny * L.nz, dv, out);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace gbfd

@@ -1,0 +1,52 @@
+// Launch interfaces of the kernel translation units (internal to libgbfd).
+#pragma once
+
+#include "common.cuh"
+
+namespace gbfd {
+
+// Per-substep scalars of Eq. 10.
+struct RKStage {
+    double alpha, beta, dt;
+    double nu3;  // nu / 3, used by the second pass of the 19-point form
+    int first;   // substep 1: alpha_1 = 0, the old w is not read
+    int s;       // 0, 1, 2
+};
+
+inline RKStage make_stage(int s, double dt, double nu)
+{
+    RKStage st;
+    st.alpha = RK3_ALPHA[s];
+    st.beta = RK3_BETA[s];
+    st.dt = dt;
+    st.nu3 = nu / 3.0;
+    st.first = (s == 0);
+    st.s = s;
+    return st;
+}
+
+template <class TS, class TW, class TA>
+cudaError_t launch_substep_simple(const StateBufs &b, const Coef<TS> &c, const RKStage &st,
+                                  int nf, int form, cudaStream_t stream, int *launches);
+
+// Second pass of the 19-point form (Algorithm 3): w += dt (nu/3) grad div,
+// out += beta dt (nu/3) grad div, from the stored divergence field.
+template <class TS, class TW, class TA>
+cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKStage &st,
+                                cudaStream_t stream, int *launches);
+
+// State copies between a compact [f][z][y][x] staging buffer (FP64 or FP32)
+// and the padded layout (ghosts filled on the way in).
+cudaError_t launch_scatter(const void *src, int src_fp64, void *dst, const Layout &L, int nf,
+                           cudaStream_t stream, int *launches);
+cudaError_t launch_gather(const void *src, const Layout &L, void *dst, int dst_fp64, int nf,
+                          cudaStream_t stream, int *launches);
+
+// FP64 reductions: partials per block, then one fixed-order final pass.
+// out[16]: mass, ekin, umax, urms, rms[5], maxabs[5], nonfinite, (pad).
+int diag_blocks(const Layout &L);
+cudaError_t launch_diagnostics(const void *state, const Layout &L, int nf, double dv,
+                               double *partials, int nblocks, double *out, cudaStream_t stream,
+                               int *launches);
+
+}  // namespace gbfd

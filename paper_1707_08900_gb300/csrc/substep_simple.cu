@@ -1,0 +1,181 @@
+// Simple substep kernels: one thread per grid point, every stencil value read
+// from global memory (L1/L2 cached).  They are the generic path for any
+// valid grid and the cross-check for the tiled kernels; the fused
+// 55-point substep is Algorithm 2, the two kernels of the 19-point form are
+// the two passes of Algorithm 3 (Eqs. 14-16).
+#include "kernels.cuh"
+#include "stencil.cuh"
+
+namespace gbfd {
+
+namespace {
+
+template <class T>
+struct GlobalAcc {
+    const T *__restrict__ base;  // origin of the padded state
+    Layout L;
+    int x, y;
+    int zk[7];  // wrapped plane index for dz = -3..3
+    __device__ __forceinline__ T operator()(int f, int dz, int dy, int dx) const
+    {
+        return __ldg(base + (long long)f * L.fpitch + (long long)zk[dz + 3] * L.plane +
+                     (long long)(y + GY + dy) * L.P + (x + GX + dx));
+    }
+};
+
+template <class T>
+__device__ __forceinline__ GlobalAcc<T> make_acc(const T *base, const Layout &L, int x, int y,
+                                                 int z)
+{
+    GlobalAcc<T> A;
+    A.base = base;
+    A.L = L;
+    A.x = x;
+    A.y = y;
+#pragma unroll
+    for (int k = -3; k <= 3; ++k) {
+        int zz = z + k;
+        zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
+        A.zk[k + 3] = zz;
+    }
+    return A;
+}
+
+// Algorithm 2 (MIXED = true) or the first pass of Algorithm 3 (MIXED = false,
+// which also stores div u for the second pass).
+template <class TS, class TW, class TA, int NF, bool MIXED>
+__global__ void __launch_bounds__(128) k_substep_simple(const TS *__restrict__ in,
+                                                        TS *__restrict__ out,
+                                                        TW *__restrict__ w, TS *__restrict__ divf,
+                                                        Layout Ls, Layout Lw, Coef<TS> c,
+                                                        RKStage st)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= Ls.nx || y >= Ls.ny)
+        return;
+    GlobalAcc<TS> A = make_acc(in, Ls, x, y, z);
+    PointDerivs<TS> d;
+    gather_derivs<TS, NF, MIXED>(A, c, d);
+    TS r[5];
+    rhs_point<TS, NF>(d, c, r);
+    if (!MIXED) {
+        TS div = d.gu[0][0] + d.gu[1][1] + d.gu[2][2];
+        store_ghosted(divf, Ls, 0, z, y, x, div);
+    }
+    const TA alpha = (TA)st.alpha, beta = (TA)st.beta, dt = (TA)st.dt;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const long long iw = lidx(Lw, f, z, y, x);
+        TW wv = st.first ? (TW)0 : w[iw];
+        TS o;
+        rk3_update<TA, TW, TS>(st.first, alpha, beta, dt, (TA)r[f], A(f, 0, 0, 0), wv, o);
+        w[iw] = wv;
+        store_ghosted(out, Ls, f, z, y, x, o);
+    }
+}
+
+// Second pass of Algorithm 3: w += dt (nu/3) grad(div u),
+// out += beta dt (nu/3) grad(div u), grad by Eq. 6 on the stored divergence.
+template <class TS, class TW, class TA>
+__global__ void __launch_bounds__(128) k_pass2_simple(const TS *__restrict__ divf,
+                                                      TS *__restrict__ out, TW *__restrict__ w,
+                                                      Layout Ls, Layout Lw, Coef<TS> c,
+                                                      RKStage st)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= Ls.nx || y >= Ls.ny)
+        return;
+    GlobalAcc<TS> A = make_acc(divf, Ls, x, y, z);
+    const TA dt = (TA)st.dt, beta = (TA)st.beta, nu3 = (TA)st.nu3;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const TA g = (TA)d1_axis(A, 0, i, c);
+        const long long iw = lidx(Lw, 1 + i, z, y, x);
+        const long long io = lidx(Ls, 1 + i, z, y, x);
+        w[iw] = (TW)((TA)w[iw] + dt * nu3 * g);
+        store_ghosted(out, Ls, 1 + i, z, y, x, (TS)((TA)out[io] + beta * dt * nu3 * g));
+    }
+}
+
+}  // namespace
+
+template <class TS, class TW, class TA>
+cudaError_t launch_substep_simple(const StateBufs &b, const Coef<TS> &c, const RKStage &st,
+                                  int nf, int form, cudaStream_t stream, int *launches)
+{
+    const dim3 block(32, 4, 1);
+    const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
+    const TS *in = (const TS *)b.in;
+    TS *out = (TS *)b.out;
+    TW *w = (TW *)b.w;
+    TS *divf = (TS *)b.div;
+    if (form == 0) {
+        if (nf == 5)
+            k_substep_simple<TS, TW, TA, 5, true><<<grid, block, 0, stream>>>(in, out, w, divf, b.Ls,
+                                                                             b.Lw, c, st);
+        else
+            k_substep_simple<TS, TW, TA, 4, true><<<grid, block, 0, stream>>>(in, out, w, divf, b.Ls,
+                                                                             b.Lw, c, st);
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    if (nf == 5)
+        k_substep_simple<TS, TW, TA, 5, false><<<grid, block, 0, stream>>>(in, out, w, divf, b.Ls,
+                                                                          b.Lw, c, st);
+    else
+        k_substep_simple<TS, TW, TA, 4, false><<<grid, block, 0, stream>>>(in, out, w, divf, b.Ls,
+                                                                          b.Lw, c, st);
+    cudaError_t e = cudaGetLastError();
+    *launches += 1;
+    if (e != cudaSuccess)
+        return e;
+    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
+}
+
+template <class TS, class TW, class TA>
+cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKStage &st,
+                                cudaStream_t stream, int *launches)
+{
+    const dim3 block(32, 4, 1);
+    const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
+    k_pass2_simple<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,
+                                                           (TW *)b.w, b.Ls, b.Lw, c, st);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_substep_simple<double, double, double>(const StateBufs &,
+                                                                   const Coef<double> &,
+                                                                   const RKStage &, int, int,
+                                                                   cudaStream_t, int *);
+template cudaError_t launch_substep_simple<float, float, float>(const StateBufs &,
+                                                               const Coef<float> &,
+                                                               const RKStage &, int, int,
+                                                               cudaStream_t, int *);
+template cudaError_t launch_substep_simple<float, float, double>(const StateBufs &,
+                                                                const Coef<float> &,
+                                                                const RKStage &, int, int,
+                                                                cudaStream_t, int *);
+template cudaError_t launch_substep_simple<float, double, double>(const StateBufs &,
+                                                                 const Coef<float> &,
+                                                                 const RKStage &, int, int,
+                                                                 cudaStream_t, int *);
+
+template cudaError_t launch_pass2_simple<double, double, double>(const StateBufs &,
+                                                              const Coef<double> &, const RKStage &,
+                                                              cudaStream_t, int *);
+template cudaError_t launch_pass2_simple<float, float, float>(const StateBufs &,
+                                                              const Coef<float> &, const RKStage &,
+                                                              cudaStream_t, int *);
+template cudaError_t launch_pass2_simple<float, float, double>(const StateBufs &,
+                                                              const Coef<float> &, const RKStage &,
+                                                              cudaStream_t, int *);
+template cudaError_t launch_pass2_simple<float, double, double>(const StateBufs &,
+                                                              const Coef<float> &, const RKStage &,
+                                                              cudaStream_t, int *);
+
+}  // namespace gbfd

@@ -1,0 +1,43 @@
+// Tiled substep kernels (TMA-staged shared-memory plane ring, register
+// sliding along z).  Internal to libgbfd.
+#pragma once
+
+#include <cuda.h>
+
+#include "kernels.cuh"
+
+namespace gbfd {
+
+// One entry of a tile table searched by the autotuner.
+struct TileConfig {
+    int tx, ty;  // xy tile (threads per CTA = tx * ty, one point each per plane)
+    int zc;      // planes streamed per CTA
+    int ns;      // plane slots in the shared-memory ring
+};
+
+// Number of z-chunk lengths offered per (tx, ty, ns) variant; table index
+// i is variant i / kZcChoices with the (i % kZcChoices)-th chunk length.
+constexpr int kZcChoices = 4;
+
+// Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
+int tiled_config_count(int sbytes);
+TileConfig tiled_config(int sbytes, int i);
+
+// Encoded TMA descriptors of the state buffers, cached per context.
+struct TmapCache {
+    struct Entry {
+        const void *base;
+        int cfg;
+        int nf;
+        bool valid;
+        CUtensorMap map;
+    } e[8];
+    int next;
+};
+
+template <class TS, class TW, class TA>
+cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
+                                 int form, int cfg, int *dev_error, TmapCache *cache,
+                                 cudaStream_t stream, int *launches);
+
+}  // namespace gbfd

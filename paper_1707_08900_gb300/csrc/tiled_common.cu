@@ -1,0 +1,86 @@
+// Tile tables of the tiled substep kernels and TMA descriptor encoding.
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "tiled.cuh"
+
+namespace gbfd {
+
+namespace {
+
+// (tx, ty, ns) variants compiled per storage width; each is offered with
+// several z-chunk lengths.
+const TileConfig kVariants4[] = {{32, 8, 0, 9}, {32, 4, 0, 9}, {64, 4, 0, 9}, {32, 16, 0, 9}};
+const TileConfig kVariants8[] = {{32, 4, 0, 8}, {16, 8, 0, 8}};
+const int kZc[kZcChoices] = {32, 16, 64, 128};
+constexpr int kNz = kZcChoices;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+int tiled_config_count(int sbytes)
+{
+    return (sbytes == 8 ? (int)(sizeof kVariants8 / sizeof kVariants8[0])
+                        : (int)(sizeof kVariants4 / sizeof kVariants4[0])) *
+           kNz;
+}
+
+TileConfig tiled_config(int sbytes, int i)
+{
+    TileConfig t = sbytes == 8 ? kVariants8[i / kNz] : kVariants4[i / kNz];
+    t.zc = kZc[i % kNz];
+    return t;
+}
+
+bool get_state_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, int tx, int ty,
+                    int cfg_key, CUtensorMap **out)
+{
+    for (int i = 0; i < 8; ++i) {
+        TmapCache::Entry &e = cache->e[i];
+        if (e.valid && e.base == origin && e.cfg == cfg_key && e.nf == nf) {
+            *out = &e.map;
+            return true;
+        }
+    }
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn)
+        return false;
+    TmapCache::Entry &e = cache->e[cache->next];
+    cache->next = (cache->next + 1) % 8;
+    memset(&e, 0, sizeof e);
+    const cuuint64_t dims[4] = {(cuuint64_t)(L.nx + 2 * GX), (cuuint64_t)L.rows,
+                                (cuuint64_t)L.nz, (cuuint64_t)nf};
+    const cuuint64_t strides[3] = {(cuuint64_t)(L.P * L.w), (cuuint64_t)(L.plane * L.w),
+                                   (cuuint64_t)(L.fpitch * L.w)};
+    const cuuint32_t box[4] = {(cuuint32_t)(tx + 2 * GX), (cuuint32_t)(ty + 2 * GY), 1u,
+                               (cuuint32_t)nf};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(&e.map, L.w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    4, const_cast<void *>(origin), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return false;
+    e.base = origin;
+    e.cfg = cfg_key;
+    e.nf = nf;
+    e.valid = true;
+    *out = &e.map;
+    return true;
+}
+
+}  // namespace gbfd

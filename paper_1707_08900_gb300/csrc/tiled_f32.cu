@@ -1,0 +1,44 @@
+// Tiled substep instantiations with FP32 storage and FP32 arithmetic.
+#include "tiled_impl.cuh"
+
+namespace gbfd {
+
+template <class TS, class TW, class TA>
+cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
+                                 int form, int cfg, int *dev_error, TmapCache *cache,
+                                 cudaStream_t stream, int *launches)
+{
+    const int idx = cfg < 0 ? 0 : cfg;
+    const TileConfig t = tiled_config(4, idx);
+    const int v = idx / kZcChoices;
+    cudaError_t e;
+    switch (v) {
+    case 0:
+        e = launch_tiled_cfg<TS, TW, TA, 32, 8, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
+                                                   stream, launches);
+        break;
+    case 1:
+        e = launch_tiled_cfg<TS, TW, TA, 32, 4, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
+                                                   stream, launches);
+        break;
+    case 2:
+        e = launch_tiled_cfg<TS, TW, TA, 64, 4, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
+                                                   stream, launches);
+        break;
+    default:
+        e = launch_tiled_cfg<TS, TW, TA, 32, 16, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
+                                                    stream, launches);
+        break;
+    }
+    if (e != cudaSuccess || form == 0)
+        return e;
+    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
+}
+
+template cudaError_t launch_substep_tiled<float, float, float>(const StateBufs &,
+                                                               const Coef<float> &,
+                                                               const RKStage &, int, int, int,
+                                                               int *, TmapCache *, cudaStream_t,
+                                                               int *);
+
+}  // namespace gbfd

@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libgbfd (include/gbfd.h): same names, argument
+marshalling only.  Every step of the solver runs in the library's CUDA
+kernels; there is no CPU path.  PyTorch provides the device workspace and
+the stream.
+
+Low-level functions mirror the C ABI one to one (``gbfd_init``,
+``gbfd_rk3_step``, ...) and raise ``GbfdError`` on a non-OK status.
+``Solver`` bundles a context with its torch-allocated workspace.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GBFD_OK = 0
+STATUS = {0: "GBFD_OK", 1: "GBFD_ERR_INVALID_ARG", 2: "GBFD_ERR_WORKSPACE", 3: "GBFD_ERR_CUDA",
+          4: "GBFD_ERR_TIMEOUT", 5: "GBFD_ERR_UNSUPPORTED", 6: "GBFD_ERR_STATE"}
+
+GBFD_FP64, GBFD_FP32, GBFD_FP32_ACC64, GBFD_FP32_ACC64_W64 = 0, 1, 2, 3
+GBFD_55P, GBFD_19P = 0, 1
+GBFD_OPT_KERNEL_PATH, GBFD_OPT_TILE_CONFIG = 1, 2
+
+PRECISIONS = {"fp64": GBFD_FP64, "fp32": GBFD_FP32, "fp32_acc64": GBFD_FP32_ACC64,
+              "fp32_acc64_w64": GBFD_FP32_ACC64_W64}
+FORMS = {"55p": GBFD_55P, "19p": GBFD_19P}
+
+# exported symbols of include/gbfd.h (checked by the ABI test)
+EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state",
+           "gbfd_get_state", "gbfd_rk3_step", "gbfd_substep", "gbfd_diagnostics", "gbfd_cfl_dt",
+           "gbfd_sync", "gbfd_set_option", "gbfd_launch_count", "gbfd_last_error",
+           "gbfd_status_string")
+
+
+class GbfdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gbfd_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("entropy_mode", ctypes.c_int32), ("lx", ctypes.c_double),
+                ("ly", ctypes.c_double), ("lz", ctypes.c_double), ("cs", ctypes.c_double),
+                ("nu", ctypes.c_double)]
+
+
+class gbfd_diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("ekin", ctypes.c_double),
+                ("umax", ctypes.c_double), ("urms", ctypes.c_double),
+                ("rms", ctypes.c_double * 5), ("maxabs", ctypes.c_double * 5),
+                ("nonfinite", ctypes.c_int32), ("nfields", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"mass": self.mass, "ekin": self.ekin, "umax": self.umax, "urms": self.urms,
+                "rms": np.array(self.rms[:]), "maxabs": np.array(self.maxabs[:]),
+                "nonfinite": int(self.nonfinite), "nfields": int(self.nfields)}
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Open libgbfd.so (built by ``build.build()``); raises OSError if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise OSError(f"libgbfd.so not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    L.gbfd_workspace_bytes.restype = ctypes.c_size_t
+    L.gbfd_workspace_bytes.argtypes = [ctypes.POINTER(gbfd_params)]
+    L.gbfd_init.argtypes = [ctypes.POINTER(gbfd_params), _VP, ctypes.c_size_t, _VP,
+                            ctypes.POINTER(_VP)]
+    L.gbfd_destroy.argtypes = [_VP]
+    L.gbfd_set_state.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int]
+    L.gbfd_get_state.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int]
+    L.gbfd_rk3_step.argtypes = [_VP, ctypes.c_double, ctypes.c_int]
+    L.gbfd_substep.argtypes = [_VP, ctypes.c_int, ctypes.c_double]
+    L.gbfd_diagnostics.argtypes = [_VP, ctypes.POINTER(gbfd_diag)]
+    L.gbfd_cfl_dt.argtypes = [_VP, ctypes.c_double, ctypes.c_double,
+                              ctypes.POINTER(ctypes.c_double)]
+    L.gbfd_sync.argtypes = [_VP]
+    L.gbfd_set_option.argtypes = [_VP, ctypes.c_int, ctypes.c_int64]
+    L.gbfd_launch_count.restype = ctypes.c_int64
+    L.gbfd_launch_count.argtypes = [_VP]
+    L.gbfd_last_error.restype = ctypes.c_char_p
+    L.gbfd_last_error.argtypes = [_VP]
+    L.gbfd_status_string.restype = ctypes.c_char_p
+    L.gbfd_status_string.argtypes = [ctypes.c_int]
+    for name in EXPORTS:
+        getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != GBFD_OK:
+        msg = load().gbfd_last_error(ctx).decode(errors="replace")
+        raise GbfdError(status, msg)
+
+
+# ------------------------------------------------------------ C-ABI mirror
+
+def gbfd_workspace_bytes(params):
+    return load().gbfd_workspace_bytes(ctypes.byref(params))
+
+
+def gbfd_init(params, workspace_ptr, workspace_bytes, stream_ptr):
+    ctx = _VP()
+    _check(load().gbfd_init(ctypes.byref(params), _VP(workspace_ptr), workspace_bytes,
+                            _VP(stream_ptr), ctypes.byref(ctx)))
+    return ctx
+
+
+def gbfd_destroy(ctx):
+    _check(load().gbfd_destroy(ctx))
+
+
+def gbfd_set_state(ctx, src_ptr, src_on_device, src_is_fp64):
+    _check(load().gbfd_set_state(ctx, _VP(src_ptr), int(src_on_device), int(src_is_fp64)), ctx)
+
+
+def gbfd_get_state(ctx, dst_ptr, dst_on_device, dst_is_fp64):
+    _check(load().gbfd_get_state(ctx, _VP(dst_ptr), int(dst_on_device), int(dst_is_fp64)), ctx)
+
+
+def gbfd_rk3_step(ctx, dt, nsteps):
+    _check(load().gbfd_rk3_step(ctx, float(dt), int(nsteps)), ctx)
+
+
+def gbfd_substep(ctx, s, dt):
+    _check(load().gbfd_substep(ctx, int(s), float(dt)), ctx)
+
+
+def gbfd_diagnostics(ctx):
+    d = gbfd_diag()
+    _check(load().gbfd_diagnostics(ctx, ctypes.byref(d)), ctx)
+    return d
+
+
+def gbfd_cfl_dt(ctx, cfl=0.4, cnu=0.25):
+    out = ctypes.c_double()
+    _check(load().gbfd_cfl_dt(ctx, cfl, cnu, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def gbfd_sync(ctx):
+    _check(load().gbfd_sync(ctx), ctx)
+
+
+def gbfd_set_option(ctx, key, value):
+    _check(load().gbfd_set_option(ctx, int(key), int(value)), ctx)
+
+
+def gbfd_launch_count(ctx):
+    return load().gbfd_launch_count(ctx)
+
+
+def gbfd_last_error(ctx=None):
+    return load().gbfd_last_error(ctx).decode(errors="replace")
+
+
+# ------------------------------------------------------------ convenience
+
+def make_params(shape, lengths=(2 * np.pi,) * 3, cs=1.0, nu=5e-3, precision="fp64", form="55p",
+                entropy_mode=1):
+    nz, ny, nx = shape
+    p = gbfd_params()
+    p.nx, p.ny, p.nz = nx, ny, nz
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.form = FORMS[form] if isinstance(form, str) else int(form)
+    p.entropy_mode = int(entropy_mode)
+    p.lx, p.ly, p.lz = lengths
+    p.cs, p.nu = cs, nu
+    return p
+
+
+class Solver:
+    """A gbfd context plus its workspace (a torch CUDA uint8 tensor).
+
+    State arrays are (nfields, nz, ny, nx); nfields = 5 with entropy_mode 1,
+    4 with entropy_mode 0."""
+
+    def __init__(self, shape, lengths=(2 * np.pi,) * 3, cs=1.0, nu=5e-3, precision="fp64",
+                 form="55p", entropy_mode=1, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("gbfd needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.params = make_params(shape, lengths, cs, nu, precision, form, entropy_mode)
+        self.shape = tuple(shape)
+        self.nfields = 5 if entropy_mode else 4
+        nbytes = gbfd_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise GbfdError(1, "invalid parameters")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = gbfd_init(self.params, self.workspace.data_ptr(), nbytes,
+                             self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            gbfd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key, value):
+        gbfd_set_option(self.ctx, key, value)
+
+    def set_state(self, state):
+        """state: numpy (host) or torch (host or device) array, float64 or float32."""
+        torch = self.torch
+        if isinstance(state, np.ndarray):
+            state = torch.from_numpy(np.ascontiguousarray(state))
+        assert tuple(state.shape) == (self.nfields,) + self.shape, state.shape
+        state = state.contiguous()
+        is64 = state.dtype == torch.float64
+        if not is64 and state.dtype != torch.float32:
+            raise TypeError("state must be float64 or float32")
+        gbfd_set_state(self.ctx, state.data_ptr(), state.is_cuda, is64)
+        if not state.is_cuda:
+            self.stream.synchronize()  # the host buffer may be released after return
+
+    def get_state(self, fp64=True, out=None):
+        """Returns a numpy array (host), or fills `out` (torch, host or device)."""
+        torch = self.torch
+        if out is None:
+            out = np.empty((self.nfields,) + self.shape, dtype=np.float64 if fp64 else np.float32)
+            gbfd_get_state(self.ctx, out.ctypes.data, 0, fp64)
+            return out
+        gbfd_get_state(self.ctx, out.data_ptr(), out.is_cuda, out.dtype == torch.float64)
+        return out
+
+    def rk3_step(self, dt, nsteps=1):
+        gbfd_rk3_step(self.ctx, dt, nsteps)
+
+    def substep(self, s, dt):
+        gbfd_substep(self.ctx, s, dt)
+
+    def diagnostics(self):
+        return gbfd_diagnostics(self.ctx).as_dict()
+
+    def cfl_dt(self, cfl=0.4, cnu=0.25):
+        return gbfd_cfl_dt(self.ctx, cfl, cnu)
+
+    def sync(self):
+        gbfd_sync(self.ctx)
+
+    def launches(self):
+        return gbfd_launch_count(self.ctx)

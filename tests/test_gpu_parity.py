@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (stated by the task's numerical contract):
+  FP64  - per-field relative L2 ||g - o|| / ||o|| <= 1e-12 after the
+          configured steps (absolute 1e-14 where the oracle field is 0);
+  FP32  - one step from the oracle state rounded to FP32, against one FP64
+          oracle step from the same rounded state: relative L2 <= 1e-5 per
+          field;
+  FP32 stencil + FP64 accumulators: same 1e-5 bar.
+"""
+import numpy as np
+import pytest
+
+from oracle import fd
+from paper_1707_08900_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1707_08900_gb300 import build
+    build.build()
+
+
+def _solver(shape, **kw):
+    from paper_1707_08900_gb300 import gbfd
+    return gbfd.Solver(shape, **kw)
+
+
+def rel_l2(got, ref, abs_floor=1e-14):
+    out = []
+    for g, o in zip(got, ref):
+        no = np.linalg.norm(o.ravel())
+        d = np.linalg.norm((g - o).ravel())
+        out.append(d / no if no > 0 else (0.0 if d <= abs_floor * np.sqrt(o.size) else np.inf))
+    return np.array(out)
+
+
+def _grid(shape, lengths=(2 * np.pi,) * 3):
+    nz, ny, nx = shape
+    return fd.Grid(nx, ny, nz, *lengths)
+
+
+PATHS = {"tiled": 0, "simple": 1}
+
+
+def _run_parallel(shape, st0, nsteps, precision="fp64", form="55p", entropy_mode=1, path="tiled",
+                  nu=5e-3, cs=1.0, lengths=(2 * np.pi,) * 3, cfl=0.4):
+    """Advance oracle and GPU side by side with the oracle's CFL dt per step."""
+    from paper_1707_08900_gb300 import gbfd
+    g = _grid(shape, lengths)
+    ph = fd.Physics(cs=cs, nu=nu, entropy_mode=entropy_mode)
+    s = _solver(shape, precision=precision, form=form, entropy_mode=entropy_mode, nu=nu, cs=cs,
+                lengths=lengths)
+    s.set_option(gbfd.GBFD_OPT_KERNEL_PATH, PATHS[path])
+    s.set_state(st0)
+    ref = st0.copy()
+    ofm = fd.FORM_55P if form == "55p" else fd.FORM_19P
+    for _ in range(nsteps):
+        dt = fd.cfl_dt(ref, g, ph, cfl)
+        ref = fd.rk3_step(ref, dt, g, ph, ofm, nsteps=1)
+        s.rk3_step(dt, 1)
+    s.sync()
+    got = s.get_state()
+    s.close()
+    return got, ref
+
+
+@pytest.mark.parametrize("path", ["tiled", "simple"])
+def test_config1_fp64_55p_ten_steps(path):
+    """32^3, c_s = 1, nu = 5e-3, sine-mode IC seed 0, 10 steps at CFL 0.4."""
+    shape = (32, 32, 32)
+    st0 = inputs.sine_modes(shape, 0)
+    got, ref = _run_parallel(shape, st0, 10, path=path)
+    err = rel_l2(got, ref)
+    assert np.all(err <= FP64_TOL), err
+
+
+@pytest.mark.parametrize("form", ["55p", "19p"])
+@pytest.mark.parametrize("entropy_mode", [0, 1])
+@pytest.mark.parametrize("path", ["tiled", "simple"])
+def test_fp64_ragged_grid(form, entropy_mode, path):
+    """36 x 44 x 20 with unequal box lengths: partial tiles in x and y, a
+    partial z-chunk, and the periodic ghosts on every face."""
+    shape = (20, 44, 36)
+    lengths = (3.0, 4.5, 2.5)
+    st0 = inputs.random_state(shape, 7, scale=0.02, nfields=5 if entropy_mode else 4)
+    st0 += inputs.sine_modes(shape, 3, lengths=lengths, nfields=st0.shape[0])
+    got, ref = _run_parallel(shape, st0, 2, form=form, entropy_mode=entropy_mode, path=path,
+                             nu=0.02, lengths=lengths)
+    err = rel_l2(got, ref)
+    assert np.all(err <= FP64_TOL), err
+
+
+def _fp32_one_step(shape, st64, precision, form, path="tiled", nu=5e-3, dt=None):
+    from paper_1707_08900_gb300 import gbfd
+    g = _grid(shape)
+    ph = fd.Physics(cs=1.0, nu=nu, entropy_mode=1)
+    st32 = st64.astype(np.float32)
+    base = st32.astype(np.float64)
+    dt = dt or fd.cfl_dt(base, g, ph, 0.4)
+    ref = fd.rk3_step(base, dt, g, ph, fd.FORM_55P if form == "55p" else fd.FORM_19P)
+    s = _solver(shape, precision=precision, form=form, nu=nu)
+    s.set_option(gbfd.GBFD_OPT_KERNEL_PATH, PATHS[path])
+    s.set_state(st32)
+    s.rk3_step(dt, 1)
+    s.sync()
+    got = s.get_state()
+    s.close()
+    return rel_l2(got, ref), got, ref
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_acc64", "fp32_acc64_w64"])
+@pytest.mark.parametrize("form", ["55p", "19p"])
+def test_fp32_one_step_within_1e5(precision, form):
+    shape = (48, 40, 64)
+    st = inputs.spectrum(shape, 1, p=-2.0, k1=1, k2=8, mach=0.1, lnrho_rms=1e-3)
+    err, _, _ = _fp32_one_step(shape, st, precision, form)
+    assert np.all(err <= FP32_TOL), err
+
+
+@pytest.mark.parametrize("path", ["tiled", "simple"])
+def test_substeps_individually(path):
+    """Each substep (alpha_1 = 0 first, then the w-carrying ones) matches."""
+    from paper_1707_08900_gb300 import gbfd
+    shape = (24, 16, 32)
+    g = _grid(shape)
+    ph = fd.Physics(cs=1.0, nu=0.01, entropy_mode=1)
+    st = inputs.sine_modes(shape, 5, u_amp=0.05)
+    s = _solver(shape, precision="fp64", nu=0.01)
+    s.set_option(gbfd.GBFD_OPT_KERNEL_PATH, PATHS[path])
+    s.set_state(st)
+    w = np.zeros_like(st)
+    ref = st
+    for sub in range(3):
+        ref, w = fd.substep(ref, w, sub, 0.03, g, ph)
+        s.substep(sub, 0.03)
+        got = s.get_state()
+        assert np.all(rel_l2(got, ref) <= FP64_TOL)
+    s.close()
+
+
+def test_diagnostics_match_oracle():
+    shape = (32, 24, 40)
+    g = _grid(shape)
+    ph = fd.Physics(cs=1.0, nu=5e-3, entropy_mode=1)
+    st = inputs.spectrum(shape, 4, mach=0.3, lnrho_rms=0.05)
+    st[4] = 0.1 * st[1]
+    s = _solver(shape, precision="fp64")
+    s.set_state(st)
+    d = s.diagnostics()
+    o = fd.diagnostics(st, g, ph)
+    for k in ("mass", "ekin", "umax", "urms"):
+        assert d[k] == pytest.approx(o[k], rel=1e-12), k
+    np.testing.assert_allclose(d["rms"], o["rms"], rtol=1e-12)
+    np.testing.assert_allclose(d["maxabs"], o["maxabs"], rtol=0)
+    assert d["nonfinite"] == 0
+    assert s.cfl_dt(0.4) == pytest.approx(fd.cfl_dt(st, g, ph, 0.4), rel=1e-14)
+    st[2, 3, 4, 5] = np.nan
+    s.set_state(st)
+    assert s.diagnostics()["nonfinite"] == 1
+    s.close()
+
+
+def test_roll_equivariance_bitwise_fp32():
+    """Rolling the input rolls the output bit for bit: every point runs the
+    same arithmetic whatever tile, chunk or periodic edge it falls in."""
+    shape = (40, 48, 64)
+    st = inputs.spectrum(shape, 8, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
+    outs = []
+    for roll in ((0, 0, 0), (5, -9, 13)):
+        s = _solver(shape, precision="fp32", nu=5e-3)
+        s.set_state(np.roll(st, roll, axis=(1, 2, 3)))
+        s.rk3_step(0.01, 2)
+        outs.append(np.roll(s.get_state(fp64=False), [-r for r in roll], axis=(1, 2, 3)))
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_every_tile_config_agrees():
+    from paper_1707_08900_gb300 import gbfd
+    from paper_1707_08900_gb300 import build  # noqa: F401
+    shape = (40, 36, 68)
+    st = inputs.spectrum(shape, 9, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
+    base = None
+    for cfg in range(16):
+        s = _solver(shape, precision="fp32", nu=5e-3)
+        try:
+            s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
+        except gbfd.GbfdError:
+            s.close()
+            break
+        s.set_state(st)
+        s.rk3_step(0.01, 1)
+        out = s.get_state(fp64=False)
+        s.close()
+        if base is None:
+            base = out
+        else:
+            np.testing.assert_allclose(out, base, rtol=0, atol=1e-6 * np.abs(base).max())
+    assert base is not None
+
+
+def test_state_roundtrip_and_bad_args():
+    from paper_1707_08900_gb300 import gbfd
+    shape = (16, 16, 16)
+    st = inputs.random_state(shape, 1)
+    s = _solver(shape, precision="fp64")
+    s.set_state(st)
+    assert np.array_equal(s.get_state(), st)
+    dev = torch.from_numpy(st).cuda()
+    s.set_state(dev)
+    out = torch.empty_like(dev)
+    s.get_state(out=out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, dev)
+    with pytest.raises(gbfd.GbfdError):
+        s.rk3_step(-1.0, 1)
+    with pytest.raises(gbfd.GbfdError):
+        s.rk3_step(float("inf"), 1)
+    with pytest.raises(gbfd.GbfdError):
+        s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, 999)
+    s.close()
+    s32 = _solver(shape, precision="fp32")
+    s32.set_state(st)
+    assert np.array_equal(s32.get_state(fp64=False), st.astype(np.float32))
+    s32.close()
+
+
+def _window(a, lo, n):
+    """Periodic cut a[..., lo:lo+n] along the three grid axes."""
+    idx = [np.arange(l, l + n) % s for l, s in zip(lo, a.shape[1:])]
+    return a[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+
+
+@pytest.mark.parametrize("n,precision", [(256, "fp32"), (256, "fp64")])
+def test_full_size_window_against_oracle(n, precision):
+    """256^3 (the benchmark grid): one GPU step, checked on a 40^3 window by
+    advancing the oracle on the window plus a 9-cell halo (3 substeps x
+    radius 3; the halo absorbs the window's artificial periodic seams)."""
+    shape = (n, n, n)
+    st = inputs.spectrum(shape, 1, p=-2.0, k1=1, k2=8, mach=0.1, lnrho_rms=1e-3)
+    if precision == "fp32":
+        st = st.astype(np.float32).astype(np.float64)
+    dt = 0.4 * (2 * np.pi / n) / (1.0 + 0.5)
+    s = _solver(shape, precision=precision, nu=5e-3)
+    s.set_state(st)
+    s.rk3_step(dt, 1)
+    got = s.get_state()
+    s.close()
+    m, h = 40, 9
+    h_ = 2 * np.pi / n
+    for lo in ((0, 0, 0), (n - 20, 100, n - 7)):
+        win = _window(st, [l - h for l in lo], m + 2 * h)
+        g = fd.Grid(m + 2 * h, m + 2 * h, m + 2 * h, *(h_ * (m + 2 * h),) * 3)
+        ref = fd.rk3_step(win, dt, g, fd.Physics(cs=1.0, nu=5e-3, entropy_mode=1))
+        ref = ref[:, h:h + m, h:h + m, h:h + m]
+        gw = _window(got, lo, m)
+        err = rel_l2(gw, ref)
+        tol = FP64_TOL if precision == "fp64" else FP32_TOL
+        assert np.all(err <= tol), (lo, err)
