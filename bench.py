@@ -1,0 +1,452 @@
+"""Benchmark: RK3 grid-point updates per second on a 256^3 periodic box.
+
+One benchmark step = one full RK3 step (three fused 55-point substeps,
+Algorithm 2) of a 256^3 box, FP32 (the headline), on synthetic input of the
+paper's kind: velocity with a k^-2 spectrum over 1 <= k <= 8 at rms Mach 0.1,
+lnrho perturbation 1e-3, entropy 0 (seed 1 + rank).  The same line carries
+the FP64 and 19-point forms, the precision form, an end-to-end number
+through the public API with host buffers, the roofline of the dominant
+kernel and the CPU oracle timed on the host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank steps its own independent box (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 256
+SHAPE = (N, N, N)
+NF = 5
+METRIC = "RK3 grid-point updates/s (FP32 vs FP64) and fraction of HBM roofline"
+UNIT = "updates/s"
+WORKLOAD = ("256^3 periodic box, c_s=1, nu=5e-3, k^-2 velocity spectrum 1<=k<=8 at rms Mach 0.1 "
+            "(seed 1+rank), lnrho 1e-3, entropy 0; one step = one RK3 step (3 substeps), dt from CFL 0.4")
+# Algorithmic HBM bytes per point per RK3 step, 55-point form, F fields of w
+# bytes: substep 1 reads u and writes u_out, w (alpha_1 = 0: w not read);
+# substep 2 reads u, w, writes u_out, w; substep 3 reads u, w, writes u_out
+# (w is dead afterwards): 10 F w.
+ALG_BYTES_55 = {4: 10 * NF * 4, 8: 10 * NF * 8}
+# 19-point form (Algorithm 3): per substep pass 1 reads u (F) [+ w], writes
+# u_out (F), w, div (1); pass 2 reads div, u_out (3) [+ w (3)], writes u_out
+# (3) [+ w (3)]; w neither read in substep 1 nor written in substep 3:
+# (16 + 13) + (21 + 13) + (16 + 7) = 86 values.
+ALG_VALUES_19 = 86
+# Algorithmic flops per point per substep of the 55-point right-hand side and
+# update as written in stencil.cuh / common.cuh (FMA = 2): 15 first
+# derivatives x 8, 9 second derivatives x 10, 6 bidiagonal mixed x 14,
+# Laplacian and grad-div sums 12, physics of Eqs. 1-3 with passive entropy 87,
+# Eq. 10 update 5 fields x 5 = 418.
+FLOPS_55_SUBSTEP = 418
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), nominal
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    return 6800.0, "fallback", {}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1707_08900_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    summary is missing or was taken on different kernel sources."""
+    sha = kernel_source_sha()
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
+        kv = {}
+        for line in open(f):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("bench_key") == kernel_key and kv.get("source_sha") == sha:
+            try:
+                return float(kv["dram_bytes_per_launch_scaled"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.5)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t0, t1):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [l for (t, l) in self.lines if t0 - 0.15 <= t <= t1 + 0.15]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid_for(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+# ------------------------------------------------------------------ our arm
+
+def timed_steps(s, dt, steps, stream, torch):
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    l0 = s.launches()
+    ev0.record(stream)
+    s.rk3_step(dt, steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1), s.launches() - l0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1707_08900_gb300 import build as gb
+    from paper_1707_08900_gb300 import gbfd, inputs
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        gb.build()
+    if world > 1:
+        dist.barrier()
+    gbfd.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream(dev)
+    peak_gbs, peak_kind, peaks = measured_peaks()
+    st0 = inputs.spectrum(SHAPE, 1 + rank, p=-2.0, k1=1, k2=8, mach=0.1, lnrho_rms=1e-3)
+    st0_32 = st0.astype(np.float32)
+    npts = N ** 3
+
+    def make(precision, form):
+        s = gbfd.Solver(SHAPE, precision=precision, form=form, entropy_mode=1, nu=5e-3, cs=1.0,
+                        device=dev, stream=stream)
+        s.set_state(st0_32 if precision != "fp64" else st0)
+        return s
+
+    # ---- headline: FP32, 55-point, fused single pass
+    s = make("fp32", "55p")
+    dt = s.cfl_dt(0.4)
+    s.rk3_step(dt, args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_uuid_for(local))
+    if rank == 0:
+        sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ms, launches = timed_steps(s, dt, args.steps, stream, torch)
+    t1 = time.time()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop(t0, t1) if rank == 0 else None
+    ms_max = max_over_ranks(ms)
+    value = world * npts * args.steps / (ms_max * 1e-3)
+    avg_launch_s = ms * 1e-3 / launches
+    alg_per_launch = npts * ALG_BYTES_55[4] / 3.0
+    achieved = alg_per_launch / avg_launch_s / 1e9
+    traffic = profile_traffic("substep55_fp32_tiled_256")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
+                "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "kernel": "k_substep_tiled<float,5,55p> (3 launches per step)",
+                "alg_bytes_per_launch": alg_per_launch,
+                "frac_of_8TBs_nominal": round(achieved / 8000.0, 4)}
+    s.close()
+
+    extra = {}
+    # ---- FP64, 55-point (FP64-ALU bound on GB300)
+    k64 = max(3, args.steps // 20)
+    s = make("fp64", "55p")
+    s.rk3_step(dt, 2)
+    torch.cuda.synchronize()
+    ms64, l64 = timed_steps(s, dt, k64, stream, torch)
+    v64 = npts * k64 / (max_over_ranks(ms64) * 1e-3)  # per GPU
+    tflops64 = v64 * 3 * FLOPS_55_SUBSTEP / 1e12
+    extra["fp64_55p"] = {
+        "value": world * v64, "steps": k64, "ms_per_step": ms64 / k64,
+        "roofline": {"bound": "alu", "achieved": round(tflops64, 3), "peak": FP64_NOMINAL_TFLOPS,
+                     "unit": "TFLOP/s", "frac": round(tflops64 / FP64_NOMINAL_TFLOPS, 4),
+                     "peak_kind": "nominal GB300 FP64 (non-tensor)",
+                     "flops_per_update": 3 * FLOPS_55_SUBSTEP},
+        "hbm_frac": round(npts * ALG_BYTES_55[8] / (ms64 / k64 * 1e-3) / 1e9 / peak_gbs, 4),
+    }
+    s.close()
+    extra["fp32_vs_fp64_speedup"] = round(value / world / v64, 2)
+
+    # ---- FP32, 19-point two-pass form
+    k19 = max(3, args.steps // 4)
+    s = make("fp32", "19p")
+    s.rk3_step(dt, 2)
+    torch.cuda.synchronize()
+    ms19, l19 = timed_steps(s, dt, k19, stream, torch)
+    v19 = npts * k19 / (max_over_ranks(ms19) * 1e-3)
+    extra["fp32_19p"] = {
+        "value": world * v19, "steps": k19, "ms_per_step": ms19 / k19,
+        "hbm_frac_own_ideal": round(npts * ALG_VALUES_19 * 4 / (ms19 / k19 * 1e-3) / 1e9
+                                    / peak_gbs, 4),
+        "hbm_frac_55p_ideal": round(npts * ALG_BYTES_55[4] / (ms19 / k19 * 1e-3) / 1e9
+                                    / peak_gbs, 4),
+    }
+    s.close()
+
+    # ---- precision form: FP32 stencil, FP64 RK3 registers
+    kacc = max(3, args.steps // 4)
+    s = make("fp32_acc64", "55p")
+    s.rk3_step(dt, 2)
+    torch.cuda.synchronize()
+    msa, _ = timed_steps(s, dt, kacc, stream, torch)
+    extra["fp32_acc64_55p"] = {"value": world * npts * kacc / (max_over_ranks(msa) * 1e-3),
+                               "steps": kacc, "ms_per_step": msa / kacc}
+    s.close()
+
+    # ---- end to end through the public API with pinned host buffers:
+    # every step copies the state in (H2D), advances one RK3 step and reads
+    # the new state back (D2H)
+    s = make("fp32", "55p")
+    host_in = torch.from_numpy(st0_32).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ke = max(3, min(args.steps, 50))
+    for _ in range(2):
+        s.set_state(host_in)
+        s.rk3_step(dt, 1)
+        s.get_state(out=host_out)
+    barrier()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(ke):
+        gbfd.gbfd_set_state(s.ctx, host_in.data_ptr(), 0, 0)
+        gbfd.gbfd_rk3_step(s.ctx, dt, 1)
+        gbfd.gbfd_get_state(s.ctx, host_out.data_ptr(), 0, 0)  # synchronises
+    te = time.perf_counter() - te0
+    te = max_over_ranks(te)
+    state_bytes = host_in.numel() * host_in.element_size()
+    e2e = {"value": world * npts * ke / te, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes, "steps": ke,
+           "what": "per step: gbfd_set_state from pinned host FP32, gbfd_rk3_step(dt,1), "
+                   "gbfd_get_state to pinned host FP32"}
+    s.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(target_s=args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "256^3", "form": "55-point fused",
+                   "precision": "fp32", "fields": NF, "tile": "default (32x8, zc 32)",
+                   "l2": "inputs larger than L2: 3 x 335 MB padded FP32 state buffers",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "forms": extra,
+        "impl": "ours",
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def _oracle_sample(nyz, threads):
+    from oracle import fd
+    from paper_1707_08900_gb300 import inputs
+    ny, nz = nyz
+    fd.set_threads(threads)
+    shape = (nz, ny, N)
+    st = inputs.spectrum(shape, 1, p=-2.0, k1=1, k2=8, mach=0.1, lnrho_rms=1e-3)
+    h = 2 * np.pi / N
+    g = fd.Grid(N, ny, nz, 2 * np.pi, h * ny, h * nz)
+    ph = fd.Physics(cs=1.0, nu=5e-3, entropy_mode=1)
+    return fd, st, g, ph
+
+
+def cpu_baseline(target_s=15.0):
+    """The FP64 C oracle as it stands, OpenMP over z on all host cores: RK3
+    steps on a 256 x ny x nz slab of the workload (periodic), sized to run
+    for about target_s seconds."""
+    threads = os.cpu_count() or 1
+    fd, st, g, ph = _oracle_sample((64, 16), threads)
+    t = time.perf_counter()
+    fd.rk3_step(st, 1e-3, g, ph)
+    per_pt = (time.perf_counter() - t) / (N * 64 * 16)
+    nz = int(np.clip(target_s / (per_pt * N * N), 8, 256))
+    fd, st, g, ph = _oracle_sample((N, nz), threads)
+    t = time.perf_counter()
+    fd.rk3_step(st, 1e-3, g, ph)
+    el = time.perf_counter() - t
+    return {"value": N * N * nz / el, "unit": UNIT, "cores": fd.set_threads(0), "kind": "oracle",
+            "sample": f"one FP64 RK3 step (55-point) of a 256x256x{nz} slab of the workload, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores, one bounded sample
+    of the workload per step."""
+    if int(os.environ.get("RANK", 0)) != 0:
+        return
+    from oracle import build_oracle
+    build_oracle.build()
+    threads = os.cpu_count() or 1
+    fd, st, g, ph = _oracle_sample((64, 8), threads)
+    t = time.perf_counter()
+    fd.rk3_step(st, 1e-3, g, ph)
+    per_pt = (time.perf_counter() - t) / (N * 64 * 8)
+    budget = 150.0 / (args.steps + args.warmup)  # whole run within a few minutes
+    ny = int(np.clip(budget / (per_pt * N * 8), 8, 256))
+    fd, st, g, ph = _oracle_sample((ny, 8), threads)
+    for _ in range(args.warmup):
+        fd.rk3_step(st, 1e-3, g, ph)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        fd.rk3_step(st, 1e-3, g, ph)
+    el = time.perf_counter() - t
+    pts = N * ny * 8
+    value = pts * args.steps / el
+    sample = f"each step: one FP64 RK3 step (55-point) of a 256x{ny}x8 periodic slab of the workload"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", 1)),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "256^3 (sampled)", "form": "55-point",
+                   "precision": "fp64 oracle"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": fd.set_threads(0), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

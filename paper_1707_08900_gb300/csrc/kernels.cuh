@@ -10,6 +10,8 @@ struct RKStage {
     double alpha, beta, dt;
     double nu3;  // nu / 3, used by the second pass of the 19-point form
     int first;   // substep 1: alpha_1 = 0, the old w is not read
+    int last;    // substep 3: w is dead afterwards (the next step's substep 1
+                 // ignores it), so it is not written
     int s;       // 0, 1, 2
 };
 
@@ -21,6 +23,7 @@ inline RKStage make_stage(int s, double dt, double nu)
     st.dt = dt;
     st.nu3 = nu / 3.0;
     st.first = (s == 0);
+    st.last = (s == 2);
     st.s = s;
     return st;
 }

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(128) k_substep_simple(const TS *__restrict__ i
         TW wv = st.first ? (TW)0 : w[iw];
         TS o;
         rk3_update<TA, TW, TS>(st.first, alpha, beta, dt, (TA)r[f], A(f, 0, 0, 0), wv, o);
-        w[iw] = wv;
+        if (!st.last)
+            w[iw] = wv;
         store_ghosted(out, Ls, f, z, y, x, o);
     }
 }
@@ -96,7 +97,8 @@ __global__ void __launch_bounds__(128) k_pass2_simple(const TS *__restrict__ div
         const TA g = (TA)d1_axis(A, 0, i, c);
         const long long iw = lidx(Lw, 1 + i, z, y, x);
         const long long io = lidx(Ls, 1 + i, z, y, x);
-        w[iw] = (TW)((TA)w[iw] + dt * nu3 * g);
+        if (!st.last)
+            w[iw] = (TW)((TA)w[iw] + dt * nu3 * g);
         store_ghosted(out, Ls, 1 + i, z, y, x, (TS)((TA)out[io] + beta * dt * nu3 * g));
     }
 }

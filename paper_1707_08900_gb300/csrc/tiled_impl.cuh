@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(TX *TY) k_substep_tiled(
             for (int f = 0; f < NF; ++f) {
                 TS ov;
                 rk3_update<TA, TW, TS>(st.first, alpha, beta, dt, (TA)r[f], A.col[f][3], wv[f], ov);
-                w[lidx(Lw, f, z, y, x)] = wv[f];
+                if (!st.last)
+                    w[lidx(Lw, f, z, y, x)] = wv[f];
                 store_ghosted(out, Ls, f, z, y, x, ov);
             }
         }
