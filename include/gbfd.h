@@ -143,6 +143,29 @@ gbfd_status gbfd_cfl_dt(gbfd_ctx *ctx, double cfl, double cnu, double *dt_out);
  * (bounded waits that gave up -> TIMEOUT; CUDA errors -> CUDA). */
 gbfd_status gbfd_sync(gbfd_ctx *ctx);
 
+/* Diagnostics for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is an interface convenience.  It computes the
+ * same FP64 reductions as gbfd_diagnostics, but needs no context and no
+ * workspace: the caller passes a device state array (nfields arrays
+ * [nz][ny][nx], FP64 if state_is_fp64 else FP32, the gbfd_set_state layout)
+ * and a device buffer `out` of 16 doubles, filled asynchronously on `stream`
+ * with mass, ekin, umax, urms, rms[5], maxabs[5], nonfinite (as 0.0/1.0), 0.
+ * It is meant for code that may not call cudaMalloc (for example inside a
+ * host callback or a stream-ordered section, where the implicit device
+ * synchronisation of cudaMalloc/cudaFree would stall or deadlock, or inside a
+ * framework whose allocator does not allow it).  It calls no allocating
+ * routine: its partial sums live in a fixed file-scope device array of 1216 x
+ * 16 doubles (155,648 bytes) that every GPU loading the library holds until
+ * the process exits.  The array's device address is looked up on the first
+ * call on each device (with that device current); make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU race and must be ordered (same stream, or events).
+ * Limits: nfields 4 or 5; extents >= 1, nx*ny*nz <= 2^33; box lengths > 0.
+ * Errors: INVALID_ARG (with gbfd_last_error(NULL)), CUDA. */
+gbfd_status gbfd_diagnostics_noalloc(const void *state, int state_is_fp64, int nx, int ny, int nz,
+                                     int nfields, double lx, double ly, double lz, void *stream,
+                                     double *out);
+
 /* Tuning options (no counterpart in the paper; used by the tests and the
  * autotuner).  GBFD_OPT_KERNEL_PATH: 0 = tiled kernels (TMA-staged shared
  * memory, the default), 1 = simple one-thread-per-point kernels reading

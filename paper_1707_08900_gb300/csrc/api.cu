@@ -220,6 +220,11 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
 
 }  // namespace
 
+namespace gbfd {
+// Record a failure of a context-free entry point; read by gbfd_last_error(NULL).
+void set_global_error(const char *msg) { set_err(nullptr, "%s", msg); }
+}  // namespace gbfd
+
 extern "C" {
 
 size_t gbfd_workspace_bytes(const gbfd_params *p)

@@ -30,7 +30,7 @@ FORMS = {"55p": GBFD_55P, "19p": GBFD_19P}
 EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state",
            "gbfd_get_state", "gbfd_rk3_step", "gbfd_substep", "gbfd_diagnostics", "gbfd_cfl_dt",
            "gbfd_sync", "gbfd_set_option", "gbfd_launch_count", "gbfd_last_error",
-           "gbfd_status_string")
+           "gbfd_status_string", "gbfd_diagnostics_noalloc")
 
 
 class GbfdError(RuntimeError):
@@ -94,6 +94,9 @@ def load(path=None):
     L.gbfd_launch_count.argtypes = [_VP]
     L.gbfd_last_error.restype = ctypes.c_char_p
     L.gbfd_last_error.argtypes = [_VP]
+    L.gbfd_diagnostics_noalloc.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, _VP, _VP]
     L.gbfd_status_string.restype = ctypes.c_char_p
     L.gbfd_status_string.argtypes = [ctypes.c_int]
     for name in EXPORTS:
@@ -163,6 +166,14 @@ def gbfd_set_option(ctx, key, value):
 
 def gbfd_launch_count(ctx):
     return load().gbfd_launch_count(ctx)
+
+
+def gbfd_diagnostics_noalloc(state_ptr, state_is_fp64, nx, ny, nz, nfields, lx, ly, lz,
+                             stream_ptr, out_ptr):
+    """Diagnostics of a device state array into a device buffer of 16 doubles,
+    without a context, a workspace or any allocation (see include/gbfd.h)."""
+    _check(load().gbfd_diagnostics_noalloc(_VP(state_ptr), int(state_is_fp64), nx, ny, nz,
+                                           nfields, lx, ly, lz, _VP(stream_ptr), _VP(out_ptr)))
 
 
 def gbfd_last_error(ctx=None):
