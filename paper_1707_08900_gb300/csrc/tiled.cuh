@@ -13,11 +13,16 @@ struct TileConfig {
     int tx, ty;  // xy tile (threads per CTA = tx * ty, one point each per plane)
     int zc;      // planes streamed per CTA
     int ns;      // plane slots in the shared-memory ring
+    int px;      // points per thread along x (1, or 2 with paired loads)
 };
 
 // Number of z-chunk lengths offered per (tx, ty, ns) variant; table index
 // i is variant i / kZcChoices with the (i % kZcChoices)-th chunk length.
 constexpr int kZcChoices = 4;
+
+// Default FP32 table entry: variant 4 (32 x 8, two points per thread) with
+// the first z-chunk length.
+constexpr int kDefaultF32 = 4 * kZcChoices;
 
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);
@@ -25,13 +30,14 @@ TileConfig tiled_config(int sbytes, int i);
 
 // Encoded TMA descriptors of the state buffers, cached per context.
 struct TmapCache {
+    static constexpr int kEntries = 16;
     struct Entry {
         const void *base;
         int cfg;
         int nf;
         bool valid;
         CUtensorMap map;
-    } e[8];
+    } e[kEntries];
     int next;
 };
 

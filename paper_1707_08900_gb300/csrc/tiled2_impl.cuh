@@ -1,0 +1,527 @@
+// Tiled fused substep, two points per thread (x, x+1): the same TMA plane
+// ring and z-register sliding as tiled_impl.cuh, but every shared-memory
+// read fetches an aligned pair (float2 / double2), so one load serves both
+// points' stencil arms and the per-point index/loop overhead is halved.
+//
+// The right-hand side of Eqs. 1-3 is accumulated field by field so that only
+// the running sums stay live:
+//   grad lnrho first; then for each velocity component u_i with gradient g:
+//     rhs_i += -u.g + nu (lap u_i + g.grad lnrho) + (nu/3) D2_i u_i
+//     rhs_j += nu g_j d_i lnrho                  (the d_i u_j d_j lnrho half of
+//                                                  2 S.grad lnrho, for all j)
+//     rhs_j += (nu/3) D_ij u_i  (j != i, 55-point grad div, Eq. 8)
+//     div   += g_i
+//   finally rhs_i += -c_s^2 d_i lnrho - (2/3) nu div d_i lnrho,
+//   rhs_lnrho = -u.grad lnrho - div, rhs_s = -u.grad s.
+// This is Eq. 2 with 2 (S.grad lnrho)_i written out from Eq. 3.
+#pragma once
+
+#include "tiled_impl.cuh"
+
+namespace gbfd {
+namespace tiled2 {
+
+template <class T>
+struct V2;
+template <>
+struct V2<float> {
+    using t = float2;
+};
+template <>
+struct V2<double> {
+    using t = double2;
+};
+
+// Values of one field along x in one row: e[i] = f(x - 4 + i), i = 0..9,
+// filled only where loaded.
+template <class T>
+struct Row {
+    T e[10];
+};
+
+template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS>
+__global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
+    const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
+    TS *__restrict__ out, TW *__restrict__ w,
+    TS *__restrict__ divf, const Layout Ls, const Layout Lw, const Coef<TS> c, const RKStage st,
+    const int zc, const int tiles_x, int *__restrict__ dev_error)
+{
+    using tiled::mbar_wait;
+    using V = typename V2<TS>::t;
+    constexpr int BX = TX + 2 * GX;
+    constexpr int BY = TY + 2 * GY;
+    constexpr int FSTRIDE = BX * BY;
+    constexpr int SLOT_BYTES = NF * FSTRIDE * (int)sizeof(TS);
+    constexpr int SLOT_PITCH = (SLOT_BYTES + 127) / 128 * 128;
+    constexpr int SLOT_ELEMS = SLOT_PITCH / (int)sizeof(TS);
+    constexpr int NTX = TX / 2;
+    // u-tilde ring: NW slots of the tile (no halo), TMA-loaded two planes ahead
+    constexpr int NW = 3;
+    constexpr int WSLOT_BYTES = NF * TX * TY * (int)sizeof(TW);
+    constexpr int WSLOT_PITCH = (WSLOT_BYTES + 127) / 128 * 128;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const TS *sm = reinterpret_cast<const TS *>(smem);
+    unsigned char *wsm = smem + NS * SLOT_PITCH;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + NW * WSLOT_PITCH);
+    uint64_t *wbars = bars + NS;
+
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    const int x0 = (blockIdx.x % tiles_x) * TX;
+    const int y0 = (blockIdx.x / tiles_x) * TY;
+    const int z0 = blockIdx.y * zc;
+    const int nz = Ls.nz;
+    const int nout = min(zc, nz - z0);
+    const int nplanes = nout + 2 * R;
+    const int x = x0 + 2 * tx, y = y0 + ty;
+    const bool valid0 = (x < Ls.nx) && (y < Ls.ny);  // nx % 4 == 0: x+1 valid with x
+    // element offset of point (x, y) in a field of a slot; even, so pairs align
+    const int toff = (ty + GY) * BX + (2 * tx + GX);
+
+    if (threadIdx.x == 0) {
+#pragma unroll 1
+        for (int i = 0; i < NS + NW; ++i)
+            tiled::mbar_init(&bars[i], 1);
+        tiled::fence_mbar_init();
+    }
+    __syncthreads();
+
+    // u-tilde of output plane o (grid plane z0 + o) goes to w-slot o % NW
+    const bool need_w = !st.first;
+    int wissued = 0;
+    auto issue_w = [&](int o) {
+        const int slot = o % NW;
+        tiled::mbar_expect_tx(&wbars[slot], WSLOT_BYTES);
+        tiled::tma_load_4d(wsm + slot * WSLOT_PITCH, &wmap, &wbars[slot], x0 + GX, y0 + GY,
+                           z0 + o, 0);
+    };
+    if (threadIdx.x == 0 && need_w) {
+        for (int o = 0; o < NW - 1 && o < nout; ++o)
+            issue_w(o);
+        wissued = min(NW - 1, nout);
+    }
+
+    int issued = 0;
+    auto issue = [&](int j) {
+        int z = z0 - R + j;
+        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        const int slot = j % NS;
+        tiled::mbar_expect_tx(&bars[slot], SLOT_BYTES);
+        tiled::tma_load_4d(smem + slot * SLOT_PITCH, &tmap, &bars[slot], x0, y0, z, 0);
+    };
+    if (threadIdx.x == 0) {
+#pragma unroll 1
+        for (int j = 0; j < NS - 1 && j < nplanes; ++j)
+            issue(j);
+        issued = min(NS - 1, nplanes);
+    }
+
+    // z-column window of both points: col[f][k][j], planes o..o+6, point j
+    TS col[NF][7][2];
+    bool timeout = false;
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j) {
+        if (!mbar_wait(&bars[j % NS], (j / NS) & 1))
+            timeout = true;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const V v = *reinterpret_cast<const V *>(sm + (j % NS) * SLOT_ELEMS + f * FSTRIDE + toff);
+            col[f][j][0] = v.x;
+            col[f][j][1] = v.y;
+        }
+    }
+
+    // global offsets of point (x, y, z0): advanced by one plane per iteration
+    long long go_s = (long long)z0 * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+    long long go_w = (long long)z0 * Lw.plane + (long long)(y + GY) * Lw.P + (x + GX);
+    // periodic ghost copies this thread's points own (x even, nx % 4 == 0:
+    // both points share the x-ghost condition)
+    long long gdx = 0, gdy = 0;
+    if (x < GX)
+        gdx = Ls.nx;
+    else if (x >= Ls.nx - GX)
+        gdx = -Ls.nx;
+    if (y < GY)
+        gdy = (long long)Ls.ny * Ls.P;
+    else if (y >= Ls.ny - GY)
+        gdy = -(long long)Ls.ny * Ls.P;
+
+    const TA alpha = (TA)st.alpha, beta = (TA)st.beta, dt = (TA)st.dt;
+    int waited = 2 * R;
+    int slot0 = 0;  // slot of plane o
+#pragma unroll 1
+    for (int o = 0; o < nout; ++o) {
+        if (__syncthreads_or(timeout))
+            break;
+        if (threadIdx.x == 0) {
+            const int j = o + NS - 1;
+            tiled::fence_proxy_async();
+            if (j < nplanes) {
+                issue(j);
+                issued = j + 1;
+            }
+            if (need_w && o + NW - 1 < nout) {
+                issue_w(o + NW - 1);
+                wissued = o + NW;
+            }
+        }
+        const int jn = o + 2 * R;
+        if (!mbar_wait(&bars[jn % NS], (jn / NS) & 1))
+            timeout = true;
+        if (need_w && !mbar_wait(&wbars[o % NW], (o / NW) & 1))
+            timeout = true;
+        waited = jn + 1;
+        int so[7];  // element offsets of the 7 window planes' slots
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const int s = slot0 + k;
+            so[k] = (s >= NS ? s - NS : s) * SLOT_ELEMS + toff;
+        }
+        slot0 = slot0 + 1 == NS ? 0 : slot0 + 1;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const V v = *reinterpret_cast<const V *>(sm + so[6] + f * FSTRIDE);
+            col[f][6][0] = v.x;
+            col[f][6][1] = v.y;
+        }
+
+        // pair of field f at plane offset dz, row offset dy, x offset dx (even)
+        auto ld2 = [&](int f, int dz, int dy, int dx) -> V {
+            return *reinterpret_cast<const V *>(sm + so[dz + 3] + f * FSTRIDE + dy * BX + dx);
+        };
+        // the x row of field f at (dz, dy): pairs at -4, -2, 2, 4 (+ centre)
+        auto row = [&](int f, int dz, int dy, bool centre, bool outer) {
+            Row<TS> r;
+            V a;
+            if (outer) {
+                a = ld2(f, dz, dy, -4);
+                r.e[0] = a.x;
+                r.e[1] = a.y;
+            }
+            a = ld2(f, dz, dy, -2);
+            r.e[2] = a.x;
+            r.e[3] = a.y;
+            if (centre) {
+                a = ld2(f, dz, dy, 0);
+                r.e[4] = a.x;
+                r.e[5] = a.y;
+            }
+            a = ld2(f, dz, dy, 2);
+            r.e[6] = a.x;
+            r.e[7] = a.y;
+            if (outer) {
+                a = ld2(f, dz, dy, 4);
+                r.e[8] = a.x;
+                r.e[9] = a.y;
+            }
+            return r;
+        };
+
+        if (valid0) {
+            const int zo = z0 + o;
+            TW wv[NF][2];
+            if (need_w) {
+                const TW *ws = reinterpret_cast<const TW *>(wsm + (o % NW) * WSLOT_PITCH) +
+                               ty * TX + 2 * tx;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const typename V2<TW>::t t =
+                        *reinterpret_cast<const typename V2<TW>::t *>(ws + f * TX * TY);
+                    wv[f][0] = t.x;
+                    wv[f][1] = t.y;
+                }
+            }
+
+            // first derivatives along x, y, z of field f for both points, plus
+            // second derivatives when `second`; centre values from col[f][3]
+            TS g[2][3], d2[2][3];
+            auto axial = [&](int f, bool second) {
+                Row<TS> r0 = row(f, 0, 0, false, true);
+                r0.e[4] = col[f][3][0];
+                r0.e[5] = col[f][3][1];
+                V yp[3], ym[3];
+#pragma unroll
+                for (int k = 1; k <= 3; ++k) {
+                    yp[k - 1] = ld2(f, 0, k, 0);
+                    ym[k - 1] = ld2(f, 0, -k, 0);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const TS cc = col[f][3][j];
+                    TS ax = (TS)0, ay = (TS)0, az = (TS)0;
+                    TS bx = c.d2c[0] * cc, by = c.d2c[1] * cc, bz = c.d2c[2] * cc;
+#pragma unroll
+                    for (int k = 1; k <= 3; ++k) {
+                        const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
+                        const TS ypv = j ? yp[k - 1].y : yp[k - 1].x;
+                        const TS ymv = j ? ym[k - 1].y : ym[k - 1].x;
+                        const TS zp = col[f][3 + k][j], zm = col[f][3 - k][j];
+                        ax += c.d1[0][k - 1] * (xp - xm);
+                        ay += c.d1[1][k - 1] * (ypv - ymv);
+                        az += c.d1[2][k - 1] * (zp - zm);
+                        if (second) {
+                            bx += c.d2[0][k - 1] * (xp + xm);
+                            by += c.d2[1][k - 1] * (ypv + ymv);
+                            bz += c.d2[2][k - 1] * (zp + zm);
+                        }
+                    }
+                    g[j][0] = ax;
+                    g[j][1] = ay;
+                    g[j][2] = az;
+                    d2[j][0] = bx;
+                    d2[j][1] = by;
+                    d2[j][2] = bz;
+                }
+            };
+            // Eq. 8 in the (x, y) plane (dzsel = 0) or (x, z) plane: rows or
+            // planes at +-k, x offsets +-k, for both points
+            auto mix_x = [&](int f, bool in_y, TS *res) {
+                Row<TS> rp[3], rm[3];
+#pragma unroll
+                for (int k = 1; k <= 3; ++k) {
+                    const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
+                    rp[k - 1] = row(f, dz, dy, false, k == 3);
+                    rm[k - 1] = row(f, -dz, -dy, false, k == 3);
+                }
+                // k = 1 also needs the centre pair: x+1 for point 0, x for point 1
+                if (in_y) {
+                    V a = ld2(f, 0, 1, 0);
+                    rp[0].e[4] = a.x;
+                    rp[0].e[5] = a.y;
+                    a = ld2(f, 0, -1, 0);
+                    rm[0].e[4] = a.x;
+                    rm[0].e[5] = a.y;
+                } else {
+                    rp[0].e[4] = col[f][4][0];
+                    rp[0].e[5] = col[f][4][1];
+                    rm[0].e[4] = col[f][2][0];
+                    rm[0].e[5] = col[f][2][1];
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    TS a = (TS)0;
+#pragma unroll
+                    for (int k = 1; k <= 3; ++k) {
+                        const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
+                        const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
+                        a += c.mx[in_y ? 0 : 1][k - 1] * ((pp - mp) + (mm - pm));
+                    }
+                    res[j] = a;
+                }
+            };
+            // Eq. 8 in the (y, z) plane: pairs at (dz, dy) = (+-k, +-k)
+            auto mix_yz = [&](int f, TS *res) {
+                TS a0 = (TS)0, a1 = (TS)0;
+#pragma unroll
+                for (int k = 1; k <= 3; ++k) {
+                    const V pp = ld2(f, k, k, 0), mp = ld2(f, k, -k, 0);
+                    const V mm = ld2(f, -k, -k, 0), pm = ld2(f, -k, k, 0);
+                    a0 += c.mx[2][k - 1] * ((pp.x - mp.x) + (mm.x - pm.x));
+                    a1 += c.mx[2][k - 1] * ((pp.y - mp.y) + (mm.y - pm.y));
+                }
+                res[0] = a0;
+                res[1] = a1;
+            };
+
+            TS uc[2][3], gl[2][3], acc[2][4], dv[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    uc[j][i] = col[1 + i][3][j];
+                    acc[j][1 + i] = (TS)0;
+                }
+                dv[j] = (TS)0;
+            }
+            // grad lnrho
+            axial(0, false);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    gl[j][a] = g[j][a];
+            // velocity components
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                axial(1 + i, true);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const TS adv = uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2];
+                    const TS lap = d2[j][0] + d2[j][1] + d2[j][2];
+                    const TS sg = g[j][0] * gl[j][0] + g[j][1] * gl[j][1] + g[j][2] * gl[j][2];
+                    acc[j][1 + i] += c.nu * (lap + sg) - adv;
+                    if (MIXED)
+                        acc[j][1 + i] += c.nu3 * d2[j][i];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        acc[j][1 + a] += c.nu * g[j][a] * gl[j][i];
+                    dv[j] += g[j][i];
+                }
+                if (MIXED) {
+                    // D_ij u_i enters d_j (div u) for j != i
+                    TS m[2];
+                    if (i == 0) {
+                        mix_x(1, true, m);  // D_xy u_x -> y
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            acc[j][2] += c.nu3 * m[j];
+                        mix_x(1, false, m);  // D_xz u_x -> z
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            acc[j][3] += c.nu3 * m[j];
+                    } else if (i == 1) {
+                        mix_x(2, true, m);  // D_xy u_y -> x
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            acc[j][1] += c.nu3 * m[j];
+                        mix_yz(2, m);  // D_yz u_y -> z
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            acc[j][3] += c.nu3 * m[j];
+                    } else {
+                        mix_x(3, false, m);  // D_xz u_z -> x
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            acc[j][1] += c.nu3 * m[j];
+                        mix_yz(3, m);  // D_yz u_z -> y
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            acc[j][2] += c.nu3 * m[j];
+                    }
+                }
+            }
+            TS rs[2] = {(TS)0, (TS)0};
+            if (NF == 5) {
+                axial(4, false);
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    rs[j] = -(uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2]);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                acc[j][0] = -(uc[j][0] * gl[j][0] + uc[j][1] * gl[j][1] + uc[j][2] * gl[j][2]) - dv[j];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    acc[j][1 + a] += -c.cs2 * gl[j][a] - c.nu23 * dv[j] * gl[j][a];
+            }
+            if (!MIXED) {
+                typename V2<TS>::t dvv;
+                dvv.x = dv[0];
+                dvv.y = dv[1];
+                const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+                *reinterpret_cast<V *>(divf + gi) = dvv;
+                if (gdx)
+                    *reinterpret_cast<V *>(divf + gi + gdx) = dvv;
+                if (gdy) {
+                    *reinterpret_cast<V *>(divf + gi + gdy) = dvv;
+                    if (gdx)
+                        *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dvv;
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                TS ov[2];
+                TW wn[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const TS r = f < 4 ? acc[j][f] : rs[j];
+                    TW wo = st.first ? (TW)0 : wv[f][j];
+                    rk3_update<TA, TW, TS>(st.first, alpha, beta, dt, (TA)r, col[f][3][j], wo,
+                                           ov[j]);
+                    wn[j] = wo;
+                }
+                if (!st.last) {
+                    typename V2<TW>::t t;
+                    t.x = wn[0];
+                    t.y = wn[1];
+                    *reinterpret_cast<typename V2<TW>::t *>(w + f * Lw.fpitch + go_w) = t;
+                }
+                V o2;
+                o2.x = ov[0];
+                o2.y = ov[1];
+                TS *op = out + f * Ls.fpitch + go_s;
+                *reinterpret_cast<V *>(op) = o2;
+                if (gdx)
+                    *reinterpret_cast<V *>(op + gdx) = o2;
+                if (gdy) {
+                    *reinterpret_cast<V *>(op + gdy) = o2;
+                    if (gdx)
+                        *reinterpret_cast<V *>(op + gdy + gdx) = o2;
+                }
+            }
+        }
+        go_s += Ls.plane;
+        go_w += Lw.plane;
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                col[f][k][0] = col[f][k + 1][0];
+                col[f][k][1] = col[f][k + 1][1];
+            }
+    }
+    if (__syncthreads_or(timeout)) {
+        if (threadIdx.x == 0) {
+            atomicExch(dev_error, 1);
+            for (int j = waited; j < issued; ++j)
+                (void)mbar_wait(&bars[j % NS], (j / NS) & 1);
+            for (int o = 0; o < wissued; ++o)  // phases already complete return at once
+                (void)mbar_wait(&wbars[o % NW], (o / NW) & 1);
+        }
+        __syncthreads();
+    }
+}
+
+template <int NF, class TS, class TW, int TX, int TY, int NS>
+constexpr int px2_smem_bytes()
+{
+    return NS * ((NF * (TX + 2 * GX) * (TY + 2 * GY) * (int)sizeof(TS) + 127) / 128 * 128) +
+           3 * ((NF * TX * TY * (int)sizeof(TW) + 127) / 128 * 128) + (NS + 3) * 8;
+}
+
+}  // namespace tiled2
+
+template <class TS, class TW, class TA, int TX, int TY, int NS>
+cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
+                           int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
+                           cudaStream_t stream, int *launches)
+{
+    CUtensorMap *map = nullptr, *wmap = nullptr;
+    if (!get_state_tmap(cache, b.in, b.Ls, nf, TX, TY, cfg_key, &map))
+        return cudaErrorInvalidValue;
+    if (!get_tile_tmap(cache, b.w, b.Lw, nf, TX, TY, cfg_key, &wmap))
+        return cudaErrorInvalidValue;
+    const int tiles_x = (b.Ls.nx + TX - 1) / TX;
+    const int tiles_y = (b.Ls.ny + TY - 1) / TY;
+    const dim3 grid(tiles_x * tiles_y, (b.Ls.nz + zc - 1) / zc);
+    const dim3 block((TX / 2) * TY);
+    TS *out = (TS *)b.out;
+    TW *w = (TW *)b.w;
+    TS *divf = (TS *)b.div;
+    cudaError_t e;
+#define GBFD_LAUNCH2(NFV, MIX)                                                                    \
+    do {                                                                                          \
+        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS>;                      \
+        constexpr int sm = tiled2::px2_smem_bytes<NFV, TS, TW, TX, TY, NS>();                     \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
+        if (e != cudaSuccess)                                                                     \
+            return e;                                                                             \
+        kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, divf, b.Ls, b.Lw, c, st, zc,       \
+                                          tiles_x, dev_error);                                    \
+    } while (0)
+    if (form == 0) {
+        if (nf == 5)
+            GBFD_LAUNCH2(5, true);
+        else
+            GBFD_LAUNCH2(4, true);
+    } else {
+        if (nf == 5)
+            GBFD_LAUNCH2(5, false);
+        else
+            GBFD_LAUNCH2(4, false);
+    }
+#undef GBFD_LAUNCH2
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace gbfd

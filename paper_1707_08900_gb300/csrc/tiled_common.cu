@@ -11,8 +11,10 @@ namespace {
 
 // (tx, ty, ns) variants compiled per storage width; each is offered with
 // several z-chunk lengths.
-const TileConfig kVariants4[] = {{32, 8, 0, 9}, {32, 4, 0, 9}, {64, 4, 0, 9}, {32, 16, 0, 9}};
-const TileConfig kVariants8[] = {{32, 4, 0, 8}, {16, 8, 0, 8}};
+const TileConfig kVariants4[] = {{32, 8, 0, 9, 1},  {32, 4, 0, 9, 1},  {64, 4, 0, 9, 1},
+                                 {32, 16, 0, 9, 1}, {32, 8, 0, 8, 2},  {32, 16, 0, 9, 2},
+                                 {64, 8, 0, 9, 2}};
+const TileConfig kVariants8[] = {{32, 4, 0, 8, 1}, {16, 8, 0, 8, 1}};
 const int kZc[kZcChoices] = {32, 16, 64, 128};
 constexpr int kNz = kZcChoices;
 
@@ -46,12 +48,14 @@ TileConfig tiled_config(int sbytes, int i)
     return t;
 }
 
-bool get_state_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, int tx, int ty,
-                    int cfg_key, CUtensorMap **out)
+namespace {
+
+bool encode_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, int bx, int by,
+                 int key, CUtensorMap **out)
 {
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < TmapCache::kEntries; ++i) {
         TmapCache::Entry &e = cache->e[i];
-        if (e.valid && e.base == origin && e.cfg == cfg_key && e.nf == nf) {
+        if (e.valid && e.base == origin && e.cfg == key && e.nf == nf) {
             *out = &e.map;
             return true;
         }
@@ -60,14 +64,13 @@ bool get_state_tmap(TmapCache *cache, const void *origin, const Layout &L, int n
     if (!fn)
         return false;
     TmapCache::Entry &e = cache->e[cache->next];
-    cache->next = (cache->next + 1) % 8;
+    cache->next = (cache->next + 1) % TmapCache::kEntries;
     memset(&e, 0, sizeof e);
     const cuuint64_t dims[4] = {(cuuint64_t)(L.nx + 2 * GX), (cuuint64_t)L.rows,
                                 (cuuint64_t)L.nz, (cuuint64_t)nf};
     const cuuint64_t strides[3] = {(cuuint64_t)(L.P * L.w), (cuuint64_t)(L.plane * L.w),
                                    (cuuint64_t)(L.fpitch * L.w)};
-    const cuuint32_t box[4] = {(cuuint32_t)(tx + 2 * GX), (cuuint32_t)(ty + 2 * GY), 1u,
-                               (cuuint32_t)nf};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)nf};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(&e.map, L.w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                     4, const_cast<void *>(origin), dims, strides, box, estr,
@@ -76,11 +79,25 @@ bool get_state_tmap(TmapCache *cache, const void *origin, const Layout &L, int n
     if (r != CUDA_SUCCESS)
         return false;
     e.base = origin;
-    e.cfg = cfg_key;
+    e.cfg = key;
     e.nf = nf;
     e.valid = true;
     *out = &e.map;
     return true;
+}
+
+}  // namespace
+
+bool get_state_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, int tx, int ty,
+                    int cfg_key, CUtensorMap **out)
+{
+    return encode_tmap(cache, origin, L, nf, tx + 2 * GX, ty + 2 * GY, cfg_key, out);
+}
+
+bool get_tile_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, int tx, int ty,
+                   int cfg_key, CUtensorMap **out)
+{
+    return encode_tmap(cache, origin, L, nf, tx, ty, 1000 + cfg_key, out);
 }
 
 }  // namespace gbfd

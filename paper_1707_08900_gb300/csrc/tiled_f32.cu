@@ -1,5 +1,7 @@
-// Tiled substep instantiations with FP32 storage and FP32 arithmetic.
-#include "tiled_impl.cuh"
+// Tiled substep instantiations with FP32 storage and FP32 arithmetic: the
+// one-point-per-thread kernel (variants 0-3) and the paired-load
+// two-points-per-thread kernel (variants 4-6).
+#include "tiled2_impl.cuh"
 
 namespace gbfd {
 
@@ -8,7 +10,9 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
                                  int form, int cfg, int *dev_error, TmapCache *cache,
                                  cudaStream_t stream, int *launches)
 {
-    const int idx = cfg < 0 ? 0 : cfg;
+    // default: two points per thread, 32 x 8 tile, z-chunk 32 (fastest at
+    // 256^3 on GB300 in the tile sweep)
+    const int idx = cfg < 0 ? kDefaultF32 : cfg;
     const TileConfig t = tiled_config(4, idx);
     const int v = idx / kZcChoices;
     cudaError_t e;
@@ -25,9 +29,21 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         e = launch_tiled_cfg<TS, TW, TA, 64, 4, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
                                                    stream, launches);
         break;
-    default:
+    case 3:
         e = launch_tiled_cfg<TS, TW, TA, 32, 16, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
                                                     stream, launches);
+        break;
+    case 4:
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 8>(b, c, st, nf, form, t.zc, v, dev_error, cache,
+                                                 stream, launches);
+        break;
+    case 5:
+        e = launch_px2_cfg<TS, TW, TA, 32, 16, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
+                                                  stream, launches);
+        break;
+    default:
+        e = launch_px2_cfg<TS, TW, TA, 64, 8, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
+                                                 stream, launches);
         break;
     }
     if (e != cudaSuccess || form == 0)

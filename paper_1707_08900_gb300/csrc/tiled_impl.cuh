@@ -257,6 +257,10 @@ constexpr int smem_bytes()
 // buffer for a TX x TY tile: dims (X, Y, z, field), box (TX+8, TY+6, 1, NF).
 bool get_state_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, int tx, int ty,
                     int cfg_key, CUtensorMap **out);
+// Tensor map of the interior tile only (no halo): box (TX, TY, 1, NF), used
+// for the u-tilde buffer.
+bool get_tile_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, int tx, int ty,
+                   int cfg_key, CUtensorMap **out);
 
 template <class TS, class TW, class TA, int TX, int TY, int NS>
 cudaError_t launch_tiled_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,

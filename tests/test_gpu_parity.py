@@ -186,13 +186,44 @@ def test_roll_equivariance_bitwise_fp32():
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_every_tile_config_matches_oracle(precision):
+    """Every entry of the tile table (one and two points per thread, all
+    z-chunk lengths) reproduces the oracle on a ragged grid."""
+    from paper_1707_08900_gb300 import gbfd
+    shape = (20, 44, 36)
+    g = _grid(shape)
+    ph = fd.Physics(cs=1.0, nu=0.01, entropy_mode=1)
+    st = inputs.spectrum(shape, 21, mach=0.2, lnrho_rms=1e-2)
+    if precision == "fp32":
+        st = st.astype(np.float32).astype(np.float64)
+    dt = fd.cfl_dt(st, g, ph, 0.4)
+    ref = fd.rk3_step(st, dt, g, ph)
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    n = 0
+    for cfg in range(64):
+        s = _solver(shape, precision=precision, nu=0.01)
+        try:
+            s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
+        except gbfd.GbfdError:
+            s.close()
+            break
+        s.set_state(st)
+        s.rk3_step(dt, 1)
+        err = rel_l2(s.get_state(), ref)
+        s.close()
+        assert np.all(err <= tol), (cfg, err)
+        n += 1
+    assert n >= (8 if precision == "fp64" else 28)
+
+
 def test_every_tile_config_agrees():
     from paper_1707_08900_gb300 import gbfd
     from paper_1707_08900_gb300 import build  # noqa: F401
     shape = (40, 36, 68)
     st = inputs.spectrum(shape, 9, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
     base = None
-    for cfg in range(16):
+    for cfg in range(64):
         s = _solver(shape, precision="fp32", nu=5e-3)
         try:
             s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
