@@ -174,6 +174,18 @@ gbfd_status gbfd_diagnostics_noalloc(const void *state, int state_is_fp64, int n
 enum { GBFD_OPT_KERNEL_PATH = 1, GBFD_OPT_TILE_CONFIG = 2 };
 gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value);
 
+/* Tile autotuner (no counterpart in the paper; the paper tuned block shapes
+ * and points per thread by hand, Sect. 5).  Times every entry of the tiled
+ * kernels' tile table on the context's current state for `reps` RK3 steps
+ * each and selects the fastest; the state is not advanced (the timed
+ * substeps write the spare buffer and u-tilde only).  With a non-NULL
+ * `cache_path`, a JSON file keyed by GPU name, grid, precision, form and
+ * field count is read first (a hit skips the timing) and updated after.
+ * Outputs (may be NULL): the chosen table index and its ms per RK3 step
+ * (0 on a cache hit).  Synchronises the stream. */
+gbfd_status gbfd_autotune(gbfd_ctx *ctx, int reps, const char *cache_path, int *best_cfg,
+                          double *best_ms);
+
 /* Number of kernel launches the context has enqueued since init. */
 int64_t gbfd_launch_count(const gbfd_ctx *ctx);
 
@@ -184,6 +196,59 @@ const char *gbfd_last_error(const gbfd_ctx *ctx);
 
 /* Static name of a status code. */
 const char *gbfd_status_string(gbfd_status s);
+
+/* ------------------------------------------------------------------------
+ * Batched form (no counterpart in the paper; the paper advances one grid).
+ * nbox independent periodic cubic boxes, box b with n[b]^3 points (n[b] a
+ * multiple of 4 in 8..1024), side lengths[b], viscosity nu[b], common c_s,
+ * FP32 storage and arithmetic, the 55-point fused substep of Algorithm 2.
+ * Each substep of all boxes is one persistent launch over a work list of
+ * equal-cost columns (box, 32 x 8 tile, z-chunk); a run of nsteps RK3 steps
+ * is captured once as a CUDA graph (per nsteps and buffer parity) and
+ * replayed.  Per-box states use the gbfd_set_state layout.
+ * ------------------------------------------------------------------------ */
+typedef struct gbfd_batch gbfd_batch;
+
+/* Workspace bytes for the batch (0 when the sizes are invalid). */
+size_t gbfd_batch_workspace_bytes(int nbox, const int32_t *n, int entropy_mode);
+
+/* Create a batch on the caller's 256-byte aligned device workspace; no
+ * device allocation inside (one private non-blocking stream is created for
+ * graph capture).  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+gbfd_status gbfd_batch_init(int nbox, const int32_t *n, const double *lengths, const double *nu,
+                            double cs, int entropy_mode, void *workspace, size_t workspace_bytes,
+                            void *stream, gbfd_batch **out);
+gbfd_status gbfd_batch_destroy(gbfd_batch *b);
+
+/* Copy one box's state in/out (host or device, FP32 or FP64).  Host copies
+ * synchronise the stream (the staging area is shared by the boxes). */
+gbfd_status gbfd_batch_set_state(gbfd_batch *b, int box, const void *src, int src_on_device,
+                                 int src_is_fp64);
+gbfd_status gbfd_batch_get_state(gbfd_batch *b, int box, void *dst, int dst_on_device,
+                                 int dst_is_fp64);
+
+/* Advance every box nsteps RK3 steps, box b with time step dt[b] (> 0,
+ * finite; host array of nbox values, copied before the call returns). */
+gbfd_status gbfd_batch_step(gbfd_batch *b, const double *dt, int nsteps);
+
+/* FP64 diagnostics of one box (synchronises). */
+gbfd_status gbfd_batch_diagnostics(gbfd_batch *b, int box, gbfd_diag *out);
+
+/* Wait for the stream; TIMEOUT when a bounded device wait gave up. */
+gbfd_status gbfd_batch_sync(gbfd_batch *b);
+
+/* Options: GBFD_BATCH_OPT_GRAPH (1 = replay CUDA graphs, the default; 0 =
+ * direct launches), GBFD_BATCH_OPT_ZCHUNK (planes per work item: 8, 16, 32,
+ * 64), GBFD_BATCH_OPT_GRID (persistent CTAs; default SMs x resident CTAs). */
+enum { GBFD_BATCH_OPT_GRAPH = 1, GBFD_BATCH_OPT_ZCHUNK = 2, GBFD_BATCH_OPT_GRID = 3 };
+gbfd_status gbfd_batch_set_option(gbfd_batch *b, int key, int64_t value);
+
+/* Autotuner of the batch: times `steps` RK3 steps for each z-chunk length
+ * without advancing the state, keeps the fastest (outputs may be NULL). */
+gbfd_status gbfd_batch_autotune(gbfd_batch *b, int steps, int *best_zc, double *best_ms);
+
+int64_t gbfd_batch_launch_count(const gbfd_batch *b);
+const char *gbfd_batch_last_error(const gbfd_batch *b);
 
 #ifdef __cplusplus
 }

@@ -7,7 +7,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
+#include <string>
 
 #include "../../include/gbfd.h"
 #include "kernels.cuh"
@@ -172,6 +174,60 @@ gbfd_status check_ctx(gbfd_ctx *c)
         return GBFD_ERR_STATE;
     }
     return GBFD_OK;
+}
+
+gbfd_status do_substep(gbfd_ctx *c, int s, double dt);
+
+// The autotuner's timing launch: substep s from the current buffer into the
+// spare one, without making the spare one current (the state is unchanged).
+gbfd_status probe_substep(gbfd_ctx *c, int s, double dt)
+{
+    gbfd_status st = do_substep(c, s, dt);
+    if (st == GBFD_OK)
+        c->cur ^= 1;
+    return st;
+}
+
+// Autotuner cache: one JSON object, one entry per line,
+//   "key": {"cfg": <int>, "ms": <double>},
+std::map<std::string, std::pair<int, double>> read_cache(const char *path)
+{
+    std::map<std::string, std::pair<int, double>> m;
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return m;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        const char *q0 = strchr(line, '"');
+        const char *q1 = q0 ? strchr(q0 + 1, '"') : nullptr;
+        if (!q1)
+            continue;
+        int cfg = 0;
+        double ms = 0;
+        const char *c = strstr(q1, "\"cfg\":");
+        const char *t = strstr(q1, "\"ms\":");
+        if (!c || !t || sscanf(c + 6, "%d", &cfg) != 1 || sscanf(t + 5, "%lf", &ms) != 1)
+            continue;
+        m[std::string(q0 + 1, q1)] = std::make_pair(cfg, ms);
+    }
+    fclose(f);
+    return m;
+}
+
+bool write_cache(const char *path, const std::map<std::string, std::pair<int, double>> &m)
+{
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f)
+        return false;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto &kv : m)
+        fprintf(f, "  \"%s\": {\"cfg\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(),
+                kv.second.first, kv.second.second, ++i < m.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+    return rename(tmp.c_str(), path) == 0;
 }
 
 gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
@@ -501,6 +557,101 @@ gbfd_status gbfd_cfl_dt(gbfd_ctx *ctx, double cfl, double cnu, double *dt_out)
         dt = dtn < dt ? dtn : dt;
     }
     *dt_out = dt;
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_autotune(gbfd_ctx *ctx, int reps, const char *cache_path, int *best_cfg,
+                          double *best_ms)
+{
+    gbfd_status st = check_ctx(ctx);
+    if (st != GBFD_OK)
+        return st;
+    if (reps < 1) {
+        set_err(ctx, "autotune: reps must be >= 1");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "autotune device query");
+    char key[512];
+    snprintf(key, sizeof key, "%s|%dx%dx%d|precision%d|form%d|fields%d", prop.name, ctx->p.nx,
+             ctx->p.ny, ctx->p.nz, ctx->p.precision, ctx->p.form, ctx->nf);
+    for (char *p = key; *p; ++p)
+        if (*p == '"' || *p == '\\')
+            *p = '_';
+    // the precision forms compile one tile variant: tune its chunk lengths only
+    const bool acc = ctx->p.precision == GBFD_FP32_ACC64 || ctx->p.precision == GBFD_FP32_ACC64_W64;
+    const int count = acc ? kZcChoices : tiled_config_count(ctx->sbytes);
+    std::map<std::string, std::pair<int, double>> cache;
+    if (cache_path) {
+        cache = read_cache(cache_path);
+        auto it = cache.find(key);
+        if (it != cache.end() && it->second.first >= 0 && it->second.first < count) {
+            ctx->tile_cfg = it->second.first;
+            ctx->kernel_path = 0;
+            if (best_cfg)
+                *best_cfg = ctx->tile_cfg;
+            if (best_ms)
+                *best_ms = 0.0;
+            return GBFD_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "autotune events");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ctx, e, "autotune events");
+    }
+    const int saved_path = ctx->kernel_path, saved_cfg = ctx->tile_cfg;
+    ctx->kernel_path = 0;
+    int best = -1;
+    double bms = 1e300;
+    for (int cfg = 0; cfg < count && st == GBFD_OK; ++cfg) {
+        ctx->tile_cfg = cfg;
+        for (int r = 0; r <= reps && st == GBFD_OK; ++r) {
+            if (r == 1 && (e = cudaEventRecord(e0, ctx->stream)) != cudaSuccess)
+                break;
+            for (int sub = 0; sub < 3 && st == GBFD_OK; ++sub)
+                st = probe_substep(ctx, sub, 1e-6);
+        }
+        if (st != GBFD_OK || e != cudaSuccess)
+            break;
+        float ms = 0;
+        if ((e = cudaEventRecord(e1, ctx->stream)) != cudaSuccess ||
+            (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+            break;
+        if (ms / reps < bms) {
+            bms = ms / reps;
+            best = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == GBFD_OK && e != cudaSuccess)
+        st = cuda_fail(ctx, e, "autotune timing");
+    if (st != GBFD_OK || best < 0) {
+        ctx->kernel_path = saved_path;
+        ctx->tile_cfg = saved_cfg;
+        return st != GBFD_OK ? st : GBFD_ERR_CUDA;
+    }
+    ctx->tile_cfg = best;
+    if (cache_path) {
+        cache[key] = std::make_pair(best, bms);
+        if (!write_cache(cache_path, cache)) {
+            set_err(ctx, "autotune: cannot write cache %s", cache_path);
+            return GBFD_ERR_INVALID_ARG;
+        }
+    }
+    if (best_cfg)
+        *best_cfg = best;
+    if (best_ms)
+        *best_ms = bms;
     return GBFD_OK;
 }
 

@@ -78,6 +78,24 @@ struct Coef {
     T nu3;     // nu / 3
     T nu2;     // 2 nu
     T nu23;    // (2/3) nu
+    // accessors shared with CubicCoef (axis a, pair p, arm k = 1..3)
+    __host__ __device__ __forceinline__ T D1(int a, int k) const { return d1[a][k - 1]; }
+    __host__ __device__ __forceinline__ T D2c(int a) const { return d2c[a]; }
+    __host__ __device__ __forceinline__ T D2(int a, int k) const { return d2[a][k - 1]; }
+    __host__ __device__ __forceinline__ T MX(int p, int k) const { return mx[p][k - 1]; }
+};
+
+// Coefficients of a box with the same spacing h on every axis: one set of
+// stencil weights serves all axes (10 values plus 4 physics scalars), small
+// enough to live in registers when it changes from box to box.
+template <class T>
+struct CubicCoef {
+    T d1[3], d2c, d2[3], mx[3];
+    T cs2, nu, nu3, nu23;
+    __host__ __device__ __forceinline__ T D1(int, int k) const { return d1[k - 1]; }
+    __host__ __device__ __forceinline__ T D2c(int) const { return d2c; }
+    __host__ __device__ __forceinline__ T D2(int, int k) const { return d2[k - 1]; }
+    __host__ __device__ __forceinline__ T MX(int, int k) const { return mx[k - 1]; }
 };
 
 template <class T>
@@ -105,6 +123,24 @@ inline Coef<T> make_coef(double hx, double hy, double hz, double cs, double nu)
     c.nu2 = (T)(2.0 * nu);
     c.nu23 = (T)(2.0 * nu / 3.0);
     return c;
+}
+
+template <class T>
+inline CubicCoef<T> make_cubic_coef(double h, double cs, double nu)
+{
+    Coef<T> c = make_coef<T>(h, h, h, cs, nu);
+    CubicCoef<T> q;
+    for (int k = 0; k < 3; ++k) {
+        q.d1[k] = c.d1[0][k];
+        q.d2[k] = c.d2[0][k];
+        q.mx[k] = c.mx[0][k];
+    }
+    q.d2c = c.d2c[0];
+    q.cs2 = c.cs2;
+    q.nu = c.nu;
+    q.nu3 = c.nu3;
+    q.nu23 = c.nu23;
+    return q;
 }
 
 // Williamson (1980) 2N-storage RK3: the paper's Eq. 10 leaves alpha, beta to

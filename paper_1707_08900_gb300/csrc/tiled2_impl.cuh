@@ -1,7 +1,16 @@
-// Tiled fused substep, two points per thread (x, x+1): the same TMA plane
-// ring and z-register sliding as tiled_impl.cuh, but every shared-memory
-// read fetches an aligned pair (float2 / double2), so one load serves both
-// points' stencil arms and the per-point index/loop overhead is halved.
+// Tiled fused substep, two points per thread (x, x+1).
+//
+// Pipeline of one CTA over one column of a box (tile x0..x0+TX, y0..y0+TY,
+// output planes z0..z0+nout):
+// * each z-plane of all NF fields, tile plus 3-cell halo, arrives by ONE 4D
+//   TMA copy into a ring of NS shared-memory slots (per-slot mbarrier);
+// * u-tilde of the output plane (no halo) arrives by a second TMA ring of 3
+//   slots, two planes ahead, so the loop has no global loads at all;
+// * every shared-memory read fetches an aligned pair (float2 / double2) that
+//   serves both points' stencil arms; the thread's own z-column slides
+//   through registers;
+// * the barrier phases run on per-CTA counters, so a persistent CTA can
+//   stream many columns (of many boxes) through the same ring.
 //
 // The right-hand side of Eqs. 1-3 is accumulated field by field so that only
 // the running sums stay live:
@@ -39,80 +48,100 @@ struct Row {
     T e[10];
 };
 
-template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS>
-__global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
-    const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
-    TS *__restrict__ out, TW *__restrict__ w,
-    TS *__restrict__ divf, const Layout Ls, const Layout Lw, const Coef<TS> c, const RKStage st,
-    const int zc, const int tiles_x, int *__restrict__ dev_error)
+// Shared-memory carve-up of the pipeline.
+template <class TS, class TW, int NF, int TX, int TY, int NS>
+struct Ring {
+    static constexpr int BX = TX + 2 * GX;
+    static constexpr int BY = TY + 2 * GY;
+    static constexpr int FSTRIDE = BX * BY;
+    static constexpr int SLOT_BYTES = NF * FSTRIDE * (int)sizeof(TS);
+    static constexpr int SLOT_PITCH = (SLOT_BYTES + 127) / 128 * 128;
+    static constexpr int SLOT_ELEMS = SLOT_PITCH / (int)sizeof(TS);
+    static constexpr int NW = 3;
+    static constexpr int WSLOT_BYTES = NF * TX * TY * (int)sizeof(TW);
+    static constexpr int WSLOT_PITCH = (WSLOT_BYTES + 127) / 128 * 128;
+    static constexpr int W_OFF = NS * SLOT_PITCH;
+    static constexpr int BAR_OFF = W_OFF + NW * WSLOT_PITCH;
+    static constexpr int BYTES = BAR_OFF + (NS + NW) * 8;
+};
+
+__device__ __forceinline__ void init_barriers(uint64_t *bars, int n)
 {
+    if (threadIdx.x == 0) {
+#pragma unroll 1
+        for (int i = 0; i < n; ++i)
+            tiled::mbar_init(&bars[i], 1);
+        tiled::fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// One column of one box.  jrun / wrun count the state-plane and u-tilde
+// copies this CTA has made before (they continue the barrier phases) and are
+// advanced on return.  Returns false when a bounded wait gave up (after
+// recording it and draining the copies in flight).
+template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, class CoefT>
+__device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
+                                           TS *__restrict__ out, TW *__restrict__ w,
+                                           TS *__restrict__ divf, const Layout &Ls,
+                                           const Layout &Lw, const CoefT &c, const TA alpha,
+                                           const TA beta, const TA dt, const bool first,
+                                           const bool last, const int x0, const int y0,
+                                           const int z0, const int nout, int &jrun, int &wrun,
+                                           unsigned char *smem, int *dev_error)
+{
+    using RG = Ring<TS, TW, NF, TX, TY, NS>;
     using tiled::mbar_wait;
     using V = typename V2<TS>::t;
-    constexpr int BX = TX + 2 * GX;
-    constexpr int BY = TY + 2 * GY;
-    constexpr int FSTRIDE = BX * BY;
-    constexpr int SLOT_BYTES = NF * FSTRIDE * (int)sizeof(TS);
-    constexpr int SLOT_PITCH = (SLOT_BYTES + 127) / 128 * 128;
-    constexpr int SLOT_ELEMS = SLOT_PITCH / (int)sizeof(TS);
+    using VW = typename V2<TW>::t;
+    constexpr int BX = RG::BX, FSTRIDE = RG::FSTRIDE, SLOT_ELEMS = RG::SLOT_ELEMS;
+    constexpr int NW = RG::NW;
     constexpr int NTX = TX / 2;
-    // u-tilde ring: NW slots of the tile (no halo), TMA-loaded two planes ahead
-    constexpr int NW = 3;
-    constexpr int WSLOT_BYTES = NF * TX * TY * (int)sizeof(TW);
-    constexpr int WSLOT_PITCH = (WSLOT_BYTES + 127) / 128 * 128;
-    extern __shared__ __align__(128) unsigned char smem[];
     const TS *sm = reinterpret_cast<const TS *>(smem);
-    unsigned char *wsm = smem + NS * SLOT_PITCH;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + NW * WSLOT_PITCH);
+    unsigned char *wsm = smem + RG::W_OFF;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF);
     uint64_t *wbars = bars + NS;
 
     const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
-    const int x0 = (blockIdx.x % tiles_x) * TX;
-    const int y0 = (blockIdx.x / tiles_x) * TY;
-    const int z0 = blockIdx.y * zc;
     const int nz = Ls.nz;
-    const int nout = min(zc, nz - z0);
     const int nplanes = nout + 2 * R;
     const int x = x0 + 2 * tx, y = y0 + ty;
     const bool valid0 = (x < Ls.nx) && (y < Ls.ny);  // nx % 4 == 0: x+1 valid with x
     // element offset of point (x, y) in a field of a slot; even, so pairs align
     const int toff = (ty + GY) * BX + (2 * tx + GX);
+    const bool need_w = !first;
 
-    if (threadIdx.x == 0) {
-#pragma unroll 1
-        for (int i = 0; i < NS + NW; ++i)
-            tiled::mbar_init(&bars[i], 1);
-        tiled::fence_mbar_init();
-    }
+    // every thread is done with the previous column's slots
     __syncthreads();
 
-    // u-tilde of output plane o (grid plane z0 + o) goes to w-slot o % NW
-    const bool need_w = !st.first;
-    int wissued = 0;
-    auto issue_w = [&](int o) {
-        const int slot = o % NW;
-        tiled::mbar_expect_tx(&wbars[slot], WSLOT_BYTES);
-        tiled::tma_load_4d(wsm + slot * WSLOT_PITCH, &wmap, &wbars[slot], x0 + GX, y0 + GY,
-                           z0 + o, 0);
-    };
-    if (threadIdx.x == 0 && need_w) {
-        for (int o = 0; o < NW - 1 && o < nout; ++o)
-            issue_w(o);
-        wissued = min(NW - 1, nout);
-    }
-
-    int issued = 0;
+    // local state plane j is grid plane z0 - 3 + j (wrapped); it is copy
+    // jrun + j of this CTA: slot (jrun + j) % NS, phase (jrun + j) / NS
+    int issued = 0, wissued = 0;
     auto issue = [&](int j) {
         int z = z0 - R + j;
         z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-        const int slot = j % NS;
-        tiled::mbar_expect_tx(&bars[slot], SLOT_BYTES);
-        tiled::tma_load_4d(smem + slot * SLOT_PITCH, &tmap, &bars[slot], x0, y0, z, 0);
+        const int slot = (jrun + j) % NS;
+        tiled::mbar_expect_tx(&bars[slot], RG::SLOT_BYTES);
+        tiled::tma_load_4d(smem + slot * RG::SLOT_PITCH, tmap, &bars[slot], x0, y0, z, 0);
+    };
+    auto issue_w = [&](int o) {
+        const int slot = (wrun + o) % NW;
+        tiled::mbar_expect_tx(&wbars[slot], RG::WSLOT_BYTES);
+        tiled::tma_load_4d(wsm + slot * RG::WSLOT_PITCH, wmap, &wbars[slot], x0 + GX, y0 + GY,
+                           z0 + o, 0);
     };
     if (threadIdx.x == 0) {
+        tiled::fence_proxy_async();
 #pragma unroll 1
         for (int j = 0; j < NS - 1 && j < nplanes; ++j)
             issue(j);
         issued = min(NS - 1, nplanes);
+        if (need_w) {
+#pragma unroll 1
+            for (int o = 0; o < NW - 1 && o < nout; ++o)
+                issue_w(o);
+            wissued = min(NW - 1, nout);
+        }
     }
 
     // z-column window of both points: col[f][k][j], planes o..o+6, point j
@@ -120,11 +149,12 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
     bool timeout = false;
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j) {
-        if (!mbar_wait(&bars[j % NS], (j / NS) & 1))
+        const int q = jrun + j;
+        if (!mbar_wait(&bars[q % NS], (q / NS) & 1))
             timeout = true;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const V v = *reinterpret_cast<const V *>(sm + (j % NS) * SLOT_ELEMS + f * FSTRIDE + toff);
+            const V v = *reinterpret_cast<const V *>(sm + (q % NS) * SLOT_ELEMS + f * FSTRIDE + toff);
             col[f][j][0] = v.x;
             col[f][j][1] = v.y;
         }
@@ -145,11 +175,12 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
     else if (y >= Ls.ny - GY)
         gdy = -(long long)Ls.ny * Ls.P;
 
-    const TA alpha = (TA)st.alpha, beta = (TA)st.beta, dt = (TA)st.dt;
-    int waited = 2 * R;
-    int slot0 = 0;  // slot of plane o
+    int waited = 2 * R, wwaited = 0;
+    int slot0 = jrun % NS;  // slot of local plane o
 #pragma unroll 1
     for (int o = 0; o < nout; ++o) {
+        // all threads are done with plane o-1: its slot is free, and a
+        // timeout seen by any thread ends the CTA for everyone
         if (__syncthreads_or(timeout))
             break;
         if (threadIdx.x == 0) {
@@ -164,12 +195,16 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
                 wissued = o + NW;
             }
         }
-        const int jn = o + 2 * R;
-        if (!mbar_wait(&bars[jn % NS], (jn / NS) & 1))
+        const int qn = jrun + o + 2 * R;
+        if (!mbar_wait(&bars[qn % NS], (qn / NS) & 1))
             timeout = true;
-        if (need_w && !mbar_wait(&wbars[o % NW], (o / NW) & 1))
-            timeout = true;
-        waited = jn + 1;
+        waited = o + 2 * R + 1;
+        if (need_w) {
+            const int qw = wrun + o;
+            if (!mbar_wait(&wbars[qw % NW], (qw / NW) & 1))
+                timeout = true;
+            wwaited = o + 1;
+        }
         int so[7];  // element offsets of the 7 window planes' slots
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
@@ -220,12 +255,11 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
             const int zo = z0 + o;
             TW wv[NF][2];
             if (need_w) {
-                const TW *ws = reinterpret_cast<const TW *>(wsm + (o % NW) * WSLOT_PITCH) +
+                const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + o) % NW) * RG::WSLOT_PITCH) +
                                ty * TX + 2 * tx;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    const typename V2<TW>::t t =
-                        *reinterpret_cast<const typename V2<TW>::t *>(ws + f * TX * TY);
+                    const VW t = *reinterpret_cast<const VW *>(ws + f * TX * TY);
                     wv[f][0] = t.x;
                     wv[f][1] = t.y;
                 }
@@ -248,20 +282,20 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
                 for (int j = 0; j < 2; ++j) {
                     const TS cc = col[f][3][j];
                     TS ax = (TS)0, ay = (TS)0, az = (TS)0;
-                    TS bx = c.d2c[0] * cc, by = c.d2c[1] * cc, bz = c.d2c[2] * cc;
+                    TS bx = c.D2c(0) * cc, by = c.D2c(1) * cc, bz = c.D2c(2) * cc;
 #pragma unroll
                     for (int k = 1; k <= 3; ++k) {
                         const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
                         const TS ypv = j ? yp[k - 1].y : yp[k - 1].x;
                         const TS ymv = j ? ym[k - 1].y : ym[k - 1].x;
                         const TS zp = col[f][3 + k][j], zm = col[f][3 - k][j];
-                        ax += c.d1[0][k - 1] * (xp - xm);
-                        ay += c.d1[1][k - 1] * (ypv - ymv);
-                        az += c.d1[2][k - 1] * (zp - zm);
+                        ax += c.D1(0, k) * (xp - xm);
+                        ay += c.D1(1, k) * (ypv - ymv);
+                        az += c.D1(2, k) * (zp - zm);
                         if (second) {
-                            bx += c.d2[0][k - 1] * (xp + xm);
-                            by += c.d2[1][k - 1] * (ypv + ymv);
-                            bz += c.d2[2][k - 1] * (zp + zm);
+                            bx += c.D2(0, k) * (xp + xm);
+                            by += c.D2(1, k) * (ypv + ymv);
+                            bz += c.D2(2, k) * (zp + zm);
                         }
                     }
                     g[j][0] = ax;
@@ -272,7 +306,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
                     d2[j][2] = bz;
                 }
             };
-            // Eq. 8 in the (x, y) plane (dzsel = 0) or (x, z) plane: rows or
+            // Eq. 8 in the (x, y) plane (in_y) or the (x, z) plane: rows or
             // planes at +-k, x offsets +-k, for both points
             auto mix_x = [&](int f, bool in_y, TS *res) {
                 Row<TS> rp[3], rm[3];
@@ -303,7 +337,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
                     for (int k = 1; k <= 3; ++k) {
                         const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
                         const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
-                        a += c.mx[in_y ? 0 : 1][k - 1] * ((pp - mp) + (mm - pm));
+                        a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
                     }
                     res[j] = a;
                 }
@@ -315,8 +349,8 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
                 for (int k = 1; k <= 3; ++k) {
                     const V pp = ld2(f, k, k, 0), mp = ld2(f, k, -k, 0);
                     const V mm = ld2(f, -k, -k, 0), pm = ld2(f, -k, k, 0);
-                    a0 += c.mx[2][k - 1] * ((pp.x - mp.x) + (mm.x - pm.x));
-                    a1 += c.mx[2][k - 1] * ((pp.y - mp.y) + (mm.y - pm.y));
+                    a0 += c.MX(2, k) * ((pp.x - mp.x) + (mm.x - pm.x));
+                    a1 += c.MX(2, k) * ((pp.y - mp.y) + (mm.y - pm.y));
                 }
                 res[0] = a0;
                 res[1] = a1;
@@ -404,7 +438,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
                     acc[j][1 + a] += -c.cs2 * gl[j][a] - c.nu23 * dv[j] * gl[j][a];
             }
             if (!MIXED) {
-                typename V2<TS>::t dvv;
+                V dvv;
                 dvv.x = dv[0];
                 dvv.y = dv[1];
                 const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
@@ -424,16 +458,15 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const TS r = f < 4 ? acc[j][f] : rs[j];
-                    TW wo = st.first ? (TW)0 : wv[f][j];
-                    rk3_update<TA, TW, TS>(st.first, alpha, beta, dt, (TA)r, col[f][3][j], wo,
-                                           ov[j]);
+                    TW wo = first ? (TW)0 : wv[f][j];
+                    rk3_update<TA, TW, TS>(first, alpha, beta, dt, (TA)r, col[f][3][j], wo, ov[j]);
                     wn[j] = wo;
                 }
-                if (!st.last) {
-                    typename V2<TW>::t t;
+                if (!last) {
+                    VW t;
                     t.x = wn[0];
                     t.y = wn[1];
-                    *reinterpret_cast<typename V2<TW>::t *>(w + f * Lw.fpitch + go_w) = t;
+                    *reinterpret_cast<VW *>(w + f * Lw.fpitch + go_w) = t;
                 }
                 V o2;
                 o2.x = ov[0];
@@ -459,23 +492,40 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
                 col[f][k][1] = col[f][k + 1][1];
             }
     }
-    if (__syncthreads_or(timeout)) {
-        if (threadIdx.x == 0) {
-            atomicExch(dev_error, 1);
-            for (int j = waited; j < issued; ++j)
-                (void)mbar_wait(&bars[j % NS], (j / NS) & 1);
-            for (int o = 0; o < wissued; ++o)  // phases already complete return at once
-                (void)mbar_wait(&wbars[o % NW], (o / NW) & 1);
-        }
-        __syncthreads();
+    const bool bad = __syncthreads_or(timeout);
+    if (bad && threadIdx.x == 0) {
+        atomicExch(dev_error, 1);
+        // drain the copies still in flight into this CTA's shared memory
+        for (int j = waited; j < issued; ++j)
+            (void)mbar_wait(&bars[(jrun + j) % NS], ((jrun + j) / NS) & 1);
+        for (int o = wwaited; o < wissued; ++o)
+            (void)mbar_wait(&wbars[(wrun + o) % NW], ((wrun + o) / NW) & 1);
     }
+    jrun += nplanes;
+    wrun += need_w ? nout : 0;
+    return !bad;
 }
 
-template <int NF, class TS, class TW, int TX, int TY, int NS>
-constexpr int px2_smem_bytes()
+// Single box: one CTA per (tile, z-chunk).
+template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS>
+__global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
+    const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
+    TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
+    const Layout Lw, const Coef<TS> c, const RKStage st, const int zc, const int tiles_x,
+    int *__restrict__ dev_error)
 {
-    return NS * ((NF * (TX + 2 * GX) * (TY + 2 * GY) * (int)sizeof(TS) + 127) / 128 * 128) +
-           3 * ((NF * TX * TY * (int)sizeof(TW) + 127) / 128 * 128) + (NS + 3) * 8;
+    using RG = Ring<TS, TW, NF, TX, TY, NS>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    init_barriers(reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF), NS + RG::NW);
+    const int x0 = (blockIdx.x % tiles_x) * TX;
+    const int y0 = (blockIdx.x / tiles_x) * TY;
+    const int z0 = blockIdx.y * zc;
+    const int nout = min(zc, Ls.nz - z0);
+    int jrun = 0, wrun = 0;
+    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
+                                                  (TA)st.alpha, (TA)st.beta, (TA)st.dt,
+                                                  st.first != 0, st.last != 0, x0, y0, z0, nout,
+                                                  jrun, wrun, smem, dev_error);
 }
 
 }  // namespace tiled2
@@ -501,7 +551,7 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
 #define GBFD_LAUNCH2(NFV, MIX)                                                                    \
     do {                                                                                          \
         auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS>;                      \
-        constexpr int sm = tiled2::px2_smem_bytes<NFV, TS, TW, TX, TY, NS>();                     \
+        constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS>::BYTES;                          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \

@@ -30,7 +30,12 @@ FORMS = {"55p": GBFD_55P, "19p": GBFD_19P}
 EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state",
            "gbfd_get_state", "gbfd_rk3_step", "gbfd_substep", "gbfd_diagnostics", "gbfd_cfl_dt",
            "gbfd_sync", "gbfd_set_option", "gbfd_launch_count", "gbfd_last_error",
-           "gbfd_status_string", "gbfd_diagnostics_noalloc")
+           "gbfd_status_string", "gbfd_diagnostics_noalloc", "gbfd_autotune",
+           "gbfd_batch_workspace_bytes", "gbfd_batch_init", "gbfd_batch_destroy",
+           "gbfd_batch_set_state", "gbfd_batch_get_state", "gbfd_batch_step",
+           "gbfd_batch_diagnostics", "gbfd_batch_sync", "gbfd_batch_set_option",
+           "gbfd_batch_autotune", "gbfd_batch_launch_count", "gbfd_batch_last_error")
+GBFD_BATCH_OPT_GRAPH, GBFD_BATCH_OPT_ZCHUNK, GBFD_BATCH_OPT_GRID = 1, 2, 3
 
 
 class GbfdError(RuntimeError):
@@ -97,6 +102,26 @@ def load(path=None):
     L.gbfd_diagnostics_noalloc.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, _VP, _VP]
+    L.gbfd_autotune.argtypes = [_VP, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_double)]
+    _I32P = ctypes.POINTER(ctypes.c_int32)
+    _DP = ctypes.POINTER(ctypes.c_double)
+    L.gbfd_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.gbfd_batch_workspace_bytes.argtypes = [ctypes.c_int, _I32P, ctypes.c_int]
+    L.gbfd_batch_init.argtypes = [ctypes.c_int, _I32P, _DP, _DP, ctypes.c_double, ctypes.c_int,
+                                  _VP, ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]
+    L.gbfd_batch_destroy.argtypes = [_VP]
+    L.gbfd_batch_set_state.argtypes = [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int]
+    L.gbfd_batch_get_state.argtypes = [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int]
+    L.gbfd_batch_step.argtypes = [_VP, _DP, ctypes.c_int]
+    L.gbfd_batch_diagnostics.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(gbfd_diag)]
+    L.gbfd_batch_sync.argtypes = [_VP]
+    L.gbfd_batch_set_option.argtypes = [_VP, ctypes.c_int, ctypes.c_int64]
+    L.gbfd_batch_autotune.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP]
+    L.gbfd_batch_launch_count.restype = ctypes.c_int64
+    L.gbfd_batch_launch_count.argtypes = [_VP]
+    L.gbfd_batch_last_error.restype = ctypes.c_char_p
+    L.gbfd_batch_last_error.argtypes = [_VP]
     L.gbfd_status_string.restype = ctypes.c_char_p
     L.gbfd_status_string.argtypes = [ctypes.c_int]
     for name in EXPORTS:
@@ -174,6 +199,16 @@ def gbfd_diagnostics_noalloc(state_ptr, state_is_fp64, nx, ny, nz, nfields, lx, 
     without a context, a workspace or any allocation (see include/gbfd.h)."""
     _check(load().gbfd_diagnostics_noalloc(_VP(state_ptr), int(state_is_fp64), nx, ny, nz,
                                            nfields, lx, ly, lz, _VP(stream_ptr), _VP(out_ptr)))
+
+
+def gbfd_autotune(ctx, reps=3, cache_path=None):
+    """Pick the fastest tile configuration (see include/gbfd.h); returns
+    (table index, ms per RK3 step, 0.0 on a cache hit)."""
+    cfg = ctypes.c_int()
+    ms = ctypes.c_double()
+    path = cache_path.encode() if cache_path else None
+    _check(load().gbfd_autotune(ctx, int(reps), path, ctypes.byref(cfg), ctypes.byref(ms)), ctx)
+    return cfg.value, ms.value
 
 
 def gbfd_last_error(ctx=None):
@@ -275,3 +310,98 @@ class Solver:
 
     def launches(self):
         return gbfd_launch_count(self.ctx)
+
+    def autotune(self, reps=3, cache_path=None):
+        return gbfd_autotune(self.ctx, reps, cache_path)
+
+
+# ------------------------------------------------------------ batched form
+
+def _bcheck(status, b=None):
+    if status != GBFD_OK:
+        raise GbfdError(status, load().gbfd_batch_last_error(b).decode(errors="replace"))
+
+
+class Batch:
+    """Many independent periodic cubic boxes (FP32, 55-point) advanced by one
+    persistent launch per substep, replayed from a CUDA graph.
+
+    n, lengths, nu: per-box points per side, side length and viscosity."""
+
+    def __init__(self, n, lengths, nu, cs=1.0, entropy_mode=1, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("gbfd needs a CUDA device; there is no CPU path")
+        L = load()
+        self.torch = torch
+        self.n = [int(v) for v in n]
+        self.nbox = len(self.n)
+        self.nfields = 5 if entropy_mode else 4
+        self._n = (ctypes.c_int32 * self.nbox)(*self.n)
+        self._len = (ctypes.c_double * self.nbox)(*[float(v) for v in lengths])
+        self._nu = (ctypes.c_double * self.nbox)(*[float(v) for v in nu])
+        nbytes = L.gbfd_batch_workspace_bytes(self.nbox, self._n, int(entropy_mode))
+        if nbytes == 0:
+            raise GbfdError(1, "invalid batch sizes")
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.b = _VP()
+        _bcheck(L.gbfd_batch_init(self.nbox, self._n, self._len, self._nu, float(cs),
+                                  int(entropy_mode), _VP(self.workspace.data_ptr()), nbytes,
+                                  _VP(self.stream.cuda_stream), ctypes.byref(self.b)))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().gbfd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, box, state):
+        torch = self.torch
+        if isinstance(state, np.ndarray):
+            state = torch.from_numpy(np.ascontiguousarray(state))
+        state = state.contiguous()
+        n = self.n[box]
+        assert tuple(state.shape) == (self.nfields, n, n, n), state.shape
+        _bcheck(load().gbfd_batch_set_state(self.b, int(box), _VP(state.data_ptr()),
+                                            int(state.is_cuda),
+                                            int(state.dtype == torch.float64)), self.b)
+
+    def get_state(self, box, fp64=True):
+        n = self.n[box]
+        out = np.empty((self.nfields, n, n, n), dtype=np.float64 if fp64 else np.float32)
+        _bcheck(load().gbfd_batch_get_state(self.b, int(box), _VP(out.ctypes.data), 0, int(fp64)),
+                self.b)
+        return out
+
+    def step(self, dt, nsteps=1):
+        arr = (ctypes.c_double * self.nbox)(*[float(v) for v in dt])
+        _bcheck(load().gbfd_batch_step(self.b, arr, int(nsteps)), self.b)
+
+    def diagnostics(self, box):
+        d = gbfd_diag()
+        _bcheck(load().gbfd_batch_diagnostics(self.b, int(box), ctypes.byref(d)), self.b)
+        return d.as_dict()
+
+    def sync(self):
+        _bcheck(load().gbfd_batch_sync(self.b), self.b)
+
+    def set_option(self, key, value):
+        _bcheck(load().gbfd_batch_set_option(self.b, int(key), int(value)), self.b)
+
+    def autotune(self, steps=2):
+        zc = ctypes.c_int()
+        ms = ctypes.c_double()
+        _bcheck(load().gbfd_batch_autotune(self.b, int(steps), ctypes.byref(zc), ctypes.byref(ms)),
+                self.b)
+        return zc.value, ms.value
+
+    def launches(self):
+        return load().gbfd_batch_launch_count(self.b)
