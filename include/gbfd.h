@@ -250,6 +250,61 @@ gbfd_status gbfd_batch_autotune(gbfd_batch *b, int steps, int *best_zc, double *
 int64_t gbfd_batch_launch_count(const gbfd_batch *b);
 const char *gbfd_batch_last_error(const gbfd_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Learned coarse-grid correction (no counterpart in the paper).  A small
+ * network corrects a coarse FP32 solver state after each RK3 step:
+ *   state += std_out * net((state - mean_in) / std_in)   per channel,
+ * net = conv3 . GELU . conv2 . GELU . conv1, each a periodic 3x3x3
+ * cross-correlation y[o,p] = b[o] + sum_{c,t} W[o,c,t] x[c,p+t] (channels
+ * 5 -> 32 -> 32 -> 5, exact GELU).  BF16 weights and activations, FP32
+ * accumulation: the convolutions and their input gradients run as
+ * implicit GEMMs on the tcgen05 tensor cores; weight gradients are FP32
+ * sums over the grid; Adam keeps FP32 master weights.
+ * Compact state arrays are [batch][5][n][n][n] FP32 on the device (the fifth
+ * channel is ignored when nf = 4).  Parameters are exchanged in FP32, layer
+ * by layer: W1 [32][5][3][3][3], b1 [32], W2 [32][32][3][3][3], b2 [32],
+ * W3 [5][32][3][3][3], b3 [5] (gbfd_cnn_param_count() floats).
+ * ------------------------------------------------------------------------ */
+typedef struct gbfd_cnn gbfd_cnn;
+
+/* Workspace for a network on an n^3 grid training on up to `batch` samples
+ * at once (0 when invalid: n in 4..512, batch * n^3 <= 2^30). */
+size_t gbfd_cnn_workspace_bytes(int n, int batch);
+/* Create on a 1024-byte aligned device workspace (no device allocation). */
+gbfd_status gbfd_cnn_init(int n, int batch, void *workspace, size_t workspace_bytes, void *stream,
+                          gbfd_cnn **out);
+gbfd_status gbfd_cnn_destroy(gbfd_cnn *c);
+int gbfd_cnn_param_count(void);
+/* Host FP32 parameters in / out (set resets the Adam moments). */
+gbfd_status gbfd_cnn_set_params(gbfd_cnn *c, const float *params);
+gbfd_status gbfd_cnn_get_params(gbfd_cnn *c, float *params);
+/* Per-channel input mean/std and output std (5 values each, host). */
+gbfd_status gbfd_cnn_set_norm(gbfd_cnn *c, const float *mean_in, const float *std_in,
+                              const float *std_out);
+/* Normalised network output ys [batch][5][n^3] of device states xs. */
+gbfd_status gbfd_cnn_forward(gbfd_cnn *c, const float *xs, int nf, int batch, float *ys);
+/* Loss (mean over batch, channel and point of (net(x) - (t - x)/std_out)^2)
+ * and its gradient w.r.t. the parameters (host, param_count floats; NULL
+ * skips the copy); xs are coarse-stepped states, ts the targets.
+ * Synchronises. */
+gbfd_status gbfd_cnn_gradients(gbfd_cnn *c, const float *xs, const float *ts, int nf, int batch,
+                               float *grads, double *loss);
+/* One Adam step (beta = 0.9, 0.999, eps 1e-8) on the same loss; the loss
+ * before the step is returned when `loss` is non-NULL (synchronises then). */
+gbfd_status gbfd_cnn_train_step(gbfd_cnn *c, const float *xs, const float *ts, int nf, int batch,
+                                float lr, double *loss);
+/* Apply the correction to the current state of an FP32 cubic context of the
+ * network's grid (on the context's stream). */
+gbfd_status gbfd_cnn_apply(gbfd_cnn *c, gbfd_ctx *ctx);
+/* nsteps of: one RK3 step, then the correction. */
+gbfd_status gbfd_step_corrected(gbfd_ctx *ctx, gbfd_cnn *c, double dt, int nsteps);
+/* Centred box filter of an FP32 cubic context's state to an r times coarser
+ * grid (r even): per axis weights (1/2, 1, ..., 1, 1/2) / r over fine offsets
+ * -r/2..r/2 about fine vertex r I; out is [nf][nc^3] FP32 on the device. */
+gbfd_status gbfd_box_filter(gbfd_ctx *fine, int r, float *out);
+int64_t gbfd_cnn_launch_count(const gbfd_cnn *c);
+const char *gbfd_cnn_last_error(const gbfd_cnn *c);
+
 #ifdef __cplusplus
 }
 #endif

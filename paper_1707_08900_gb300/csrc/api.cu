@@ -279,6 +279,19 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
 namespace gbfd {
 // Record a failure of a context-free entry point; read by gbfd_last_error(NULL).
 void set_global_error(const char *msg) { set_err(nullptr, "%s", msg); }
+
+// Current state of an FP32-storage context on a cubic grid (used by the
+// correction network and the box filter); false otherwise.
+bool ctx_view(gbfd_ctx *c, float **origin, Layout *L, int *nf, cudaStream_t *s)
+{
+    if (!c || c->broken || c->sbytes != 4 || c->p.nx != c->p.ny || c->p.ny != c->p.nz)
+        return false;
+    *origin = reinterpret_cast<float *>(c->state_region[c->cur] + c->Ls.origin);
+    *L = c->Ls;
+    *nf = c->nf;
+    *s = c->stream;
+    return true;
+}
 }  // namespace gbfd
 
 extern "C" {

@@ -33,7 +33,7 @@ namespace batch {
 
 constexpr int TX = 32, TY = 8, NS = 8;
 
-struct alignas(64) BoxDesc {
+struct BoxDesc {
     CUtensorMap tm_state[2];  // halo boxes of state buffers 0 and 1
     CUtensorMap tm_w;         // tile boxes of u-tilde
     float *state[2];          // origins of the padded state buffers

@@ -1,0 +1,1124 @@
+// Coarse-grid correction network: three periodic 3x3x3 convolutions
+// (5 -> 32 -> 32 -> 5 channels, exact GELU after the first two) applied to a
+// coarse solver state after each RK3 step, trained on the GPU.
+//
+// * Convolutions (forward, and the input gradient of the backward pass) are
+//   implicit GEMMs on the tcgen05 tensor cores: M = 128 grid points per tile,
+//   N = output channels, K = 27 taps x input channels; BF16 operands staged
+//   in shared memory as K-major core matrices, FP32 accumulators in TMEM.
+//   The A operand (im2col rows) is gathered per tap straight from the
+//   channels-last activations with periodic wrap; the B operand (weights) is
+//   resident in shared memory.  The input gradient is the same kernel with
+//   the weights transposed in channels and flipped in taps.
+// * The weight gradient sums over all grid points (K = points) on CUDA cores
+//   in FP32, split over CTAs and reduced in a fixed order (deterministic).
+// * MSE loss, Adam (FP32 master weights, BF16 copies in both GEMM layouts),
+//   input normalisation, the residual update of the solver state, and the
+//   centred box filter that makes training targets from fine-grid runs.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gbfd.h"
+#include "kernels.cuh"
+#include "tcgen05.cuh"
+#include "tiled_impl.cuh"
+
+namespace gbfd {
+bool ctx_view(gbfd_ctx *c, float **origin, Layout *L, int *nf, cudaStream_t *s);
+}
+
+namespace gbfd {
+namespace cnn {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int TAPS = 27;
+constexpr int MT = 128;    // points per tile (MMA M)
+constexpr int NTHR = 128;  // threads per conv CTA (4 warps = 128 TMEM lanes)
+constexpr int NC = 5;      // physical channels (lnrho, u_x, u_y, u_z, s)
+constexpr int C0 = 16;     // padded input channels of layer 1
+constexpr int CH = 32;     // hidden channels
+constexpr int C3 = 16;     // padded output channels of layer 3
+
+enum { EPI_GELU = 0, EPI_LINEAR = 1, EPI_DGELU = 2 };
+
+// Packed FP32 parameters: W[co_pad][tap][ci_pad] then b[co_pad], per layer;
+// padded channel counts per layer: (32, 16), (32, 32), (16, 32).
+__host__ __device__ constexpr int dim_co(int l) { return l == 2 ? C3 : CH; }
+__host__ __device__ constexpr int dim_ci(int l) { return l == 0 ? C0 : CH; }
+
+__host__ __device__ constexpr int wcount(int l) { return dim_co(l) * TAPS * dim_ci(l); }
+__host__ __device__ constexpr int pcount(int l) { return wcount(l) + dim_co(l); }
+__host__ __device__ constexpr int poff(int l)
+{
+    return l == 0 ? 0 : (l == 1 ? pcount(0) : pcount(0) + pcount(1));
+}
+constexpr int kParams = pcount(0) + pcount(1) + pcount(2);
+// real (unpadded) sizes, in the W[o][c][3][3][3] + b[o] order, layers 1..3
+constexpr int kRealOut[3] = {CH, CH, NC};
+constexpr int kRealIn[3] = {NC, CH, CH};
+constexpr int kRealParams = (CH * NC * 27 + CH) + (CH * CH * 27 + CH) + (NC * CH * 27 + NC);
+
+// element index of (row n, col k) of an N x K operand in core-matrix order
+__host__ __device__ inline int core_idx(int n, int k, int K)
+{
+    return (n / 8) * (K * 8) + (k / 8) * 64 + (n % 8) * 8 + (k % 8);
+}
+
+__device__ __forceinline__ float gelu(float h) { return 0.5f * h * (1.0f + erff(h * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad(float h)
+{
+    return 0.5f * (1.0f + erff(h * 0.70710678118654752f)) +
+           h * expf(-0.5f * h * h) * 0.39894228040143268f;
+}
+
+struct ConvArgs {
+    const bf16 *x;       // [npts][CIN] channels-last input
+    const bf16 *wB;      // [N][27*CIN] in core-matrix order
+    const float *bias;   // [N]                      (EPI_GELU, EPI_LINEAR)
+    float *hsave;        // [npts][N] pre-activation (EPI_GELU)
+    bf16 *yb;            // [npts][N]                (EPI_GELU: GELU(h), EPI_DGELU: dh)
+    float *yf;           // [npts][8]                (EPI_LINEAR)
+    const float *hprev;  // [npts][N]                (EPI_DGELU)
+    int n;               // grid side
+    int npts;            // batch * n^3
+    int *dev_error;
+};
+
+template <int CIN, int N, int EPI>
+struct ConvSmem {
+    static constexpr int K = TAPS * CIN;
+    static constexpr int B_BYTES = N * K * 2;
+    static constexpr int STAGE = MT * CIN * 2;
+    static constexpr int A_OFF = (B_BYTES + 1023) / 1024 * 1024;
+    static constexpr int BAR_OFF = A_OFF + 2 * STAGE;
+    static constexpr int BYTES = BAR_OFF + 64;
+};
+
+template <int CIN, int N, int EPI>
+__global__ void __launch_bounds__(NTHR) k_conv_tc(const ConvArgs a)
+{
+    using SM = ConvSmem<CIN, N, EPI>;
+    constexpr int K = SM::K;
+    constexpr int KSTEPS = CIN / 16;  // MMAs per tap
+    constexpr int SBO_A = CIN * 16;
+    constexpr int SBO_B = K * 16;
+    constexpr int CH8 = CIN / 8;      // 16-byte chunks per point
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sB = smem;
+    unsigned char *sA = smem + SM::A_OFF;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::BAR_OFF);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + SM::BAR_OFF + 16);
+
+    for (int i = threadIdx.x; i < SM::B_BYTES / 16; i += NTHR)
+        reinterpret_cast<uint4 *>(sB)[i] = reinterpret_cast<const uint4 *>(a.wB)[i];
+    if (threadIdx.x == 0) {
+        tiled::mbar_init(&bars[0], 1);
+        tiled::mbar_init(&bars[1], 1);
+        tiled::fence_mbar_init();
+    }
+    if (threadIdx.x < 32)
+        tc::tmem_alloc(tslot, 32);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(MT, N);
+    const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
+    uint32_t ph0 = 0, ph1 = 0;
+    const int n = a.n;
+    const int n2 = n * n, n3 = n2 * n;
+    const int ntiles = (a.npts + MT - 1) / MT;
+    bool timeout = false;
+
+#pragma unroll 1
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int p = tile * MT + threadIdx.x;
+        const bool valid = p < a.npts;
+        const int pp = valid ? p : 0;
+        const int b = pp / n3;
+        int r = pp - b * n3;
+        const int z = r / n2;
+        r -= z * n2;
+        const int y = r / n;
+        const int x = r - y * n;
+        uint4 v[CH8];
+        auto gather = [&](int tap) {
+            int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+            zz += zz < 0 ? n : 0;
+            zz -= zz >= n ? n : 0;
+            yy += yy < 0 ? n : 0;
+            yy -= yy >= n ? n : 0;
+            xx += xx < 0 ? n : 0;
+            xx -= xx >= n ? n : 0;
+            const long long q = (long long)b * n3 + ((long long)zz * n + yy) * n + xx;
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.x + q * CIN);
+#pragma unroll
+            for (int c = 0; c < CH8; ++c)
+                v[c] = valid ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
+        };
+        gather(0);
+#pragma unroll 1
+        for (int tap = 0; tap < TAPS; ++tap) {
+            const int st = tap & 1;
+            if (tap >= 2) {
+                if (!tiled::mbar_wait(&bars[st], st ? ph1 : ph0))
+                    timeout = true;
+                if (st)
+                    ph1 ^= 1;
+                else
+                    ph0 ^= 1;
+            }
+            unsigned char *As = sA + st * SM::STAGE;
+            const int t = threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < CH8; ++c)
+                *reinterpret_cast<uint4 *>(As + (t / 8) * SBO_A + c * 128 + (t % 8) * 16) = v[c];
+            if (tap + 1 < TAPS)
+                gather(tap + 1);
+            tc::fence_smem_to_async();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tc::fence_after_sync();
+#pragma unroll
+                for (int s = 0; s < KSTEPS; ++s) {
+                    const uint64_t ad = tc::smem_desc(sA_u32 + st * SM::STAGE + s * 256, 128, SBO_A);
+                    const uint64_t bd = tc::smem_desc(sB_u32 + (tap * KSTEPS + s) * 256, 128, SBO_B);
+                    tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || s > 0) ? 1u : 0u);
+                }
+                tc::commit(&bars[st]);
+            }
+        }
+        // last commits: tap 26 on stage 0, tap 25 on stage 1
+        if (!tiled::mbar_wait(&bars[0], ph0))
+            timeout = true;
+        ph0 ^= 1;
+        if (!tiled::mbar_wait(&bars[1], ph1))
+            timeout = true;
+        ph1 ^= 1;
+        tc::fence_after_sync();
+        float acc[32];
+        const uint32_t taddr = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
+        tc::tmem_ld16(taddr, acc);
+        if (N > 16)
+            tc::tmem_ld16(taddr + 16, acc + 16);
+        if (valid && !timeout) {
+            if (EPI == EPI_GELU) {
+                float4 *hs = reinterpret_cast<float4 *>(a.hsave + (long long)p * N);
+                uint4 *yo = reinterpret_cast<uint4 *>(a.yb + (long long)p * N);
+#pragma unroll
+                for (int c = 0; c < N; c += 8) {
+                    float h[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        h[i] = acc[c + i] + __ldg(a.bias + c + i);
+                    hs[c / 4] = make_float4(h[0], h[1], h[2], h[3]);
+                    hs[c / 4 + 1] = make_float4(h[4], h[5], h[6], h[7]);
+                    __nv_bfloat162 o[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        o[i] = __floats2bfloat162_rn(gelu(h[2 * i]), gelu(h[2 * i + 1]));
+                    yo[c / 8] = *reinterpret_cast<uint4 *>(o);
+                }
+            } else if (EPI == EPI_LINEAR) {
+                float4 *yo = reinterpret_cast<float4 *>(a.yf + (long long)p * 8);
+                yo[0] = make_float4(acc[0] + __ldg(a.bias + 0), acc[1] + __ldg(a.bias + 1),
+                                    acc[2] + __ldg(a.bias + 2), acc[3] + __ldg(a.bias + 3));
+                yo[1] = make_float4(acc[4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
+            } else {
+                const float4 *hp = reinterpret_cast<const float4 *>(a.hprev + (long long)p * N);
+                uint4 *yo = reinterpret_cast<uint4 *>(a.yb + (long long)p * N);
+#pragma unroll
+                for (int c = 0; c < N; c += 8) {
+                    const float4 h0 = __ldg(hp + c / 4), h1 = __ldg(hp + c / 4 + 1);
+                    const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                    __nv_bfloat162 o[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        o[i] = __floats2bfloat162_rn(acc[c + 2 * i] * gelu_grad(h[2 * i]),
+                                                     acc[c + 2 * i + 1] * gelu_grad(h[2 * i + 1]));
+                    yo[c / 8] = *reinterpret_cast<uint4 *>(o);
+                }
+            }
+        }
+        tc::fence_before_sync();
+        if (__syncthreads_or(timeout)) {
+            if (threadIdx.x == 0)
+                atomicExch(a.dev_error, 2);
+            break;
+        }
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x < 32)
+        tc::tmem_dealloc(tmem, 32);
+}
+
+// Weight (and bias) gradient of one layer, summed over this CTA's share of
+// the points: dW[co][tap][ci] += dY[p][co] X[p + tap][ci]; db[co] += dY[p][co].
+template <int CO, int CI>
+__global__ void __launch_bounds__(TAPS *(CI / 4)) k_wgrad(const bf16 *__restrict__ dY,
+                                                          const bf16 *__restrict__ X, int n,
+                                                          int npts, float *__restrict__ part)
+{
+    constexpr int NT = TAPS * (CI / 4);
+    __shared__ __align__(16) bf16 sdy[MT * CO];
+    const int t = threadIdx.x;
+    const int tap = t / (CI / 4), cq = t % (CI / 4);
+    const int dz = tap / 9 - 1, dyo = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int n2 = n * n, n3 = n2 * n;
+    float acc[CO][4];
+    float db[CO];
+#pragma unroll
+    for (int c = 0; c < CO; ++c) {
+        db[c] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            acc[c][i] = 0.f;
+    }
+    const long long chunk = ((long long)npts + gridDim.x - 1) / gridDim.x;
+    const long long p0 = chunk * blockIdx.x;
+    const long long p1 = min((long long)npts, p0 + chunk);
+    for (long long base = p0; base < p1; base += MT) {
+        const int cnt = (int)min((long long)MT, p1 - base);
+        __syncthreads();
+        for (int i = t; i < cnt * CO / 8; i += NT)
+            reinterpret_cast<uint4 *>(sdy)[i] = __ldg(reinterpret_cast<const uint4 *>(dY + base * CO) + i);
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const long long p = base + j;
+            const int b = (int)(p / n3);
+            int r = (int)(p - (long long)b * n3);
+            const int z = r / n2;
+            r -= z * n2;
+            const int y = r / n;
+            const int x = r - y * n;
+            int zz = z + dz, yy = y + dyo, xx = x + dx;
+            zz += zz < 0 ? n : 0;
+            zz -= zz >= n ? n : 0;
+            yy += yy < 0 ? n : 0;
+            yy -= yy >= n ? n : 0;
+            xx += xx < 0 ? n : 0;
+            xx -= xx >= n ? n : 0;
+            const long long q = (long long)b * n3 + ((long long)zz * n + yy) * n + xx;
+            const uint2 xr = __ldg(reinterpret_cast<const uint2 *>(X + q * CI + 4 * cq));
+            const float2 x01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&xr.x));
+            const float2 x23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&xr.y));
+            const float xv[4] = {x01.x, x01.y, x23.x, x23.y};
+#pragma unroll
+            for (int c = 0; c < CO; c += 2) {
+                const float2 d = __bfloat1622float2(
+                    *reinterpret_cast<const __nv_bfloat162 *>(sdy + j * CO + c));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc[c][i] += d.x * xv[i];
+                    acc[c + 1][i] += d.y * xv[i];
+                }
+                db[c] += d.x;
+                db[c + 1] += d.y;
+            }
+        }
+    }
+    float *out = part + (long long)blockIdx.x * (CO * TAPS * CI + CO);
+#pragma unroll
+    for (int c = 0; c < CO; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            out[(c * TAPS + tap) * CI + 4 * cq + i] = acc[c][i];
+    if (t == 0)
+#pragma unroll
+        for (int c = 0; c < CO; ++c)
+            out[CO * TAPS * CI + c] = db[c];
+}
+
+// g[i] = sum over CTAs of part[cta][i], fixed order.
+__global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int count,
+                               float *__restrict__ g)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count)
+        return;
+    float s = 0.f;
+    for (int c = 0; c < nparts; ++c)
+        s += part[(long long)c * count + i];
+    g[i] = s;
+}
+
+// Normalised, channels-last, zero-padded BF16 input of layer 1 from compact
+// FP32 states [batch][5][n^3] (nf physical fields present).
+__global__ void k_input_compact(const float *__restrict__ xs, int nf, int n3, int npts,
+                                const float *__restrict__ mean, const float *__restrict__ stdv,
+                                bf16 *__restrict__ x0)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts)
+        return;
+    const int b = p / n3, r = p - b * n3;
+    __nv_bfloat162 o[8];
+    float v[C0];
+#pragma unroll
+    for (int c = 0; c < C0; ++c)
+        v[c] = (c < nf) ? (xs[((long long)b * NC + c) * n3 + r] - mean[c]) / stdv[c] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        o[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    uint4 *dst = reinterpret_cast<uint4 *>(x0 + (long long)p * C0);
+    dst[0] = reinterpret_cast<uint4 *>(o)[0];
+    dst[1] = reinterpret_cast<uint4 *>(o)[1];
+}
+
+// Same from a solver context's padded FP32 state (one box, batch 1).
+__global__ void k_input_state(const float *__restrict__ st, Layout L, int nf,
+                              const float *__restrict__ mean, const float *__restrict__ stdv,
+                              bf16 *__restrict__ x0)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = L.nx;
+    if (p >= n * n * n)
+        return;
+    const int z = p / (n * n), y = (p / n) % n, x = p % n;
+    __nv_bfloat162 o[8];
+    float v[C0];
+#pragma unroll
+    for (int c = 0; c < C0; ++c)
+        v[c] = (c < nf) ? (st[lidx(L, c, z, y, x)] - mean[c]) / stdv[c] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        o[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    uint4 *dst = reinterpret_cast<uint4 *>(x0 + (long long)p * C0);
+    dst[0] = reinterpret_cast<uint4 *>(o)[0];
+    dst[1] = reinterpret_cast<uint4 *>(o)[1];
+}
+
+// state += std_out * y (the de-normalised predicted residual), ghosts kept.
+__global__ void k_apply(float *__restrict__ st, Layout L, int nf, const float *__restrict__ y,
+                        const float *__restrict__ sout)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = L.nx;
+    if (p >= n * n * n)
+        return;
+    const int z = p / (n * n), yy = (p / n) % n, x = p % n;
+    for (int f = 0; f < nf; ++f) {
+        const float v = st[lidx(L, f, z, yy, x)] + sout[f] * y[(long long)p * 8 + f];
+        store_ghosted(st, L, f, z, yy, x, v);
+    }
+}
+
+// Normalised output [batch][5][n^3] from the layer-3 rows (tests, inference).
+__global__ void k_output_compact(const float *__restrict__ y, int n3, int npts,
+                                 float *__restrict__ out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts)
+        return;
+    const int b = p / n3, r = p - b * n3;
+    for (int c = 0; c < NC; ++c)
+        out[((long long)b * NC + c) * n3 + r] = y[(long long)p * 8 + c];
+}
+
+// MSE of the normalised residual: t = (target - x) / std_out; loss partial
+// sums per block (FP64) and dY3 = 2 (y - t) / count in BF16, channels-last.
+__global__ void k_loss(const float *__restrict__ y, const float *__restrict__ xs,
+                       const float *__restrict__ ts, const float *__restrict__ sout, int nf,
+                       int n3, int npts, float inv_count, bf16 *__restrict__ dy3,
+                       double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (p < npts) {
+        const int b = p / n3, r = p - b * n3;
+        float d[C3];
+#pragma unroll
+        for (int c = 0; c < C3; ++c)
+            d[c] = 0.f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const long long i = ((long long)b * NC + c) * n3 + r;
+            const float t = c < nf ? (ts[i] - xs[i]) / sout[c] : 0.f;
+            const float e = y[(long long)p * 8 + c] - t;
+            l += (double)e * (double)e;
+            d[c] = 2.f * e * inv_count;
+        }
+        __nv_bfloat162 o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            o[i] = __floats2bfloat162_rn(d[2 * i], d[2 * i + 1]);
+        uint4 *dst = reinterpret_cast<uint4 *>(dy3 + (long long)p * C3);
+        dst[0] = reinterpret_cast<uint4 *>(o)[0];
+        dst[1] = reinterpret_cast<uint4 *>(o)[1];
+    }
+    sh[threadIdx.x] = l;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_double(const double *__restrict__ part, int n, double *__restrict__ out)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256)
+        s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k)
+            sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *out = sh[0];
+}
+
+struct PackArgs {
+    float *w, *m, *v;  // FP32 master parameters and Adam moments [kParams]
+    const float *g;    // gradients [kParams] (NULL: pack only)
+    float lr, b1, b2, eps, bc1, bc2;
+    bf16 *fwd[3];      // forward B operands, layer l: [co][27*ci]
+    bf16 *bwd[3];      // input-gradient B operands (layers 2, 3): [ci][27*co]
+    float *bias[3];    // FP32 biases [co]
+};
+
+// Adam step (Kingma & Ba 2015) on the master weights, then the BF16 GEMM
+// copies: forward B[co][tap*CI + ci]; input-gradient B'[ci][(26-tap)*CO + co]
+// (channels transposed, taps flipped).
+__global__ void k_adam_pack(PackArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kParams)
+        return;
+    float w = a.w[i];
+    if (a.g) {
+        const float g = a.g[i];
+        const float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+        const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+        a.m[i] = m;
+        a.v[i] = v;
+        w -= a.lr * (m / a.bc1) / (sqrtf(v / a.bc2) + a.eps);
+        a.w[i] = w;
+    }
+    int l = i < poff(1) ? 0 : (i < poff(2) ? 1 : 2);
+    const int j = i - poff(l);
+    const int CO = dim_co(l), CI = dim_ci(l);
+    if (j >= wcount(l)) {
+        a.bias[l][j - wcount(l)] = w;
+        return;
+    }
+    const int co = j / (TAPS * CI), tap = (j / CI) % TAPS, ci = j % CI;
+    a.fwd[l][core_idx(co, tap * CI + ci, TAPS * CI)] = __float2bfloat16_rn(w);
+    if (l > 0)
+        a.bwd[l][core_idx(ci, (TAPS - 1 - tap) * CO + co, TAPS * CO)] = __float2bfloat16_rn(w);
+}
+
+// Centred box filter: coarse vertex I sits on fine vertex r I; per axis the
+// weights are (1/2, 1, ..., 1, 1/2) / r over fine offsets -r/2..r/2.
+__global__ void k_box_filter(const float *__restrict__ fine, Layout L, int nf, int r,
+                             float *__restrict__ out)
+{
+    const int nc = L.nx / r;
+    const long long nc3 = (long long)nc * nc * nc;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc3 * nf)
+        return;
+    const int f = (int)(i / nc3);
+    const long long q = i - f * nc3;
+    const int Z = (int)(q / ((long long)nc * nc)), Y = (int)((q / nc) % nc), X = (int)(q % nc);
+    const int h = r / 2;
+    double acc = 0.0;
+    for (int a = -h; a <= h; ++a) {
+        const double wa = (a == -h || a == h) ? 0.5 : 1.0;
+        const int z = ((r * Z + a) % L.nz + L.nz) % L.nz;
+        for (int b = -h; b <= h; ++b) {
+            const double wb = (b == -h || b == h) ? 0.5 : 1.0;
+            const int y = ((r * Y + b) % L.ny + L.ny) % L.ny;
+            for (int c = -h; c <= h; ++c) {
+                const double wc = (c == -h || c == h) ? 0.5 : 1.0;
+                const int x = ((r * X + c) % L.nx + L.nx) % L.nx;
+                acc += wa * wb * wc * (double)fine[lidx(L, f, z, y, x)];
+            }
+        }
+    }
+    out[i] = (float)(acc / ((double)r * r * r));
+}
+
+}  // namespace cnn
+}  // namespace gbfd
+
+using namespace gbfd;
+using namespace gbfd::cnn;
+
+struct gbfd_cnn {
+    int n, batch, npts_max;
+    cudaStream_t stream;
+    char *ws;
+    size_t ws_bytes;
+    float *w, *m, *v, *g;
+    bf16 *fwd[3], *bwd[3];
+    float *bias[3];
+    float *norm;  // mean_in[5], std_in[5], std_out[5]
+    bf16 *x0, *a1, *a2, *dy3, *dh2, *dh1;
+    float *h1, *h2, *y3;
+    float *parts;
+    int nparts;
+    double *lparts, *loss;
+    int *derr;
+    int adam_t;
+    int grid_conv;
+    int64_t launches;
+    char err[512];
+};
+
+namespace {
+
+thread_local char g_cnn_err[512];
+
+void cerr(gbfd_cnn *c, const char *fmt, ...)
+{
+    char *buf = c ? c->err : g_cnn_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+}
+
+gbfd_status ccuda(gbfd_cnn *c, cudaError_t e, const char *what)
+{
+    cerr(c, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return GBFD_ERR_CUDA;
+}
+
+size_t al(size_t v) { return (v + 1023) & ~(size_t)1023; }
+
+struct CnnPlan {
+    size_t off[32];
+    size_t total;
+    int nparts;
+};
+
+constexpr int kWgradParts = 296;  // CTAs of the weight-gradient kernels
+
+CnnPlan plan_for(int n, int batch)
+{
+    CnnPlan pl;
+    const size_t np = (size_t)batch * n * n * n;
+    const size_t sizes[] = {
+        kParams * 4, kParams * 4, kParams * 4, kParams * 4,  // w m v g
+        (size_t)CH * TAPS * C0 * 2, (size_t)CH * TAPS * CH * 2, (size_t)C3 * TAPS * CH * 2,  // fwd
+        (size_t)C0 * TAPS * CH * 2, (size_t)CH * TAPS * CH * 2, (size_t)CH * TAPS * C3 * 2,  // bwd
+        CH * 4, CH * 4, C3 * 4, 64 * 4,                                   // biases, norm
+        np * C0 * 2, np * CH * 2, np * CH * 2, np * C3 * 2, np * CH * 2, np * CH * 2,  // bf16 acts
+        np * CH * 4, np * CH * 4, np * 8 * 4,                             // h1 h2 y3
+        (size_t)kWgradParts * (CH * TAPS * CH + CH) * 4,                 // parts
+        ((np + 255) / 256 + 8) * 8, 64, 256};
+    size_t off = 0;
+    const int cnt = sizeof(sizes) / sizeof(sizes[0]);
+    for (int i = 0; i < cnt; ++i) {
+        pl.off[i] = off;
+        off = al(off + sizes[i]);
+    }
+    pl.total = off;
+    pl.nparts = kWgradParts;
+    return pl;
+}
+
+template <int CIN, int N, int EPI>
+cudaError_t conv(gbfd_cnn *c, const ConvArgs &a)
+{
+    using SM = ConvSmem<CIN, N, EPI>;
+    auto k = k_conv_tc<CIN, N, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
+    if (e != cudaSuccess)
+        return e;
+    const int ntiles = (a.npts + MT - 1) / MT;
+    k<<<std::min(ntiles, c->grid_conv), NTHR, SM::BYTES, c->stream>>>(a);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t pack(gbfd_cnn *c, const float *g, float lr)
+{
+    PackArgs a;
+    a.w = c->w;
+    a.m = c->m;
+    a.v = c->v;
+    a.g = g;
+    a.lr = lr;
+    a.b1 = 0.9f;
+    a.b2 = 0.999f;
+    a.eps = 1e-8f;
+    a.bc1 = 1.f - powf(0.9f, (float)c->adam_t);
+    a.bc2 = 1.f - powf(0.999f, (float)c->adam_t);
+    for (int l = 0; l < 3; ++l) {
+        a.fwd[l] = c->fwd[l];
+        a.bwd[l] = c->bwd[l];
+        a.bias[l] = c->bias[l];
+    }
+    k_adam_pack<<<(kParams + 255) / 256, 256, 0, c->stream>>>(a);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// forward of `npts` points whose layer-1 input is already in x0
+cudaError_t forward(gbfd_cnn *c, int npts)
+{
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = c->n;
+    a.npts = npts;
+    a.dev_error = c->derr;
+    a.x = c->x0;
+    a.wB = c->fwd[0];
+    a.bias = c->bias[0];
+    a.hsave = c->h1;
+    a.yb = c->a1;
+    cudaError_t e = conv<C0, CH, EPI_GELU>(c, a);
+    if (e != cudaSuccess)
+        return e;
+    a.x = c->a1;
+    a.wB = c->fwd[1];
+    a.bias = c->bias[1];
+    a.hsave = c->h2;
+    a.yb = c->a2;
+    e = conv<CH, CH, EPI_GELU>(c, a);
+    if (e != cudaSuccess)
+        return e;
+    a.x = c->a2;
+    a.wB = c->fwd[2];
+    a.bias = c->bias[2];
+    a.hsave = nullptr;
+    a.yb = nullptr;
+    a.yf = c->y3;
+    return conv<CH, C3, EPI_LINEAR>(c, a);
+}
+
+template <int CO, int CI>
+cudaError_t wgrad(gbfd_cnn *c, const bf16 *dY, const bf16 *X, int npts, float *g)
+{
+    k_wgrad<CO, CI><<<c->nparts, TAPS * (CI / 4), 0, c->stream>>>(dY, X, c->n, npts, c->parts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const int count = CO * TAPS * CI + CO;
+    k_reduce_parts<<<(count + 255) / 256, 256, 0, c->stream>>>(c->parts, c->nparts, count, g);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+// loss, backward and gradients for `batch` samples (x0 and y3 from forward)
+cudaError_t backward(gbfd_cnn *c, const float *xs, const float *ts, int nf, int batch)
+{
+    const int n3 = c->n * c->n * c->n, npts = batch * n3;
+    const int blocks = (npts + 255) / 256;
+    const float *sout = c->norm + 10;
+    k_loss<<<blocks, 256, 0, c->stream>>>(c->y3, xs, ts, sout, nf, n3, npts,
+                                          1.0f / ((float)NC * npts), c->dy3, c->lparts);
+    k_sum_double<<<1, 256, 0, c->stream>>>(c->lparts, blocks, c->loss);
+    c->launches += 2;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    // layer 3: weight gradient, then input gradient through GELU'(h2)
+    e = wgrad<C3, CH>(c, c->dy3, c->a2, npts, c->g + poff(2));
+    if (e != cudaSuccess)
+        return e;
+    ConvArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = c->n;
+    a.npts = npts;
+    a.dev_error = c->derr;
+    a.x = c->dy3;
+    a.wB = c->bwd[2];
+    a.hprev = c->h2;
+    a.yb = c->dh2;
+    e = conv<C3, CH, EPI_DGELU>(c, a);
+    if (e != cudaSuccess)
+        return e;
+    // layer 2
+    e = wgrad<CH, CH>(c, c->dh2, c->a1, npts, c->g + poff(1));
+    if (e != cudaSuccess)
+        return e;
+    a.x = c->dh2;
+    a.wB = c->bwd[1];
+    a.hprev = c->h1;
+    a.yb = c->dh1;
+    e = conv<CH, CH, EPI_DGELU>(c, a);
+    if (e != cudaSuccess)
+        return e;
+    // layer 1: weight gradient only
+    return wgrad<CH, C0>(c, c->dh1, c->x0, npts, c->g + poff(0));
+}
+
+gbfd_status check(gbfd_cnn *c, int batch)
+{
+    if (!c)
+        return GBFD_ERR_INVALID_ARG;
+    if (batch < 1 || batch > c->batch) {
+        cerr(c, "batch %d outside 1..%d", batch, c->batch);
+        return GBFD_ERR_INVALID_ARG;
+    }
+    return GBFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gbfd_cnn_workspace_bytes(int n, int batch)
+{
+    if (n < 4 || n > 512 || batch < 1 || (long long)batch * n * n * n > (1LL << 30))
+        return 0;
+    return plan_for(n, batch).total;
+}
+
+gbfd_status gbfd_cnn_init(int n, int batch, void *workspace, size_t workspace_bytes, void *stream,
+                          gbfd_cnn **out)
+{
+    if (!out) {
+        cerr(nullptr, "out is NULL");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    const size_t need = gbfd_cnn_workspace_bytes(n, batch);
+    if (need == 0) {
+        cerr(nullptr, "cnn: n must be in 4..512, batch >= 1, batch*n^3 <= 2^30");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    if (!workspace || ((uintptr_t)workspace & 1023) || workspace_bytes < need) {
+        cerr(nullptr, "cnn: workspace must be 1024-byte aligned with >= %zu bytes", need);
+        return GBFD_ERR_WORKSPACE;
+    }
+    gbfd_cnn *c = new (std::nothrow) gbfd_cnn();
+    if (!c) {
+        cerr(nullptr, "out of host memory");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    CnnPlan pl = plan_for(n, batch);
+    c->n = n;
+    c->batch = batch;
+    c->npts_max = batch * n * n * n;
+    c->stream = (cudaStream_t)stream;
+    c->ws = (char *)workspace;
+    c->ws_bytes = workspace_bytes;
+    char *b = c->ws;
+    int k = 0;
+    c->w = (float *)(b + pl.off[k++]);
+    c->m = (float *)(b + pl.off[k++]);
+    c->v = (float *)(b + pl.off[k++]);
+    c->g = (float *)(b + pl.off[k++]);
+    for (int l = 0; l < 3; ++l)
+        c->fwd[l] = (bf16 *)(b + pl.off[k++]);
+    for (int l = 0; l < 3; ++l)
+        c->bwd[l] = (bf16 *)(b + pl.off[k++]);
+    for (int l = 0; l < 3; ++l)
+        c->bias[l] = (float *)(b + pl.off[k++]);
+    c->norm = (float *)(b + pl.off[k++]);
+    c->x0 = (bf16 *)(b + pl.off[k++]);
+    c->a1 = (bf16 *)(b + pl.off[k++]);
+    c->a2 = (bf16 *)(b + pl.off[k++]);
+    c->dy3 = (bf16 *)(b + pl.off[k++]);
+    c->dh2 = (bf16 *)(b + pl.off[k++]);
+    c->dh1 = (bf16 *)(b + pl.off[k++]);
+    c->h1 = (float *)(b + pl.off[k++]);
+    c->h2 = (float *)(b + pl.off[k++]);
+    c->y3 = (float *)(b + pl.off[k++]);
+    c->parts = (float *)(b + pl.off[k++]);
+    c->lparts = (double *)(b + pl.off[k++]);
+    c->loss = (double *)(b + pl.off[k++]);
+    c->derr = (int *)(b + pl.off[k++]);
+    c->nparts = pl.nparts;
+    c->adam_t = 0;
+    c->launches = 0;
+    c->err[0] = 0;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->grid_conv = 3 * (sms > 0 ? sms : 1);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->ws, 0, pl.total, c->stream);
+    // identity normalisation until set
+    std::vector<float> nm(64, 0.f);
+    for (int i = 0; i < 5; ++i)
+        nm[5 + i] = nm[10 + i] = 1.f;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->norm, nm.data(), 64 * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        ccuda(nullptr, e, "cnn init");
+        delete c;
+        return GBFD_ERR_CUDA;
+    }
+    *out = c;
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_cnn_destroy(gbfd_cnn *c)
+{
+    delete c;
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_cnn_set_params(gbfd_cnn *c, const float *params)
+{
+    if (!c || !params) {
+        cerr(c, "cnn set_params: NULL argument");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    std::vector<float> packed(kParams, 0.f);
+    const float *src = params;
+    for (int l = 0; l < 3; ++l) {
+        const int CO = dim_co(l), CI = dim_ci(l);
+        for (int o = 0; o < kRealOut[l]; ++o)
+            for (int ci = 0; ci < kRealIn[l]; ++ci)
+                for (int t = 0; t < TAPS; ++t)
+                    packed[poff(l) + (o * TAPS + t) * CI + ci] = src[(o * kRealIn[l] + ci) * TAPS + t];
+        src += kRealOut[l] * kRealIn[l] * TAPS;
+        for (int o = 0; o < kRealOut[l]; ++o)
+            packed[poff(l) + CO * TAPS * CI + o] = src[o];
+        src += kRealOut[l];
+    }
+    cudaError_t e =
+        cudaMemcpyAsync(c->w, packed.data(), kParams * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->m, 0, kParams * 4, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->v, 0, kParams * 4, c->stream);
+    c->adam_t = 0;
+    if (e == cudaSuccess)
+        e = pack(c, nullptr, 0.f);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? GBFD_OK : ccuda(c, e, "cnn set_params");
+}
+
+// unpack a padded parameter vector (device) into the real-size host layout
+static gbfd_status unpack(gbfd_cnn *c, const float *dev, float *host)
+{
+    std::vector<float> packed(kParams);
+    cudaError_t e =
+        cudaMemcpyAsync(packed.data(), dev, kParams * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return ccuda(c, e, "cnn read parameters");
+    float *dst = host;
+    for (int l = 0; l < 3; ++l) {
+        const int CO = dim_co(l), CI = dim_ci(l);
+        for (int o = 0; o < kRealOut[l]; ++o)
+            for (int ci = 0; ci < kRealIn[l]; ++ci)
+                for (int t = 0; t < TAPS; ++t)
+                    dst[(o * kRealIn[l] + ci) * TAPS + t] = packed[poff(l) + (o * TAPS + t) * CI + ci];
+        dst += kRealOut[l] * kRealIn[l] * TAPS;
+        for (int o = 0; o < kRealOut[l]; ++o)
+            dst[o] = packed[poff(l) + CO * TAPS * CI + o];
+        dst += kRealOut[l];
+    }
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_cnn_get_params(gbfd_cnn *c, float *params)
+{
+    if (!c || !params) {
+        cerr(c, "cnn get_params: NULL argument");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    return unpack(c, c->w, params);
+}
+
+int gbfd_cnn_param_count(void) { return kRealParams; }
+
+gbfd_status gbfd_cnn_set_norm(gbfd_cnn *c, const float *mean_in, const float *std_in,
+                              const float *std_out)
+{
+    if (!c || !mean_in || !std_in || !std_out) {
+        cerr(c, "cnn set_norm: NULL argument");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    float nm[64] = {0};
+    for (int i = 0; i < 5; ++i) {
+        if (!(std_in[i] > 0) || !(std_out[i] > 0)) {
+            cerr(c, "cnn set_norm: standard deviations must be > 0");
+            return GBFD_ERR_INVALID_ARG;
+        }
+        nm[i] = mean_in[i];
+        nm[5 + i] = std_in[i];
+        nm[10 + i] = std_out[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(c->norm, nm, sizeof nm, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? GBFD_OK : ccuda(c, e, "cnn set_norm");
+}
+
+gbfd_status gbfd_cnn_forward(gbfd_cnn *c, const float *xs, int nf, int batch, float *ys)
+{
+    gbfd_status st = check(c, batch);
+    if (st != GBFD_OK)
+        return st;
+    if (!xs || !ys || (nf != 4 && nf != 5)) {
+        cerr(c, "cnn forward: bad arguments");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const int n3 = c->n * c->n * c->n, npts = batch * n3;
+    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, n3, npts, c->norm,
+                                                                c->norm + 5, c->x0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = forward(c, npts);
+    if (e == cudaSuccess) {
+        k_output_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(c->y3, n3, npts, ys);
+        e = cudaGetLastError();
+    }
+    c->launches += 2;
+    return e == cudaSuccess ? GBFD_OK : ccuda(c, e, "cnn forward");
+}
+
+gbfd_status gbfd_cnn_gradients(gbfd_cnn *c, const float *xs, const float *ts, int nf, int batch,
+                               float *grads, double *loss)
+{
+    gbfd_status st = check(c, batch);
+    if (st != GBFD_OK)
+        return st;
+    if (!xs || !ts || (nf != 4 && nf != 5)) {
+        cerr(c, "cnn gradients: bad arguments");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const int n3 = c->n * c->n * c->n, npts = batch * n3;
+    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, n3, npts, c->norm,
+                                                                c->norm + 5, c->x0);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = forward(c, npts);
+    if (e == cudaSuccess)
+        e = backward(c, xs, ts, nf, batch);
+    double l = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&l, c->loss, 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return ccuda(c, e, "cnn gradients");
+    if (loss)
+        *loss = l / ((double)NC * npts);
+    return grads ? unpack(c, c->g, grads) : GBFD_OK;
+}
+
+gbfd_status gbfd_cnn_train_step(gbfd_cnn *c, const float *xs, const float *ts, int nf, int batch,
+                                float lr, double *loss)
+{
+    gbfd_status st = check(c, batch);
+    if (st != GBFD_OK)
+        return st;
+    if (!xs || !ts || (nf != 4 && nf != 5) || !(lr >= 0)) {
+        cerr(c, "cnn train_step: bad arguments");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const int n3 = c->n * c->n * c->n, npts = batch * n3;
+    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, n3, npts, c->norm,
+                                                                c->norm + 5, c->x0);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = forward(c, npts);
+    if (e == cudaSuccess)
+        e = backward(c, xs, ts, nf, batch);
+    c->adam_t++;
+    if (e == cudaSuccess)
+        e = pack(c, c->g, lr);
+    if (e == cudaSuccess && loss) {
+        double l = 0;
+        e = cudaMemcpyAsync(&l, c->loss, 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        *loss = l / ((double)NC * npts);
+    }
+    return e == cudaSuccess ? GBFD_OK : ccuda(c, e, "cnn train_step");
+}
+
+gbfd_status gbfd_cnn_apply(gbfd_cnn *c, gbfd_ctx *ctx)
+{
+    if (!c || !ctx)
+        return GBFD_ERR_INVALID_ARG;
+    float *st = nullptr;
+    Layout L;
+    int nf = 0;
+    cudaStream_t s;
+    if (!ctx_view(ctx, &st, &L, &nf, &s)) {
+        cerr(c, "cnn apply: context must be FP32 with a cubic grid");
+        return GBFD_ERR_UNSUPPORTED;
+    }
+    if (L.nx != c->n) {
+        cerr(c, "cnn apply: grid %d does not match the network's %d", L.nx, c->n);
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const int n3 = c->n * c->n * c->n;
+    // run on the solver's stream so the correction is ordered with its steps
+    const cudaStream_t saved = c->stream;
+    c->stream = s;
+    k_input_state<<<(n3 + 255) / 256, 256, 0, s>>>(st, L, nf, c->norm, c->norm + 5, c->x0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = forward(c, n3);
+    if (e == cudaSuccess) {
+        k_apply<<<(n3 + 255) / 256, 256, 0, s>>>(st, L, nf, c->y3, c->norm + 10);
+        e = cudaGetLastError();
+    }
+    c->stream = saved;
+    c->launches += 2;
+    return e == cudaSuccess ? GBFD_OK : ccuda(c, e, "cnn apply");
+}
+
+gbfd_status gbfd_step_corrected(gbfd_ctx *ctx, gbfd_cnn *c, double dt, int nsteps)
+{
+    if (!ctx || !c || nsteps < 0)
+        return GBFD_ERR_INVALID_ARG;
+    for (int i = 0; i < nsteps; ++i) {
+        gbfd_status st = gbfd_rk3_step(ctx, dt, 1);
+        if (st != GBFD_OK)
+            return st;
+        st = gbfd_cnn_apply(c, ctx);
+        if (st != GBFD_OK)
+            return st;
+    }
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_box_filter(gbfd_ctx *fine, int r, float *out)
+{
+    float *st = nullptr;
+    Layout L;
+    int nf = 0;
+    cudaStream_t s;
+    if (!fine || !out || r < 2 || r % 2)
+        return GBFD_ERR_INVALID_ARG;
+    if (!ctx_view(fine, &st, &L, &nf, &s) || L.nx % r)
+        return GBFD_ERR_UNSUPPORTED;
+    const int nc = L.nx / r;
+    const long long cnt = (long long)nc * nc * nc * nf;
+    k_box_filter<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(st, L, nf, r, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBFD_OK : GBFD_ERR_CUDA;
+}
+
+int64_t gbfd_cnn_launch_count(const gbfd_cnn *c) { return c ? c->launches : 0; }
+
+const char *gbfd_cnn_last_error(const gbfd_cnn *c) { return c ? c->err : g_cnn_err; }
+
+}  // extern "C"

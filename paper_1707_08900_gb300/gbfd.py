@@ -34,7 +34,12 @@ EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state"
            "gbfd_batch_workspace_bytes", "gbfd_batch_init", "gbfd_batch_destroy",
            "gbfd_batch_set_state", "gbfd_batch_get_state", "gbfd_batch_step",
            "gbfd_batch_diagnostics", "gbfd_batch_sync", "gbfd_batch_set_option",
-           "gbfd_batch_autotune", "gbfd_batch_launch_count", "gbfd_batch_last_error")
+           "gbfd_batch_autotune", "gbfd_batch_launch_count", "gbfd_batch_last_error",
+           "gbfd_cnn_workspace_bytes", "gbfd_cnn_init", "gbfd_cnn_destroy",
+           "gbfd_cnn_param_count", "gbfd_cnn_set_params", "gbfd_cnn_get_params",
+           "gbfd_cnn_set_norm", "gbfd_cnn_forward", "gbfd_cnn_gradients",
+           "gbfd_cnn_train_step", "gbfd_cnn_apply", "gbfd_step_corrected", "gbfd_box_filter",
+           "gbfd_cnn_launch_count", "gbfd_cnn_last_error")
 GBFD_BATCH_OPT_GRAPH, GBFD_BATCH_OPT_ZCHUNK, GBFD_BATCH_OPT_GRID = 1, 2, 3
 
 
@@ -122,6 +127,27 @@ def load(path=None):
     L.gbfd_batch_launch_count.argtypes = [_VP]
     L.gbfd_batch_last_error.restype = ctypes.c_char_p
     L.gbfd_batch_last_error.argtypes = [_VP]
+    _FP = ctypes.POINTER(ctypes.c_float)
+    L.gbfd_cnn_workspace_bytes.restype = ctypes.c_size_t
+    L.gbfd_cnn_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.gbfd_cnn_init.argtypes = [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t, _VP,
+                                ctypes.POINTER(_VP)]
+    L.gbfd_cnn_destroy.argtypes = [_VP]
+    L.gbfd_cnn_param_count.argtypes = []
+    L.gbfd_cnn_set_params.argtypes = [_VP, _FP]
+    L.gbfd_cnn_get_params.argtypes = [_VP, _FP]
+    L.gbfd_cnn_set_norm.argtypes = [_VP, _FP, _FP, _FP]
+    L.gbfd_cnn_forward.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP]
+    L.gbfd_cnn_gradients.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _FP, _DP]
+    L.gbfd_cnn_train_step.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                      _DP]
+    L.gbfd_cnn_apply.argtypes = [_VP, _VP]
+    L.gbfd_step_corrected.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_int]
+    L.gbfd_box_filter.argtypes = [_VP, ctypes.c_int, _VP]
+    L.gbfd_cnn_launch_count.restype = ctypes.c_int64
+    L.gbfd_cnn_launch_count.argtypes = [_VP]
+    L.gbfd_cnn_last_error.restype = ctypes.c_char_p
+    L.gbfd_cnn_last_error.argtypes = [_VP]
     L.gbfd_status_string.restype = ctypes.c_char_p
     L.gbfd_status_string.argtypes = [ctypes.c_int]
     for name in EXPORTS:
@@ -405,3 +431,136 @@ class Batch:
 
     def launches(self):
         return load().gbfd_batch_launch_count(self.b)
+
+
+# ------------------------------------------------------------ correction network
+
+def _ccheck(status, c=None):
+    if status != GBFD_OK:
+        raise GbfdError(status, load().gbfd_cnn_last_error(c).decode(errors="replace"))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class CNN:
+    """The coarse-grid correction network (see include/gbfd.h) on an n^3 grid,
+    training on up to `batch` samples at a time.  State tensors are torch
+    CUDA float32 [batch, 5, n, n, n]."""
+
+    def __init__(self, n, batch=1, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("gbfd needs a CUDA device; there is no CPU path")
+        L = load()
+        self.torch = torch
+        self.n = int(n)
+        self.batch = int(batch)
+        nbytes = L.gbfd_cnn_workspace_bytes(self.n, self.batch)
+        if nbytes == 0:
+            raise GbfdError(1, "invalid network grid / batch")
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes + 1024, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 1023) // 1024 * 1024
+        self.c = _VP()
+        _ccheck(L.gbfd_cnn_init(self.n, self.batch, _VP(aligned), nbytes,
+                                _VP(self.stream.cuda_stream), ctypes.byref(self.c)))
+        self.nparams = L.gbfd_cnn_param_count()
+
+    def close(self):
+        if getattr(self, "c", None):
+            load().gbfd_cnn_destroy(self.c)
+            self.c = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def flatten(p):
+        """Oracle-style dict {W1,b1,W2,b2,W3,b3} -> ABI parameter vector."""
+        return np.concatenate([np.asarray(p[k], dtype=np.float64).ravel()
+                               for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+
+    @staticmethod
+    def unflatten(v, hidden=32, cin=5, cout=5):
+        shapes = [("W1", (hidden, cin, 3, 3, 3)), ("b1", (hidden,)),
+                  ("W2", (hidden, hidden, 3, 3, 3)), ("b2", (hidden,)),
+                  ("W3", (cout, hidden, 3, 3, 3)), ("b3", (cout,))]
+        out, i = {}, 0
+        for k, sh in shapes:
+            m = int(np.prod(sh))
+            out[k] = np.asarray(v[i:i + m], dtype=np.float64).reshape(sh)
+            i += m
+        return out
+
+    def set_params(self, p):
+        v = np.ascontiguousarray(p if isinstance(p, np.ndarray) else self.flatten(p),
+                                 dtype=np.float32)
+        assert v.size == self.nparams
+        _ccheck(load().gbfd_cnn_set_params(self.c, _fptr(v)), self.c)
+
+    def get_params(self):
+        v = np.empty(self.nparams, dtype=np.float32)
+        _ccheck(load().gbfd_cnn_get_params(self.c, _fptr(v)), self.c)
+        return v
+
+    def set_norm(self, mean_in, std_in, std_out):
+        a = [np.ascontiguousarray(x, dtype=np.float32) for x in (mean_in, std_in, std_out)]
+        _ccheck(load().gbfd_cnn_set_norm(self.c, *[_fptr(x) for x in a]), self.c)
+
+    def _dev(self, x):
+        x = x.contiguous()
+        assert x.is_cuda and x.dtype == self.torch.float32 and x.shape[1] == 5
+        return x
+
+    def forward(self, xs, nf=5):
+        xs = self._dev(xs)
+        ys = self.torch.empty_like(xs)
+        _ccheck(load().gbfd_cnn_forward(self.c, _VP(xs.data_ptr()), nf, xs.shape[0],
+                                        _VP(ys.data_ptr())), self.c)
+        return ys
+
+    def gradients(self, xs, ts, nf=5):
+        xs, ts = self._dev(xs), self._dev(ts)
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        _ccheck(load().gbfd_cnn_gradients(self.c, _VP(xs.data_ptr()), _VP(ts.data_ptr()), nf,
+                                          xs.shape[0], _fptr(g), ctypes.byref(loss)), self.c)
+        return g, loss.value
+
+    def train_step(self, xs, ts, lr, nf=5, want_loss=True):
+        xs, ts = self._dev(xs), self._dev(ts)
+        loss = ctypes.c_double()
+        _ccheck(load().gbfd_cnn_train_step(self.c, _VP(xs.data_ptr()), _VP(ts.data_ptr()), nf,
+                                           xs.shape[0], float(lr),
+                                           ctypes.byref(loss) if want_loss else None), self.c)
+        return loss.value if want_loss else None
+
+    def apply(self, solver):
+        _ccheck(load().gbfd_cnn_apply(self.c, solver.ctx), self.c)
+
+    def step_corrected(self, solver, dt, nsteps=1):
+        _ccheck(load().gbfd_step_corrected(solver.ctx, self.c, float(dt), int(nsteps)), self.c)
+
+    def launches(self):
+        return load().gbfd_cnn_launch_count(self.c)
+
+
+def box_filter(solver, r=4):
+    """Centred box filter of a cubic FP32 solver's state to an r times coarser
+    grid; returns a torch CUDA float32 tensor [nf, nc, nc, nc]."""
+    torch = solver.torch
+    n = solver.shape[0]
+    out = torch.empty((solver.nfields, n // r, n // r, n // r), dtype=torch.float32,
+                      device=solver.device)
+    st = load().gbfd_box_filter(solver.ctx, int(r), _VP(out.data_ptr()))
+    if st != GBFD_OK:
+        raise GbfdError(st, "box filter needs a cubic FP32 context with n % r == 0")
+    return out
