@@ -169,6 +169,24 @@ def flush_l2(buf):
     buf.zero_()
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(v, world, dist=None, device=None):
+    """Max of a per-rank scalar over all ranks (the slowest rank's time)."""
+    if world == 1:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank, steps, ms_max, world):
+    """Updates/s of the whole job: every rank advances its own box (weak
+    scaling), the job takes as long as its slowest rank."""
+    return world * points_per_rank * steps / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ our arm
 
 def timed_steps(s, dt, steps, stream, torch):
@@ -205,12 +223,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_(v):
+        return max_over_ranks(v, world, dist, dev)
 
     stream = torch.cuda.current_stream(dev)
     peak_gbs, peak_kind, peaks = measured_peaks()
@@ -240,8 +254,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop(t0, t1) if rank == 0 else None
-    ms_max = max_over_ranks(ms)
-    value = world * npts * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks_(ms)
+    value = whole_job_rate(npts, args.steps, ms_max, world)
     avg_launch_s = ms * 1e-3 / launches
     alg_per_launch = npts * ALG_BYTES_55[4] / 3.0
     achieved = alg_per_launch / avg_launch_s / 1e9
@@ -262,7 +276,7 @@ def run_ours(args):
     s.rk3_step(dt, 2)
     torch.cuda.synchronize()
     ms64, l64 = timed_steps(s, dt, k64, stream, torch)
-    v64 = npts * k64 / (max_over_ranks(ms64) * 1e-3)  # per GPU
+    v64 = npts * k64 / (max_over_ranks_(ms64) * 1e-3)  # per GPU
     tflops64 = v64 * 3 * FLOPS_55_SUBSTEP / 1e12
     extra["fp64_55p"] = {
         "value": world * v64, "steps": k64, "ms_per_step": ms64 / k64,
@@ -281,7 +295,7 @@ def run_ours(args):
     s.rk3_step(dt, 2)
     torch.cuda.synchronize()
     ms19, l19 = timed_steps(s, dt, k19, stream, torch)
-    v19 = npts * k19 / (max_over_ranks(ms19) * 1e-3)
+    v19 = npts * k19 / (max_over_ranks_(ms19) * 1e-3)
     extra["fp32_19p"] = {
         "value": world * v19, "steps": k19, "ms_per_step": ms19 / k19,
         "hbm_frac_own_ideal": round(npts * ALG_VALUES_19 * 4 / (ms19 / k19 * 1e-3) / 1e9
@@ -297,7 +311,7 @@ def run_ours(args):
     s.rk3_step(dt, 2)
     torch.cuda.synchronize()
     msa, _ = timed_steps(s, dt, kacc, stream, torch)
-    extra["fp32_acc64_55p"] = {"value": world * npts * kacc / (max_over_ranks(msa) * 1e-3),
+    extra["fp32_acc64_55p"] = {"value": world * npts * kacc / (max_over_ranks_(msa) * 1e-3),
                                "steps": kacc, "ms_per_step": msa / kacc}
     s.close()
 
@@ -326,7 +340,7 @@ def run_ours(args):
     bat.step(bdt, bsteps)
     e1.record(stream)
     e1.synchronize()
-    bms = max_over_ranks(e0.elapsed_time(e1))
+    bms = max_over_ranks_(e0.elapsed_time(e1))
     bpts = sum(n ** 3 for n in bns)
     extra["fp32_batched_96"] = {
         "value": world * bpts * bsteps / (bms * 1e-3), "steps": bsteps, "ms_per_step": bms / bsteps,
@@ -335,6 +349,43 @@ def run_ours(args):
         "hbm_frac": round(bpts * ALG_BYTES_55[4] / (bms / bsteps * 1e-3) / 1e9 / peak_gbs, 4),
     }
     bat.close()
+
+    # ---- learned coarse-grid form: 64^3 FP32 coarse step plain vs with the
+    # correction network (3 tcgen05 implicit-GEMM convolutions after every
+    # RK3 step); timing only (accuracy comes from the training runs)
+    from paper_1707_08900_gb300 import learned
+    nc = 64
+    cst = inputs.spectrum((nc,) * 3, 1200 + rank, p=-2.0, k1=1, k2=8, mach=0.1,
+                          lnrho_rms=1e-3).astype(np.float32)
+    cs_ = gbfd.Solver((nc,) * 3, precision="fp32", nu=5e-3, device=dev, stream=stream)
+    cs_.set_state(cst)
+    cdt = cs_.cfl_dt(0.4)
+    net = gbfd.CNN(nc, batch=1, device=dev, stream=stream)
+    net.set_params(learned.init_params(0))
+    csteps = max(10, args.steps // 10)
+    cs_.rk3_step(cdt, 3)
+    net.step_corrected(cs_, cdt, 3)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    cs_.rk3_step(cdt, csteps)
+    ev[1].record(stream)
+    net.step_corrected(cs_, cdt, csteps)
+    ev[2].record(stream)
+    ev[2].synchronize()
+    ms_plain = max_over_ranks_(ev[0].elapsed_time(ev[1])) / csteps
+    ms_corr = max_over_ranks_(ev[1].elapsed_time(ev[2])) / csteps
+    # tensor-core work of one network application: 2 M K N flop per conv
+    # (K = 27 x padded input channels, N = padded output channels)
+    cnn_flop = 2 * nc ** 3 * (27 * 16 * 32 + 27 * 32 * 32 + 27 * 32 * 16)
+    extra["fp32_learned_64"] = {
+        "plain_ms_per_step": ms_plain, "corrected_ms_per_step": ms_corr,
+        "network_ms_per_application": ms_corr - ms_plain,
+        "network_tensor_tflops": cnn_flop / ((ms_corr - ms_plain) * 1e-3) / 1e12,
+        "value_corrected": world * nc ** 3 / (ms_corr * 1e-3), "steps": csteps,
+    }
+    net.close()
+    cs_.close()
 
     # ---- end to end through the public API with pinned host buffers:
     # every step copies the state in (H2D), advances one RK3 step and reads
@@ -355,7 +406,7 @@ def run_ours(args):
         gbfd.gbfd_rk3_step(s.ctx, dt, 1)
         gbfd.gbfd_get_state(s.ctx, host_out.data_ptr(), 0, 0)  # synchronises
     te = time.perf_counter() - te0
-    te = max_over_ranks(te)
+    te = max_over_ranks_(te)
     state_bytes = host_in.numel() * host_in.element_size()
     e2e = {"value": world * npts * ke / te, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": state_bytes, "steps": ke,

@@ -171,7 +171,12 @@ gbfd_status gbfd_diagnostics_noalloc(const void *state, int state_is_fp64, int n
  * memory, the default), 1 = simple one-thread-per-point kernels reading
  * global memory.  GBFD_OPT_TILE_CONFIG: index into the tiled kernels' tile
  * table, -1 = built-in default.  Out-of-range values -> INVALID_ARG. */
-enum { GBFD_OPT_KERNEL_PATH = 1, GBFD_OPT_TILE_CONFIG = 2 };
+enum { GBFD_OPT_KERNEL_PATH = 1, GBFD_OPT_TILE_CONFIG = 2, GBFD_OPT_FAULT_SKIP_COPY = 3 };
+/* GBFD_OPT_FAULT_SKIP_COPY (tests only): value j >= 0 makes the first CTA of
+ * the two-points-per-thread tiled kernel skip the TMA copy of its local plane
+ * j, so its bounded mbarrier wait gives up after about 2 s, the launch ends
+ * early and gbfd_sync reports GBFD_ERR_TIMEOUT with the context still
+ * usable; -1 (the default) turns it off. */
 gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value);
 
 /* Tile autotuner (no counterpart in the paper; the paper tuned block shapes

@@ -38,6 +38,7 @@ struct gbfd_ctx {
     int64_t launches;
     int kernel_path;  // 0 = tiled when supported, 1 = simple
     int tile_cfg;     // index into the tiled kernel's tile table (-1 = default)
+    int fault_skip;   // test-only fault injection (-1 = off)
     TmapCache tmaps;  // encoded TMA descriptors of the two state buffers
     bool broken;
     Coef<double> c64;
@@ -234,6 +235,7 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
 {
     StateBufs b = bufs(c);
     RKStage st = make_stage(s, dt, c->p.nu);
+    st.fault_skip_plane = c->fault_skip;
     int n = 0;
     cudaError_t e = cudaSuccess;
     const bool tiled = c->kernel_path == 0;
@@ -361,6 +363,7 @@ gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_by
     c->launches = 0;
     c->kernel_path = 0;
     c->tile_cfg = -1;
+    c->fault_skip = -1;
     memset(&c->tmaps, 0, sizeof c->tmaps);
     c->broken = false;
     const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
@@ -394,6 +397,11 @@ gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value)
         if (value != 0 && value != 1)
             break;
         ctx->kernel_path = (int)value;
+        return GBFD_OK;
+    case GBFD_OPT_FAULT_SKIP_COPY:
+        if (value < -1 || value > 1000000)
+            break;
+        ctx->fault_skip = (int)value;
         return GBFD_OK;
     case GBFD_OPT_TILE_CONFIG:
         if (value < -1 || value >= tiled_config_count(ctx->sbytes))

@@ -13,6 +13,9 @@ struct RKStage {
     int last;    // substep 3: w is dead afterwards (the next step's substep 1
                  // ignores it), so it is not written
     int s;       // 0, 1, 2
+    int fault_skip_plane;  // test only: CTA 0 of the tiled kernel never copies
+                           // this local plane (-1: off); its bounded wait must
+                           // give up and report GBFD_ERR_TIMEOUT
 };
 
 inline RKStage make_stage(int s, double dt, double nu)
@@ -24,6 +27,7 @@ inline RKStage make_stage(int s, double dt, double nu)
     st.nu3 = nu / 3.0;
     st.first = (s == 0);
     st.last = (s == 2);
+    st.fault_skip_plane = -1;
     st.s = s;
     return st;
 }

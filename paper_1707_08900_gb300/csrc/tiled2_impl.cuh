@@ -88,7 +88,8 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                                            const TA beta, const TA dt, const bool first,
                                            const bool last, const int x0, const int y0,
                                            const int z0, const int nout, int &jrun, int &wrun,
-                                           unsigned char *smem, int *dev_error)
+                                           unsigned char *smem, int *dev_error,
+                                           const int skip_plane = -1)
 {
     using RG = Ring<TS, TW, NF, TX, TY, NS>;
     using tiled::mbar_wait;
@@ -118,6 +119,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     // jrun + j of this CTA: slot (jrun + j) % NS, phase (jrun + j) / NS
     int issued = 0, wissued = 0;
     auto issue = [&](int j) {
+        // fault injection for the bounded-wait test: never copy this plane
+        if (j == skip_plane)
+            return;
         int z = z0 - R + j;
         z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
         const int slot = (jrun + j) % NS;
@@ -512,7 +516,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
     const Layout Lw, const Coef<TS> c, const RKStage st, const int zc, const int tiles_x,
-    int *__restrict__ dev_error)
+    int *__restrict__ dev_error, const int skip_plane)
 {
     using RG = Ring<TS, TW, NF, TX, TY, NS>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -525,7 +529,8 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
     run_column<TS, TW, TA, NF, MIXED, TX, TY, NS>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
                                                   (TA)st.alpha, (TA)st.beta, (TA)st.dt,
                                                   st.first != 0, st.last != 0, x0, y0, z0, nout,
-                                                  jrun, wrun, smem, dev_error);
+                                                  jrun, wrun, smem, dev_error,
+                                                  blockIdx.x == 0 && blockIdx.y == 0 ? skip_plane : -1);
 }
 
 }  // namespace tiled2
@@ -535,6 +540,7 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
                            int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
 {
+    const int skip_plane = st.fault_skip_plane;
     CUtensorMap *map = nullptr, *wmap = nullptr;
     if (!get_state_tmap(cache, b.in, b.Ls, nf, TX, TY, cfg_key, &map))
         return cudaErrorInvalidValue;
@@ -556,7 +562,7 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \
         kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, divf, b.Ls, b.Lw, c, st, zc,       \
-                                          tiles_x, dev_error);                                    \
+                                          tiles_x, dev_error, skip_plane);                        \
     } while (0)
     if (form == 0) {
         if (nf == 5)

@@ -1,0 +1,47 @@
+"""Failure detection on the GPU without a GPU fault: a test-only option makes
+the first CTA of the tiled kernel skip one TMA copy, so its mbarrier wait
+runs out (bounded, about 2 s).  The kernel must record the failure and
+leave; gbfd_sync must report GBFD_ERR_TIMEOUT; the context must stay usable
+and give correct results once the option is cleared."""
+import numpy as np
+import pytest
+
+from oracle import fd
+from paper_1707_08900_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1707_08900_gb300 import build
+    build.build()
+
+
+def test_bounded_wait_times_out_and_context_recovers():
+    from paper_1707_08900_gb300 import gbfd
+    shape = (16, 16, 32)
+    st = inputs.spectrum(shape, 12, mach=0.1, lnrho_rms=1e-3).astype(np.float32)
+    s = gbfd.Solver(shape, precision="fp32", nu=5e-3)
+    s.set_state(st)
+    s.set_option(gbfd.GBFD_OPT_FAULT_SKIP_COPY, 8)
+    s.substep(0, 0.01)
+    with pytest.raises(gbfd.GbfdError) as err:
+        s.sync()
+    assert err.value.status == 4  # GBFD_ERR_TIMEOUT
+    s.set_option(gbfd.GBFD_OPT_FAULT_SKIP_COPY, -1)
+    s.sync()  # the error word was cleared
+    s.set_state(st)
+    s.rk3_step(0.01, 1)
+    s.sync()
+    got = s.get_state()
+    g = fd.Grid(32, 16, 16)
+    ref = fd.rk3_step(st.astype(np.float64), 0.01, g, fd.Physics(cs=1.0, nu=5e-3))
+    err = [np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-30)
+           for a, b in zip(got[:4], ref[:4])]
+    assert max(err) < 1e-5
+    s.close()
