@@ -24,9 +24,13 @@ only the shear wave and the explosion shell):
   / (2 d^2)) e_r about the box centre (Sect. 6; the printed exponent lacks
   its minus sign).
 """
+import os
+
 import numpy as np
+import scipy.fft
 
 TWO_PI = 2.0 * np.pi
+_WORKERS = os.cpu_count() or 1
 
 
 def coords(n, length):
@@ -89,7 +93,7 @@ def _shell_field(rng, shape, p, k1, k2):
     shell = (kk >= k1) & (kk <= k2)
     amp = np.zeros(rshape)
     amp[shell] = kk[shell] ** ((p - 2.0) / 2.0)
-    return np.fft.irfftn((re + 1j * im) * amp, s=shape, axes=(0, 1, 2))
+    return scipy.fft.irfftn((re + 1j * im) * amp, s=shape, axes=(0, 1, 2), workers=_WORKERS)
 
 
 def spectrum(shape, seed, p=-2.0, k1=1.0, k2=8.0, mach=0.1, cs=1.0, lnrho_rms=1e-3,

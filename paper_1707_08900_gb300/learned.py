@@ -13,7 +13,11 @@ Recipe (the paper has no learned component; these are the readings used):
 * a training pair: the filtered fine state c_t advanced one coarse step by
   the coarse solver (x), and the filtered fine state one coarse step later
   (t); the network learns (t - x) / std_out from (x - mean_in) / std_in;
-* Adam, lr 1e-3, mini-batches drawn without replacement each epoch;
+* Adam with a cosine learning-rate decay from lr to lr/10, mini-batches
+  drawn without replacement each epoch; each input is perturbed by Gaussian
+  noise of `noise` x std_out per channel, and the target residual is taken
+  from the perturbed input, so the network also learns to remove error that
+  earlier corrected steps left behind (this keeps long rollouts stable);
 * evaluation: from the filtered initial state, the plain coarse solver and
   the corrected one (RK3 step + network after every step) against the
   filtered fine run, relative L2 of velocity and lnrho, and wall times of
@@ -84,9 +88,15 @@ def init_params(seed, hidden=32):
     return p
 
 
-def train(net, xs, ts, steps, batch, lr=1e-3, seed=0, log_every=50):
+def train(net, xs, ts, steps, batch, lr=3e-4, seed=0, log_every=50, noise=0.0, std_out=None):
     import torch
     rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=xs.device)
+    gen.manual_seed(seed)
+    scale = None
+    if noise > 0:
+        scale = torch.as_tensor(noise * np.asarray(std_out), dtype=torch.float32,
+                                device=xs.device).view(1, -1, 1, 1, 1)
     S = xs.shape[0]
     order = rng.permutation(S)
     pos = 0
@@ -98,7 +108,11 @@ def train(net, xs, ts, steps, batch, lr=1e-3, seed=0, log_every=50):
         idx = torch.as_tensor(order[pos:pos + batch], device=xs.device)
         pos += batch
         want = (it % log_every == 0) or (it == steps - 1)
-        loss = net.train_step(xs.index_select(0, idx), ts.index_select(0, idx), lr, want_loss=want)
+        lr_t = lr * (0.1 + 0.9 * 0.5 * (1.0 + np.cos(np.pi * it / max(steps - 1, 1))))
+        xb = xs.index_select(0, idx)
+        if scale is not None:
+            xb = xb + scale * torch.randn(xb.shape, generator=gen, device=xb.device)
+        loss = net.train_step(xb, ts.index_select(0, idx), lr_t, want_loss=want)
         if want:
             hist.append((it, loss))
     return hist
@@ -164,7 +178,7 @@ def evaluate(net, seeds, n_fine, ratio, nsteps, nu=5e-3, k2=8, mach_range=(0.1, 
 
 
 def run(fine=256, ratio=4, train_seeds=200, eval_seeds=20, nsnap=10, gap=None, steps=200,
-        train_steps=2000, batch=8, lr=1e-3, nu=5e-3, k2=8, seed=0, check_every=50):
+        train_steps=4000, batch=8, lr=3e-4, nu=5e-3, k2=8, seed=0, check_every=25, noise=1.0):
     """The full pipeline; returns a JSON-able summary."""
     import torch
     nc = fine // ratio
@@ -177,17 +191,22 @@ def run(fine=256, ratio=4, train_seeds=200, eval_seeds=20, nsnap=10, gap=None, s
     net.set_params(init_params(seed))
     net.set_norm(mean_in, std_in, std_out)
     t0 = time.perf_counter()
-    hist = train(net, xs, ts, train_steps, batch, lr, seed)
+    hist = train(net, xs, ts, train_steps, batch, lr, seed, noise=noise, std_out=std_out)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    # one-step objective on the whole training set, after training
+    full = []
+    for i in range(0, xs.shape[0] - batch + 1, batch):
+        full.append(net.gradients(xs[i:i + batch], ts[i:i + batch])[1])
     ev = evaluate(net, range(1200, 1200 + eval_seeds), fine, ratio, steps, nu, k2,
                   check_every=check_every)
     mean = lambda v: float(np.mean(v)) if v else None
     return {
         "fine": fine, "coarse": nc, "ratio": ratio, "train_pairs": int(xs.shape[0]),
         "train_seeds": train_seeds, "eval_seeds": eval_seeds, "coarse_steps": steps,
-        "train_steps": train_steps, "batch": batch, "lr": lr,
+        "train_steps": train_steps, "batch": batch, "lr": lr, "input_noise": noise,
         "loss_first": hist[0][1], "loss_last": hist[-1][1], "loss_history": hist,
+        "train_loss_final_mean": float(np.mean(full)) if full else None,
         "seconds_data": t_data, "seconds_train": t_train,
         "rel_l2_u_plain": mean(ev["plain_u"]), "rel_l2_u_corrected": mean(ev["corrected_u"]),
         "rel_l2_lnrho_plain": mean(ev["plain_lnrho"]),
@@ -205,15 +224,17 @@ def main():
     ap.add_argument("--eval-seeds", type=int, default=20)
     ap.add_argument("--nsnap", type=int, default=10)
     ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=3e-4)
+    ap.add_argument("--k2", type=int, default=8)
+    ap.add_argument("--noise", type=float, default=1.0)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     from . import build
     build.build()
     res = run(a.fine, a.ratio, a.train_seeds, a.eval_seeds, a.nsnap, None, a.steps,
-              a.train_steps, a.batch, a.lr)
+              a.train_steps, a.batch, a.lr, k2=a.k2, noise=a.noise)
     text = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:
