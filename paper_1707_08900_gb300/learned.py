@@ -190,14 +190,17 @@ def run(fine=256, ratio=4, train_seeds=200, eval_seeds=20, nsnap=10, gap=None, s
     net = gbfd.CNN(nc, batch=batch)
     net.set_params(init_params(seed))
     net.set_norm(mean_in, std_in, std_out)
+
+    def set_loss():  # one-step objective over the whole training set, noise-free
+        return float(np.mean([net.gradients(xs[i:i + batch], ts[i:i + batch])[1]
+                              for i in range(0, xs.shape[0] - batch + 1, batch)]))
+
+    loss0 = set_loss()
     t0 = time.perf_counter()
     hist = train(net, xs, ts, train_steps, batch, lr, seed, noise=noise, std_out=std_out)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    # one-step objective on the whole training set, after training
-    full = []
-    for i in range(0, xs.shape[0] - batch + 1, batch):
-        full.append(net.gradients(xs[i:i + batch], ts[i:i + batch])[1])
+    loss1 = set_loss()
     ev = evaluate(net, range(1200, 1200 + eval_seeds), fine, ratio, steps, nu, k2,
                   check_every=check_every)
     mean = lambda v: float(np.mean(v)) if v else None
@@ -206,7 +209,7 @@ def run(fine=256, ratio=4, train_seeds=200, eval_seeds=20, nsnap=10, gap=None, s
         "train_seeds": train_seeds, "eval_seeds": eval_seeds, "coarse_steps": steps,
         "train_steps": train_steps, "batch": batch, "lr": lr, "input_noise": noise,
         "loss_first": hist[0][1], "loss_last": hist[-1][1], "loss_history": hist,
-        "train_loss_final_mean": float(np.mean(full)) if full else None,
+        "train_loss_initial_mean": loss0, "train_loss_final_mean": loss1,
         "seconds_data": t_data, "seconds_train": t_train,
         "rel_l2_u_plain": mean(ev["plain_u"]), "rel_l2_u_corrected": mean(ev["corrected_u"]),
         "rel_l2_lnrho_plain": mean(ev["plain_lnrho"]),
