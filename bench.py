@@ -264,7 +264,7 @@ def run_ours(args):
                 "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": "k_substep_px2<float,5,55p,32x8> (3 launches per step)",
+                "kernel": "k_substep_px2<float,5,55p,32x8,packed> (3 launches per step)",
                 "alg_bytes_per_launch": alg_per_launch,
                 "frac_of_8TBs_nominal": round(achieved / 8000.0, 4)}
     s.close()
@@ -428,7 +428,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": "256^3", "form": "55-point fused",
-                   "precision": "fp32", "fields": NF, "tile": "default (32x8, two points per thread, zc 32)",
+                   "precision": "fp32", "fields": NF, "tile": "default (32x8, two points per thread, packed FP32x2, zc 32)",
                    "l2": "inputs larger than L2: 3 x 335 MB padded FP32 state buffers",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,

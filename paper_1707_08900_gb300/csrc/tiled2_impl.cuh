@@ -25,6 +25,8 @@
 // This is Eq. 2 with 2 (S.grad lnrho)_i written out from Eq. 3.
 #pragma once
 
+#include <type_traits>
+
 #include "tiled_impl.cuh"
 
 namespace gbfd {
@@ -46,6 +48,33 @@ struct V2<double> {
 template <class T>
 struct Row {
     T e[10];
+};
+
+// Operations on the pair (point x, point x+1).  For FP32 these are the
+// packed two-lane instructions of sm_100+ (one instruction, two results);
+// for FP64 they fall back to two scalar operations.
+template <class T>
+struct PairOps;
+template <>
+struct PairOps<float> {
+    using V = float2;
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V bc(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct PairOps<double> {
+    using V = double2;
+    static __device__ __forceinline__ V fma(V a, V b, V c)
+    {
+        return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+    }
+    static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ V bc(double a) { return make_double2(a, a); }
+    static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
 };
 
 // Shared-memory carve-up of the pipeline.
@@ -80,7 +109,8 @@ __device__ __forceinline__ void init_barriers(uint64_t *bars, int n)
 // copies this CTA has made before (they continue the barrier phases) and are
 // advanced on return.  Returns false when a bounded wait gave up (after
 // recording it and draining the copies in flight).
-template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, class CoefT>
+template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK,
+          class CoefT>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            TS *__restrict__ out, TW *__restrict__ w,
                                            TS *__restrict__ divf, const Layout &Ls,
@@ -148,8 +178,68 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         }
     }
 
-    // z-column window of both points: col[f][k][j], planes o..o+6, point j
-    TS col[NF][7][2];
+    // z-column window of both points: colv[f][k] = (point x, point x+1) of
+    // field f at planes o..o+6
+    V colv[NF][7];
+
+    // Packed 55-point form: the Eq. 8 terms that pair z with x or y,
+    //   D_xz f(z) = sum_k MX_k [h_k(z+k) - h_k(z-k)],  h_k = f(x+k) - f(x-k),
+    //   D_yz f(z) = sum_k MX_k [g_k(z+k) - g_k(z-k)],  g_k = f(y+k) - f(y-k),
+    // are accumulated forward: each plane, when it arrives, adds its h_k /
+    // g_k to the pending outputs k planes below and subtracts them from those
+    // k planes above.  acx/acy/acz[m] hold the terms of output plane o+m for
+    // the x (D_xz u_z), y (D_yz u_z) and z (D_xz u_x + D_yz u_y) components.
+    constexpr bool FWD = PK && MIXED;
+    V acx[FWD ? 7 : 1], acy[FWD ? 7 : 1], acz[FWD ? 7 : 1];
+    if constexpr (FWD) {
+#pragma unroll
+        for (int m = 0; m < 7; ++m)
+            acx[m] = acy[m] = acz[m] = PairOps<TS>::bc((TS)0);
+    }
+    // plane at element offset `base` (slot + toff), its column values in
+    // colv[.][Q + 3]; it sits Q planes above the current output plane
+    auto absorb = [&](int base, auto qc) {
+        if constexpr (FWD) {
+            using P = PairOps<TS>;
+            constexpr int Q = decltype(qc)::value;
+            const V NEG1 = P::bc((TS)-1);
+            auto at = [&](int f, int dy, int dx) -> V {
+                return *reinterpret_cast<const V *>(sm + base + f * FSTRIDE + dy * BX + dx);
+            };
+            // x-differences of u_x (field 1) and u_z (field 3)
+            V hx[2][3];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int f = u ? 3 : 1;
+                const V m4 = at(f, 0, -4), m2 = at(f, 0, -2), p2 = at(f, 0, 2), p4 = at(f, 0, 4);
+                const V cc = colv[f][Q + 3];
+                hx[u][0] = P::mk(cc.y - m2.y, p2.x - cc.x);
+                hx[u][1] = P::fma(m2, NEG1, p2);
+                hx[u][2] = P::mk(p2.y - m4.y, p4.x - m2.x);
+            }
+#pragma unroll
+            for (int k = 1; k <= 3; ++k) {
+                // y-differences of u_y (field 2) and u_z (field 3)
+                const V gy = P::fma(at(2, -k, 0), NEG1, at(2, k, 0));
+                const V gz = P::fma(at(3, -k, 0), NEG1, at(3, k, 0));
+                const V MX1 = P::bc(c.MX(1, k)), MX2 = P::bc(c.MX(2, k));
+                const V tx = P::mul(MX1, hx[1][k - 1]);
+                const V ty = P::mul(MX2, gz);
+                const V tz = P::fma(MX2, gy, P::mul(MX1, hx[0][k - 1]));
+                if (Q - k >= 0) {
+                    acx[Q - k] = P::add(acx[Q - k], tx);
+                    acy[Q - k] = P::add(acy[Q - k], ty);
+                    acz[Q - k] = P::add(acz[Q - k], tz);
+                }
+                if (Q + k <= 6) {
+                    acx[Q + k] = P::fma(tx, NEG1, acx[Q + k]);
+                    acy[Q + k] = P::fma(ty, NEG1, acy[Q + k]);
+                    acz[Q + k] = P::fma(tz, NEG1, acz[Q + k]);
+                }
+            }
+        }
+    };
+
     bool timeout = false;
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j) {
@@ -158,9 +248,18 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
             timeout = true;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const V v = *reinterpret_cast<const V *>(sm + (q % NS) * SLOT_ELEMS + f * FSTRIDE + toff);
-            col[f][j][0] = v.x;
-            col[f][j][1] = v.y;
+            colv[f][j] = *reinterpret_cast<const V *>(sm + (q % NS) * SLOT_ELEMS + f * FSTRIDE + toff);
+        }
+        if constexpr (FWD) {
+            const int base = (q % NS) * SLOT_ELEMS + toff;
+            switch (j) {
+            case 0: absorb(base, std::integral_constant<int, -3>{}); break;
+            case 1: absorb(base, std::integral_constant<int, -2>{}); break;
+            case 2: absorb(base, std::integral_constant<int, -1>{}); break;
+            case 3: absorb(base, std::integral_constant<int, 0>{}); break;
+            case 4: absorb(base, std::integral_constant<int, 1>{}); break;
+            default: absorb(base, std::integral_constant<int, 2>{}); break;
+            }
         }
     }
 
@@ -218,10 +317,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         slot0 = slot0 + 1 == NS ? 0 : slot0 + 1;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const V v = *reinterpret_cast<const V *>(sm + so[6] + f * FSTRIDE);
-            col[f][6][0] = v.x;
-            col[f][6][1] = v.y;
+            colv[f][6] = *reinterpret_cast<const V *>(sm + so[6] + f * FSTRIDE);
         }
+        absorb(so[6], std::integral_constant<int, 3>{});
 
         // pair of field f at plane offset dz, row offset dy, x offset dx (even)
         auto ld2 = [&](int f, int dz, int dy, int dx) -> V {
@@ -255,234 +353,434 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
             return r;
         };
 
-        if (valid0) {
-            const int zo = z0 + o;
-            TW wv[NF][2];
-            if (need_w) {
-                const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + o) % NW) * RG::WSLOT_PITCH) +
-                               ty * TX + 2 * tx;
+        if constexpr (PK) {
+            static_assert(std::is_same<TS, TW>::value && std::is_same<TS, TA>::value,
+                          "the packed path computes in one type");
+            using P = PairOps<TS>;
+            if (valid0) {
+                const int zo = z0 + o;
+                const V NEG1 = P::bc((TS)-1);
+                V wv[NF];
+                if (need_w) {
+                    const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + o) % NW) * RG::WSLOT_PITCH) +
+                                   ty * TX + 2 * tx;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const VW t = *reinterpret_cast<const VW *>(ws + f * TX * TY);
-                    wv[f][0] = t.x;
-                    wv[f][1] = t.y;
+                    for (int f = 0; f < NF; ++f)
+                        wv[f] = *reinterpret_cast<const V *>(ws + f * TX * TY);
                 }
-            }
-
-            // first derivatives along x, y, z of field f for both points, plus
-            // second derivatives when `second`; centre values from col[f][3]
-            TS g[2][3], d2[2][3];
-            auto axial = [&](int f, bool second) {
-                Row<TS> r0 = row(f, 0, 0, false, true);
-                r0.e[4] = col[f][3][0];
-                r0.e[5] = col[f][3][1];
-                V yp[3], ym[3];
+                // first (and second) derivatives of field f along x, y, z:
+                // x per point from the loaded row, y and z on the pair
+                V g[3], d2[3];
+                auto axial = [&](int f, bool second) {
+                    Row<TS> r0 = row(f, 0, 0, false, true);
+                    r0.e[4] = colv[f][3].x;
+                    r0.e[5] = colv[f][3].y;
+                    TS ax[2], bx[2];
 #pragma unroll
-                for (int k = 1; k <= 3; ++k) {
-                    yp[k - 1] = ld2(f, 0, k, 0);
-                    ym[k - 1] = ld2(f, 0, -k, 0);
-                }
+                    for (int j = 0; j < 2; ++j) {
+                        ax[j] = (TS)0;
+                        bx[j] = c.D2c(0) * r0.e[4 + j];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const TS cc = col[f][3][j];
-                    TS ax = (TS)0, ay = (TS)0, az = (TS)0;
-                    TS bx = c.D2c(0) * cc, by = c.D2c(1) * cc, bz = c.D2c(2) * cc;
-#pragma unroll
-                    for (int k = 1; k <= 3; ++k) {
-                        const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
-                        const TS ypv = j ? yp[k - 1].y : yp[k - 1].x;
-                        const TS ymv = j ? ym[k - 1].y : ym[k - 1].x;
-                        const TS zp = col[f][3 + k][j], zm = col[f][3 - k][j];
-                        ax += c.D1(0, k) * (xp - xm);
-                        ay += c.D1(1, k) * (ypv - ymv);
-                        az += c.D1(2, k) * (zp - zm);
-                        if (second) {
-                            bx += c.D2(0, k) * (xp + xm);
-                            by += c.D2(1, k) * (ypv + ymv);
-                            bz += c.D2(2, k) * (zp + zm);
+                        for (int k = 1; k <= 3; ++k) {
+                            const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
+                            ax[j] += c.D1(0, k) * (xp - xm);
+                            if (second)
+                                bx[j] += c.D2(0, k) * (xp + xm);
                         }
                     }
-                    g[j][0] = ax;
-                    g[j][1] = ay;
-                    g[j][2] = az;
-                    d2[j][0] = bx;
-                    d2[j][1] = by;
-                    d2[j][2] = bz;
-                }
-            };
-            // Eq. 8 in the (x, y) plane (in_y) or the (x, z) plane: rows or
-            // planes at +-k, x offsets +-k, for both points
-            auto mix_x = [&](int f, bool in_y, TS *res) {
-                Row<TS> rp[3], rm[3];
-#pragma unroll
-                for (int k = 1; k <= 3; ++k) {
-                    const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
-                    rp[k - 1] = row(f, dz, dy, false, k == 3);
-                    rm[k - 1] = row(f, -dz, -dy, false, k == 3);
-                }
-                // k = 1 also needs the centre pair: x+1 for point 0, x for point 1
-                if (in_y) {
-                    V a = ld2(f, 0, 1, 0);
-                    rp[0].e[4] = a.x;
-                    rp[0].e[5] = a.y;
-                    a = ld2(f, 0, -1, 0);
-                    rm[0].e[4] = a.x;
-                    rm[0].e[5] = a.y;
-                } else {
-                    rp[0].e[4] = col[f][4][0];
-                    rp[0].e[5] = col[f][4][1];
-                    rm[0].e[4] = col[f][2][0];
-                    rm[0].e[5] = col[f][2][1];
-                }
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    TS a = (TS)0;
+                    g[0] = P::mk(ax[0], ax[1]);
+                    d2[0] = P::mk(bx[0], bx[1]);
+                    V gy, by, gz, bz;
 #pragma unroll
                     for (int k = 1; k <= 3; ++k) {
-                        const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
-                        const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
-                        a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
+                        const V yp = ld2(f, 0, k, 0), ym = ld2(f, 0, -k, 0);
+                        const V zp = colv[f][3 + k], zm = colv[f][3 - k];
+                        const V dyv = P::fma(ym, NEG1, yp), dzv = P::fma(zm, NEG1, zp);
+                        gy = k == 1 ? P::mul(P::bc(c.D1(1, k)), dyv) : P::fma(P::bc(c.D1(1, k)), dyv, gy);
+                        gz = k == 1 ? P::mul(P::bc(c.D1(2, k)), dzv) : P::fma(P::bc(c.D1(2, k)), dzv, gz);
+                        if (second) {
+                            if (k == 1) {
+                                by = P::mul(P::bc(c.D2c(1)), colv[f][3]);
+                                bz = P::mul(P::bc(c.D2c(2)), colv[f][3]);
+                            }
+                            by = P::fma(P::bc(c.D2(1, k)), P::add(yp, ym), by);
+                            bz = P::fma(P::bc(c.D2(2, k)), P::add(zp, zm), bz);
+                        }
                     }
-                    res[j] = a;
-                }
-            };
-            // Eq. 8 in the (y, z) plane: pairs at (dz, dy) = (+-k, +-k)
-            auto mix_yz = [&](int f, TS *res) {
-                TS a0 = (TS)0, a1 = (TS)0;
+                    g[1] = gy;
+                    g[2] = gz;
+                    if (second) {
+                        d2[1] = by;
+                        d2[2] = bz;
+                    }
+                };
+                // Eq. 8 in the (x, y) or (x, z) plane, per point, packed at the end
+                auto mix_x = [&](int f, bool in_y) -> V {
+                    Row<TS> rp[3], rm[3];
 #pragma unroll
-                for (int k = 1; k <= 3; ++k) {
-                    const V pp = ld2(f, k, k, 0), mp = ld2(f, k, -k, 0);
-                    const V mm = ld2(f, -k, -k, 0), pm = ld2(f, -k, k, 0);
-                    a0 += c.MX(2, k) * ((pp.x - mp.x) + (mm.x - pm.x));
-                    a1 += c.MX(2, k) * ((pp.y - mp.y) + (mm.y - pm.y));
-                }
-                res[0] = a0;
-                res[1] = a1;
-            };
-
-            TS uc[2][3], gl[2][3], acc[2][4], dv[2];
+                    for (int k = 1; k <= 3; ++k) {
+                        const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
+                        rp[k - 1] = row(f, dz, dy, false, k == 3);
+                        rm[k - 1] = row(f, -dz, -dy, false, k == 3);
+                    }
+                    if (in_y) {
+                        V a = ld2(f, 0, 1, 0);
+                        rp[0].e[4] = a.x;
+                        rp[0].e[5] = a.y;
+                        a = ld2(f, 0, -1, 0);
+                        rm[0].e[4] = a.x;
+                        rm[0].e[5] = a.y;
+                    } else {
+                        rp[0].e[4] = colv[f][4].x;
+                        rp[0].e[5] = colv[f][4].y;
+                        rm[0].e[4] = colv[f][2].x;
+                        rm[0].e[5] = colv[f][2].y;
+                    }
+                    TS res[2];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+                    for (int j = 0; j < 2; ++j) {
+                        TS a = (TS)0;
+#pragma unroll
+                        for (int k = 1; k <= 3; ++k) {
+                            const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
+                            const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
+                            a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
+                        }
+                        res[j] = a;
+                    }
+                    return P::mk(res[0], res[1]);
+                };
+                const V NU = P::bc(c.nu), NU3 = P::bc(c.nu3);
+                const V uc[3] = {colv[1][3], colv[2][3], colv[3][3]};
+                V acc[4], gl[3];
+                V dv = P::bc((TS)0);
+                axial(0, false);
+                gl[0] = g[0];
+                gl[1] = g[1];
+                gl[2] = g[2];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    uc[j][i] = col[1 + i][3][j];
-                    acc[j][1 + i] = (TS)0;
-                }
-                dv[j] = (TS)0;
-            }
-            // grad lnrho
-            axial(0, false);
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    gl[j][a] = g[j][a];
-            // velocity components
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                axial(1 + i, true);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const TS adv = uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2];
-                    const TS lap = d2[j][0] + d2[j][1] + d2[j][2];
-                    const TS sg = g[j][0] * gl[j][0] + g[j][1] * gl[j][1] + g[j][2] * gl[j][2];
-                    acc[j][1 + i] += c.nu * (lap + sg) - adv;
+                    axial(1 + i, true);
+                    V adv = P::mul(uc[0], g[0]);
+                    adv = P::fma(uc[1], g[1], adv);
+                    adv = P::fma(uc[2], g[2], adv);
+                    const V lap = P::add(P::add(d2[0], d2[1]), d2[2]);
+                    V sg = P::mul(g[0], gl[0]);
+                    sg = P::fma(g[1], gl[1], sg);
+                    sg = P::fma(g[2], gl[2], sg);
+                    V ai = P::mul(NU, P::add(lap, sg));
+                    if (i > 0)
+                        ai = P::add(ai, acc[1 + i]);
+                    ai = P::fma(adv, NEG1, ai);
                     if (MIXED)
-                        acc[j][1 + i] += c.nu3 * d2[j][i];
+                        ai = P::fma(NU3, d2[i], ai);
+                    acc[1 + i] = ai;
+                    const V nugl = P::mul(NU, gl[i]);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        acc[j][1 + a] += c.nu * g[j][a] * gl[j][i];
-                    dv[j] += g[j][i];
+                    for (int a = 0; a < 3; ++a) {
+                        if (a == i)
+                            acc[1 + a] = P::fma(g[a], nugl, acc[1 + a]);
+                        else if (a > i && i == 0)
+                            acc[1 + a] = P::mul(g[a], nugl);  // first contribution
+                        else
+                            acc[1 + a] = P::fma(g[a], nugl, acc[1 + a]);
+                    }
+                    dv = P::add(dv, g[i]);
+                    if (MIXED) {
+                        // D_ij u_i enters d_j (div u) for j != i; the pairs
+                        // with z come from the forward accumulators
+                        if (i == 0)
+                            acc[2] = P::fma(NU3, mix_x(1, true), acc[2]);  // D_xy u_x -> y
+                        else if (i == 1)
+                            acc[1] = P::fma(NU3, mix_x(2, true), acc[1]);  // D_xy u_y -> x
+                    }
                 }
                 if (MIXED) {
-                    // D_ij u_i enters d_j (div u) for j != i
-                    TS m[2];
-                    if (i == 0) {
-                        mix_x(1, true, m);  // D_xy u_x -> y
+                    acc[1] = P::fma(NU3, acx[0], acc[1]);  // D_xz u_z
+                    acc[2] = P::fma(NU3, acy[0], acc[2]);  // D_yz u_z
+                    acc[3] = P::fma(NU3, acz[0], acc[3]);  // D_xz u_x + D_yz u_y
+                }
+                V rs = P::bc((TS)0);
+                if (NF == 5) {
+                    axial(4, false);
+                    V t = P::mul(uc[0], g[0]);
+                    t = P::fma(uc[1], g[1], t);
+                    t = P::fma(uc[2], g[2], t);
+                    rs = P::mul(t, NEG1);
+                }
+                {
+                    V ug = P::mul(uc[0], gl[0]);
+                    ug = P::fma(uc[1], gl[1], ug);
+                    ug = P::fma(uc[2], gl[2], ug);
+                    acc[0] = P::mul(P::add(ug, dv), NEG1);
+                    const V NCS2 = P::bc(-c.cs2);
+                    const V t = P::mul(P::bc(-c.nu23), dv);
 #pragma unroll
-                        for (int j = 0; j < 2; ++j)
-                            acc[j][2] += c.nu3 * m[j];
-                        mix_x(1, false, m);  // D_xz u_x -> z
+                    for (int a = 0; a < 3; ++a)
+                        acc[1 + a] = P::fma(t, gl[a], P::fma(NCS2, gl[a], acc[1 + a]));
+                }
+                if (!MIXED) {
+                    const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+                    *reinterpret_cast<V *>(divf + gi) = dv;
+                    if (gdx)
+                        *reinterpret_cast<V *>(divf + gi + gdx) = dv;
+                    if (gdy) {
+                        *reinterpret_cast<V *>(divf + gi + gdy) = dv;
+                        if (gdx)
+                            *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dv;
+                    }
+                }
+                const V DT = P::bc(dt), ALPHA = P::bc(alpha), BETA = P::bc(beta);
 #pragma unroll
-                        for (int j = 0; j < 2; ++j)
-                            acc[j][3] += c.nu3 * m[j];
-                    } else if (i == 1) {
-                        mix_x(2, true, m);  // D_xy u_y -> x
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-                            acc[j][1] += c.nu3 * m[j];
-                        mix_yz(2, m);  // D_yz u_y -> z
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-                            acc[j][3] += c.nu3 * m[j];
-                    } else {
-                        mix_x(3, false, m);  // D_xz u_z -> x
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-                            acc[j][1] += c.nu3 * m[j];
-                        mix_yz(3, m);  // D_yz u_z -> y
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
-                            acc[j][2] += c.nu3 * m[j];
+                for (int f = 0; f < NF; ++f) {
+                    const V r = f < 4 ? acc[f] : rs;
+                    const V wn = first ? P::mul(DT, r) : P::fma(DT, r, P::mul(ALPHA, wv[f]));
+                    const V o2 = P::fma(BETA, wn, colv[f][3]);
+                    if (!last)
+                        *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = wn;
+                    TS *op = out + f * Ls.fpitch + go_s;
+                    *reinterpret_cast<V *>(op) = o2;
+                    if (gdx)
+                        *reinterpret_cast<V *>(op + gdx) = o2;
+                    if (gdy) {
+                        *reinterpret_cast<V *>(op + gdy) = o2;
+                        if (gdx)
+                            *reinterpret_cast<V *>(op + gdy + gdx) = o2;
                     }
                 }
             }
-            TS rs[2] = {(TS)0, (TS)0};
-            if (NF == 5) {
-                axial(4, false);
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    rs[j] = -(uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2]);
-            }
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                acc[j][0] = -(uc[j][0] * gl[j][0] + uc[j][1] * gl[j][1] + uc[j][2] * gl[j][2]) - dv[j];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    acc[j][1 + a] += -c.cs2 * gl[j][a] - c.nu23 * dv[j] * gl[j][a];
-            }
-            if (!MIXED) {
-                V dvv;
-                dvv.x = dv[0];
-                dvv.y = dv[1];
-                const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
-                *reinterpret_cast<V *>(divf + gi) = dvv;
-                if (gdx)
-                    *reinterpret_cast<V *>(divf + gi + gdx) = dvv;
-                if (gdy) {
-                    *reinterpret_cast<V *>(divf + gi + gdy) = dvv;
-                    if (gdx)
-                        *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dvv;
+        } else {
+            if (valid0) {
+                const int zo = z0 + o;
+                TW wv[NF][2];
+                if (need_w) {
+                    const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + o) % NW) * RG::WSLOT_PITCH) +
+                                   ty * TX + 2 * tx;
+    #pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const VW t = *reinterpret_cast<const VW *>(ws + f * TX * TY);
+                        wv[f][0] = t.x;
+                        wv[f][1] = t.y;
+                    }
                 }
-            }
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                TS ov[2];
-                TW wn[2];
-#pragma unroll
+
+                // first derivatives along x, y, z of field f for both points, plus
+                // second derivatives when `second`; centre values from colv[f][3]
+                TS g[2][3], d2[2][3];
+                auto axial = [&](int f, bool second) {
+                    Row<TS> r0 = row(f, 0, 0, false, true);
+                    r0.e[4] = colv[f][3].x;
+                    r0.e[5] = colv[f][3].y;
+                    V yp[3], ym[3];
+    #pragma unroll
+                    for (int k = 1; k <= 3; ++k) {
+                        yp[k - 1] = ld2(f, 0, k, 0);
+                        ym[k - 1] = ld2(f, 0, -k, 0);
+                    }
+    #pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const TS cc = j ? colv[f][3].y : colv[f][3].x;
+                        TS ax = (TS)0, ay = (TS)0, az = (TS)0;
+                        TS bx = c.D2c(0) * cc, by = c.D2c(1) * cc, bz = c.D2c(2) * cc;
+    #pragma unroll
+                        for (int k = 1; k <= 3; ++k) {
+                            const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
+                            const TS ypv = j ? yp[k - 1].y : yp[k - 1].x;
+                            const TS ymv = j ? ym[k - 1].y : ym[k - 1].x;
+                            const TS zp = j ? colv[f][3 + k].y : colv[f][3 + k].x;
+                            const TS zm = j ? colv[f][3 - k].y : colv[f][3 - k].x;
+                            ax += c.D1(0, k) * (xp - xm);
+                            ay += c.D1(1, k) * (ypv - ymv);
+                            az += c.D1(2, k) * (zp - zm);
+                            if (second) {
+                                bx += c.D2(0, k) * (xp + xm);
+                                by += c.D2(1, k) * (ypv + ymv);
+                                bz += c.D2(2, k) * (zp + zm);
+                            }
+                        }
+                        g[j][0] = ax;
+                        g[j][1] = ay;
+                        g[j][2] = az;
+                        d2[j][0] = bx;
+                        d2[j][1] = by;
+                        d2[j][2] = bz;
+                    }
+                };
+                // Eq. 8 in the (x, y) plane (in_y) or the (x, z) plane: rows or
+                // planes at +-k, x offsets +-k, for both points
+                auto mix_x = [&](int f, bool in_y, TS *res) {
+                    Row<TS> rp[3], rm[3];
+    #pragma unroll
+                    for (int k = 1; k <= 3; ++k) {
+                        const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
+                        rp[k - 1] = row(f, dz, dy, false, k == 3);
+                        rm[k - 1] = row(f, -dz, -dy, false, k == 3);
+                    }
+                    // k = 1 also needs the centre pair: x+1 for point 0, x for point 1
+                    if (in_y) {
+                        V a = ld2(f, 0, 1, 0);
+                        rp[0].e[4] = a.x;
+                        rp[0].e[5] = a.y;
+                        a = ld2(f, 0, -1, 0);
+                        rm[0].e[4] = a.x;
+                        rm[0].e[5] = a.y;
+                    } else {
+                        rp[0].e[4] = colv[f][4].x;
+                        rp[0].e[5] = colv[f][4].y;
+                        rm[0].e[4] = colv[f][2].x;
+                        rm[0].e[5] = colv[f][2].y;
+                    }
+    #pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        TS a = (TS)0;
+    #pragma unroll
+                        for (int k = 1; k <= 3; ++k) {
+                            const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
+                            const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
+                            a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
+                        }
+                        res[j] = a;
+                    }
+                };
+                // Eq. 8 in the (y, z) plane: pairs at (dz, dy) = (+-k, +-k)
+                auto mix_yz = [&](int f, TS *res) {
+                    TS a0 = (TS)0, a1 = (TS)0;
+    #pragma unroll
+                    for (int k = 1; k <= 3; ++k) {
+                        const V pp = ld2(f, k, k, 0), mp = ld2(f, k, -k, 0);
+                        const V mm = ld2(f, -k, -k, 0), pm = ld2(f, -k, k, 0);
+                        a0 += c.MX(2, k) * ((pp.x - mp.x) + (mm.x - pm.x));
+                        a1 += c.MX(2, k) * ((pp.y - mp.y) + (mm.y - pm.y));
+                    }
+                    res[0] = a0;
+                    res[1] = a1;
+                };
+
+                TS uc[2][3], gl[2][3], acc[2][4], dv[2];
+    #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const TS r = f < 4 ? acc[j][f] : rs[j];
-                    TW wo = first ? (TW)0 : wv[f][j];
-                    rk3_update<TA, TW, TS>(first, alpha, beta, dt, (TA)r, col[f][3][j], wo, ov[j]);
-                    wn[j] = wo;
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        uc[j][i] = j ? colv[1 + i][3].y : colv[1 + i][3].x;
+                        acc[j][1 + i] = (TS)0;
+                    }
+                    dv[j] = (TS)0;
                 }
-                if (!last) {
-                    VW t;
-                    t.x = wn[0];
-                    t.y = wn[1];
-                    *reinterpret_cast<VW *>(w + f * Lw.fpitch + go_w) = t;
+                // grad lnrho
+                axial(0, false);
+    #pragma unroll
+                for (int j = 0; j < 2; ++j)
+    #pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        gl[j][a] = g[j][a];
+                // velocity components
+    #pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    axial(1 + i, true);
+    #pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const TS adv = uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2];
+                        const TS lap = d2[j][0] + d2[j][1] + d2[j][2];
+                        const TS sg = g[j][0] * gl[j][0] + g[j][1] * gl[j][1] + g[j][2] * gl[j][2];
+                        acc[j][1 + i] += c.nu * (lap + sg) - adv;
+                        if (MIXED)
+                            acc[j][1 + i] += c.nu3 * d2[j][i];
+    #pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            acc[j][1 + a] += c.nu * g[j][a] * gl[j][i];
+                        dv[j] += g[j][i];
+                    }
+                    if (MIXED) {
+                        // D_ij u_i enters d_j (div u) for j != i
+                        TS m[2];
+                        if (i == 0) {
+                            mix_x(1, true, m);  // D_xy u_x -> y
+    #pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                acc[j][2] += c.nu3 * m[j];
+                            mix_x(1, false, m);  // D_xz u_x -> z
+    #pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                acc[j][3] += c.nu3 * m[j];
+                        } else if (i == 1) {
+                            mix_x(2, true, m);  // D_xy u_y -> x
+    #pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                acc[j][1] += c.nu3 * m[j];
+                            mix_yz(2, m);  // D_yz u_y -> z
+    #pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                acc[j][3] += c.nu3 * m[j];
+                        } else {
+                            mix_x(3, false, m);  // D_xz u_z -> x
+    #pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                acc[j][1] += c.nu3 * m[j];
+                            mix_yz(3, m);  // D_yz u_z -> y
+    #pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                acc[j][2] += c.nu3 * m[j];
+                        }
+                    }
                 }
-                V o2;
-                o2.x = ov[0];
-                o2.y = ov[1];
-                TS *op = out + f * Ls.fpitch + go_s;
-                *reinterpret_cast<V *>(op) = o2;
-                if (gdx)
-                    *reinterpret_cast<V *>(op + gdx) = o2;
-                if (gdy) {
-                    *reinterpret_cast<V *>(op + gdy) = o2;
+                TS rs[2] = {(TS)0, (TS)0};
+                if (NF == 5) {
+                    axial(4, false);
+    #pragma unroll
+                    for (int j = 0; j < 2; ++j)
+                        rs[j] = -(uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2]);
+                }
+    #pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    acc[j][0] = -(uc[j][0] * gl[j][0] + uc[j][1] * gl[j][1] + uc[j][2] * gl[j][2]) - dv[j];
+    #pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        acc[j][1 + a] += -c.cs2 * gl[j][a] - c.nu23 * dv[j] * gl[j][a];
+                }
+                if (!MIXED) {
+                    V dvv;
+                    dvv.x = dv[0];
+                    dvv.y = dv[1];
+                    const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+                    *reinterpret_cast<V *>(divf + gi) = dvv;
                     if (gdx)
-                        *reinterpret_cast<V *>(op + gdy + gdx) = o2;
+                        *reinterpret_cast<V *>(divf + gi + gdx) = dvv;
+                    if (gdy) {
+                        *reinterpret_cast<V *>(divf + gi + gdy) = dvv;
+                        if (gdx)
+                            *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dvv;
+                    }
+                }
+    #pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    TS ov[2];
+                    TW wn[2];
+    #pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const TS r = f < 4 ? acc[j][f] : rs[j];
+                        TW wo = first ? (TW)0 : wv[f][j];
+                        rk3_update<TA, TW, TS>(first, alpha, beta, dt, (TA)r,
+                                               j ? colv[f][3].y : colv[f][3].x, wo, ov[j]);
+                        wn[j] = wo;
+                    }
+                    if (!last) {
+                        VW t;
+                        t.x = wn[0];
+                        t.y = wn[1];
+                        *reinterpret_cast<VW *>(w + f * Lw.fpitch + go_w) = t;
+                    }
+                    V o2;
+                    o2.x = ov[0];
+                    o2.y = ov[1];
+                    TS *op = out + f * Ls.fpitch + go_s;
+                    *reinterpret_cast<V *>(op) = o2;
+                    if (gdx)
+                        *reinterpret_cast<V *>(op + gdx) = o2;
+                    if (gdy) {
+                        *reinterpret_cast<V *>(op + gdy) = o2;
+                        if (gdx)
+                            *reinterpret_cast<V *>(op + gdy + gdx) = o2;
+                    }
                 }
             }
         }
@@ -491,10 +789,17 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 #pragma unroll
         for (int f = 0; f < NF; ++f)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                col[f][k][0] = col[f][k + 1][0];
-                col[f][k][1] = col[f][k + 1][1];
+            for (int k = 0; k < 6; ++k)
+                colv[f][k] = colv[f][k + 1];
+        if constexpr (FWD) {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                acx[m] = acx[m + 1];
+                acy[m] = acy[m + 1];
+                acz[m] = acz[m + 1];
             }
+            acx[6] = acy[6] = acz[6] = PairOps<TS>::bc((TS)0);
+        }
     }
     const bool bad = __syncthreads_or(timeout);
     if (bad && threadIdx.x == 0) {
@@ -511,7 +816,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 }
 
 // Single box: one CTA per (tile, z-chunk).
-template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS>
+template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK>
 __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
@@ -526,7 +831,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
+    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
                                                   (TA)st.alpha, (TA)st.beta, (TA)st.dt,
                                                   st.first != 0, st.last != 0, x0, y0, z0, nout,
                                                   jrun, wrun, smem, dev_error,
@@ -535,7 +840,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
 
 }  // namespace tiled2
 
-template <class TS, class TW, class TA, int TX, int TY, int NS>
+template <class TS, class TW, class TA, int TX, int TY, int NS, bool PK = false>
 cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
                            int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
@@ -556,7 +861,7 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
     cudaError_t e;
 #define GBFD_LAUNCH2(NFV, MIX)                                                                    \
     do {                                                                                          \
-        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS>;                      \
+        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK>;                      \
         constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS>::BYTES;                          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \

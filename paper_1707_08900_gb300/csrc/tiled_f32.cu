@@ -1,6 +1,7 @@
 // Tiled substep instantiations with FP32 storage and FP32 arithmetic: the
-// one-point-per-thread kernel (variants 0-3) and the paired-load
-// two-points-per-thread kernel (variants 4-6).
+// one-point-per-thread kernel (variants 0-3), the paired-load
+// two-points-per-thread kernel (variants 4-6) and the same with the two
+// points' arithmetic in packed FP32x2 instructions (variant 7).
 #include "tiled2_impl.cuh"
 
 namespace gbfd {
@@ -10,8 +11,8 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
                                  int form, int cfg, int *dev_error, TmapCache *cache,
                                  cudaStream_t stream, int *launches)
 {
-    // default: two points per thread, 32 x 8 tile, z-chunk 32 (fastest at
-    // 256^3 on GB300 in the tile sweep)
+    // default: two points per thread in packed arithmetic, 32 x 8 tile,
+    // z-chunk 32 (fastest at 256^3 and 512^3 on GB300 in the tile sweep)
     const int idx = cfg < 0 ? kDefaultF32 : cfg;
     const TileConfig t = tiled_config(4, idx);
     const int v = idx / kZcChoices;
@@ -41,9 +42,13 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         e = launch_px2_cfg<TS, TW, TA, 32, 16, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
                                                   stream, launches);
         break;
-    default:
+    case 6:
         e = launch_px2_cfg<TS, TW, TA, 64, 8, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
                                                  stream, launches);
+        break;
+    default:
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true>(b, c, st, nf, form, t.zc, v, dev_error,
+                                                       cache, stream, launches);
         break;
     }
     if (e != cudaSuccess || form == 0)
