@@ -3,8 +3,8 @@
 // ONE persistent launch whose CTAs walk a work list of equal-cost columns
 // (box, 32x8 tile, z-chunk) drawn from all boxes, through the same
 // TMA-staged two-points-per-thread pipeline as the single-box kernel
-// (tiled2::run_column); a run of RK3 steps is captured once as a CUDA graph
-// and replayed.  FP32 storage and arithmetic.
+// (tiled2::run_column, packed FP32x2 form); a run of RK3 steps is captured
+// once as a CUDA graph and replayed.  FP32 storage and arithmetic.
 //
 // Per-box data lives in device memory: the TMA descriptors of the box's two
 // state buffers and its u-tilde, the buffer pointers and layout, and the
@@ -31,7 +31,7 @@
 namespace gbfd {
 namespace batch {
 
-constexpr int TX = 32, TY = 8, NS = 8;
+constexpr int TX = 32, TY = 8, NS = 8, U = 2;  // U: output planes per loop iteration
 
 struct BoxDesc {
     CUtensorMap tm_state[2];  // halo boxes of state buffers 0 and 1
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_batch_substep(
     const float *__restrict__ dts, const int zc, const RKStage st, const int parity,
     int *__restrict__ dev_error)
 {
-    using RG = tiled2::Ring<float, float, NF, TX, TY, NS>;
+    using RG = tiled2::Ring<float, float, NF, TX, TY, NS, U + 2>;
     extern __shared__ __align__(128) unsigned char smem[];
     tiled2::init_barriers(reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF), NS + RG::NW);
     int jrun = 0, wrun = 0;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_batch_substep(
         const Layout L = B->L;
         const float dt = dts[item.x];
         const int nout = min(zc, L.nz - item.w);
-        if (!tiled2::run_column<float, float, float, NF, true, TX, TY, NS, false>(
+        if (!tiled2::run_column<float, float, float, NF, true, TX, TY, NS, true, U>(
                 &B->tm_state[parity], &B->tm_w, B->state[parity ^ 1], B->w, nullptr, L, L, c,
                 (float)st.alpha, (float)st.beta, dt, st.first != 0, st.last != 0, item.y, item.z,
                 item.w, nout, jrun, wrun, smem, dev_error))
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_batch_substep(
 template <int NF>
 constexpr int smem_bytes()
 {
-    return tiled2::Ring<float, float, NF, TX, TY, NS>::BYTES;
+    return tiled2::Ring<float, float, NF, TX, TY, NS, U + 2>::BYTES;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()

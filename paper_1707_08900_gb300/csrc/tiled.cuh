@@ -14,17 +14,18 @@ struct TileConfig {
     int zc;      // planes streamed per CTA
     int ns;      // plane slots in the shared-memory ring
     int px;      // points per thread along x (1, or 2 with paired loads)
-    int pk;      // 1: the two points' arithmetic in packed FP32x2 instructions
+    int pk;      // 0: scalar arithmetic; n > 0: packed FP32x2 arithmetic with
+                 // n output planes per loop iteration
 };
 
 // Number of z-chunk lengths offered per (tx, ty, ns) variant; table index
 // i is variant i / kZcChoices with the (i % kZcChoices)-th chunk length.
 constexpr int kZcChoices = 4;
 
-// Default FP32 table entry: variant 7 (32 x 8, two points per thread,
-// packed FP32x2 arithmetic, z-paired mixed terms accumulated forward) with
-// the first z-chunk length.
-constexpr int kDefaultF32 = 7 * kZcChoices;
+// Default FP32 table entry: variant 8 (32 x 8, two points per thread,
+// packed FP32x2 arithmetic, z-paired mixed terms accumulated forward, two
+// output planes per loop iteration) with the first z-chunk length.
+constexpr int kDefaultF32 = 8 * kZcChoices;
 
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);

@@ -78,7 +78,7 @@ struct PairOps<double> {
 };
 
 // Shared-memory carve-up of the pipeline.
-template <class TS, class TW, int NF, int TX, int TY, int NS>
+template <class TS, class TW, int NF, int TX, int TY, int NS, int NW_ = 3>
 struct Ring {
     static constexpr int BX = TX + 2 * GX;
     static constexpr int BY = TY + 2 * GY;
@@ -86,7 +86,7 @@ struct Ring {
     static constexpr int SLOT_BYTES = NF * FSTRIDE * (int)sizeof(TS);
     static constexpr int SLOT_PITCH = (SLOT_BYTES + 127) / 128 * 128;
     static constexpr int SLOT_ELEMS = SLOT_PITCH / (int)sizeof(TS);
-    static constexpr int NW = 3;
+    static constexpr int NW = NW_;
     static constexpr int WSLOT_BYTES = NF * TX * TY * (int)sizeof(TW);
     static constexpr int WSLOT_PITCH = (WSLOT_BYTES + 127) / 128 * 128;
     static constexpr int W_OFF = NS * SLOT_PITCH;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void init_barriers(uint64_t *bars, int n)
 // advanced on return.  Returns false when a bounded wait gave up (after
 // recording it and draining the copies in flight).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK,
-          class CoefT>
+          int U, class CoefT>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            TS *__restrict__ out, TW *__restrict__ w,
                                            TS *__restrict__ divf, const Layout &Ls,
@@ -121,7 +121,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                                            unsigned char *smem, int *dev_error,
                                            const int skip_plane = -1)
 {
-    using RG = Ring<TS, TW, NF, TX, TY, NS>;
+    using RG = Ring<TS, TW, NF, TX, TY, NS, U + 2>;
     using tiled::mbar_wait;
     using V = typename V2<TS>::t;
     using VW = typename V2<TW>::t;
@@ -164,23 +164,32 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         tiled::tma_load_4d(wsm + slot * RG::WSLOT_PITCH, wmap, &wbars[slot], x0 + GX, y0 + GY,
                            z0 + o, 0);
     };
+    // The forward-accumulated and 19-point forms read only the centre plane
+    // and the arriving plane from shared memory, so the ring need not keep
+    // the three planes below the centre (LAG); the unpacked 55-point form
+    // reads all seven.
+    constexpr bool FWD = PK && MIXED;
+    constexpr int LAG = (MIXED && !FWD) ? 0 : R;
+    static_assert(NS >= 4 && NS >= (LAG ? U + 3 : U + 6), "ring too short for the planes in use");
     if (threadIdx.x == 0) {
         tiled::fence_proxy_async();
 #pragma unroll 1
-        for (int j = 0; j < NS - 1 && j < nplanes; ++j)
+        for (int j = 0; j < NS && j < nplanes; ++j)
             issue(j);
-        issued = min(NS - 1, nplanes);
+        issued = min(NS, nplanes);
         if (need_w) {
 #pragma unroll 1
-            for (int o = 0; o < NW - 1 && o < nout; ++o)
+            for (int o = 0; o < NW && o < nout; ++o)
                 issue_w(o);
-            wissued = min(NW - 1, nout);
+            wissued = min(NW, nout);
         }
     }
 
     // z-column window of both points: colv[f][k] = (point x, point x+1) of
-    // field f at planes o..o+6
-    V colv[NF][7];
+    // field f at local plane o + k (output plane o - 3 + k), o the first
+    // output plane of the current group of U
+    constexpr int W = 6 + U;
+    V colv[NF][W];
 
     // Packed 55-point form: the Eq. 8 terms that pair z with x or y,
     //   D_xz f(z) = sum_k MX_k [h_k(z+k) - h_k(z-k)],  h_k = f(x+k) - f(x-k),
@@ -189,15 +198,14 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     // g_k to the pending outputs k planes below and subtracts them from those
     // k planes above.  acx/acy/acz[m] hold the terms of output plane o+m for
     // the x (D_xz u_z), y (D_yz u_z) and z (D_xz u_x + D_yz u_y) components.
-    constexpr bool FWD = PK && MIXED;
-    V acx[FWD ? 7 : 1], acy[FWD ? 7 : 1], acz[FWD ? 7 : 1];
+    V acx[FWD ? W : 1], acy[FWD ? W : 1], acz[FWD ? W : 1];
     if constexpr (FWD) {
 #pragma unroll
-        for (int m = 0; m < 7; ++m)
+        for (int m = 0; m < W; ++m)
             acx[m] = acy[m] = acz[m] = PairOps<TS>::bc((TS)0);
     }
     // plane at element offset `base` (slot + toff), its column values in
-    // colv[.][Q + 3]; it sits Q planes above the current output plane
+    // colv[.][Q + 3]; it is output plane o + Q
     auto absorb = [&](int base, auto qc) {
         if constexpr (FWD) {
             using P = PairOps<TS>;
@@ -231,7 +239,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                     acy[Q - k] = P::add(acy[Q - k], ty);
                     acz[Q - k] = P::add(acz[Q - k], tz);
                 }
-                if (Q + k <= 6) {
+                if (Q + k < W) {
                     acx[Q + k] = P::fma(tx, NEG1, acx[Q + k]);
                     acy[Q + k] = P::fma(ty, NEG1, acy[Q + k]);
                     acz[Q + k] = P::fma(tz, NEG1, acz[Q + k]);
@@ -243,6 +251,18 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     bool timeout = false;
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j) {
+        if (j == NS) {
+            // a ring shorter than the six leading planes: the first ones are
+            // consumed, their slots take the rest
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tiled::fence_proxy_async();
+#pragma unroll 1
+                for (int jj = NS; jj < 2 * R; ++jj)
+                    issue(jj);
+                issued = 2 * R;
+            }
+        }
         const int q = jrun + j;
         if (!mbar_wait(&bars[q % NS], (q / NS) & 1))
             timeout = true;
@@ -279,526 +299,549 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         gdy = -(long long)Ls.ny * Ls.P;
 
     int waited = 2 * R, wwaited = 0;
-    int slot0 = jrun % NS;  // slot of local plane o
-#pragma unroll 1
-    for (int o = 0; o < nout; ++o) {
-        // all threads are done with plane o-1: its slot is free, and a
-        // timeout seen by any thread ends the CTA for everyone
-        if (__syncthreads_or(timeout))
-            break;
-        if (threadIdx.x == 0) {
-            const int j = o + NS - 1;
-            tiled::fence_proxy_async();
-            if (j < nplanes) {
-                issue(j);
-                issued = j + 1;
-            }
-            if (need_w && o + NW - 1 < nout) {
-                issue_w(o + NW - 1);
-                wissued = o + NW;
-            }
-        }
-        const int qn = jrun + o + 2 * R;
+    int slot0 = jrun % NS;  // slot of local plane oo (the output plane being computed)
+
+    // output plane oo = o + S of the current group
+    auto plane = [&](const int oo, auto sc) {
+        constexpr int S = decltype(sc)::value;
+        auto C = [&](int f, int k) -> V & { return colv[f][S + k]; };
+        const int qn = jrun + oo + 2 * R;
         if (!mbar_wait(&bars[qn % NS], (qn / NS) & 1))
             timeout = true;
-        waited = o + 2 * R + 1;
+        waited = oo + 2 * R + 1;
         if (need_w) {
-            const int qw = wrun + o;
+            const int qw = wrun + oo;
             if (!mbar_wait(&wbars[qw % NW], (qw / NW) & 1))
                 timeout = true;
-            wwaited = o + 1;
+            wwaited = oo + 1;
         }
-        int so[7];  // element offsets of the 7 window planes' slots
+        int so[7];  // element offsets of the slots of local planes oo..oo+6
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-            const int s = slot0 + k;
-            so[k] = (s >= NS ? s - NS : s) * SLOT_ELEMS + toff;
+            // slot0 < NS and NS >= 4, so two wraps cover k <= 6
+            int sl = slot0 + k;
+            sl = sl >= NS ? sl - NS : sl;
+            sl = sl >= NS ? sl - NS : sl;
+            so[k] = sl * SLOT_ELEMS + toff;
         }
         slot0 = slot0 + 1 == NS ? 0 : slot0 + 1;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            colv[f][6] = *reinterpret_cast<const V *>(sm + so[6] + f * FSTRIDE);
+            C(f, 6) = *reinterpret_cast<const V *>(sm + so[6] + f * FSTRIDE);
         }
-        absorb(so[6], std::integral_constant<int, 3>{});
+        absorb(so[6], std::integral_constant<int, S + 3>{});
 
-        // pair of field f at plane offset dz, row offset dy, x offset dx (even)
-        auto ld2 = [&](int f, int dz, int dy, int dx) -> V {
-            return *reinterpret_cast<const V *>(sm + so[dz + 3] + f * FSTRIDE + dy * BX + dx);
-        };
-        // the x row of field f at (dz, dy): pairs at -4, -2, 2, 4 (+ centre)
-        auto row = [&](int f, int dz, int dy, bool centre, bool outer) {
-            Row<TS> r;
-            V a;
-            if (outer) {
-                a = ld2(f, dz, dy, -4);
-                r.e[0] = a.x;
-                r.e[1] = a.y;
-            }
-            a = ld2(f, dz, dy, -2);
-            r.e[2] = a.x;
-            r.e[3] = a.y;
-            if (centre) {
-                a = ld2(f, dz, dy, 0);
-                r.e[4] = a.x;
-                r.e[5] = a.y;
-            }
-            a = ld2(f, dz, dy, 2);
-            r.e[6] = a.x;
-            r.e[7] = a.y;
-            if (outer) {
-                a = ld2(f, dz, dy, 4);
-                r.e[8] = a.x;
-                r.e[9] = a.y;
-            }
-            return r;
-        };
-
-        if constexpr (PK) {
-            static_assert(std::is_same<TS, TW>::value && std::is_same<TS, TA>::value,
-                          "the packed path computes in one type");
-            using P = PairOps<TS>;
-            if (valid0) {
-                const int zo = z0 + o;
-                const V NEG1 = P::bc((TS)-1);
-                V wv[NF];
-                if (need_w) {
-                    const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + o) % NW) * RG::WSLOT_PITCH) +
-                                   ty * TX + 2 * tx;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f)
-                        wv[f] = *reinterpret_cast<const V *>(ws + f * TX * TY);
+            // pair of field f at plane offset dz, row offset dy, x offset dx (even)
+            auto ld2 = [&](int f, int dz, int dy, int dx) -> V {
+                return *reinterpret_cast<const V *>(sm + so[dz + 3] + f * FSTRIDE + dy * BX + dx);
+            };
+            // the x row of field f at (dz, dy): pairs at -4, -2, 2, 4 (+ centre)
+            auto row = [&](int f, int dz, int dy, bool centre, bool outer) {
+                Row<TS> r;
+                V a;
+                if (outer) {
+                    a = ld2(f, dz, dy, -4);
+                    r.e[0] = a.x;
+                    r.e[1] = a.y;
                 }
-                // first (and second) derivatives of field f along x, y, z:
-                // x per point from the loaded row, y and z on the pair
-                V g[3], d2[3];
-                auto axial = [&](int f, bool second) {
-                    Row<TS> r0 = row(f, 0, 0, false, true);
-                    r0.e[4] = colv[f][3].x;
-                    r0.e[5] = colv[f][3].y;
-                    TS ax[2], bx[2];
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        ax[j] = (TS)0;
-                        bx[j] = c.D2c(0) * r0.e[4 + j];
-#pragma unroll
-                        for (int k = 1; k <= 3; ++k) {
-                            const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
-                            ax[j] += c.D1(0, k) * (xp - xm);
-                            if (second)
-                                bx[j] += c.D2(0, k) * (xp + xm);
-                        }
+                a = ld2(f, dz, dy, -2);
+                r.e[2] = a.x;
+                r.e[3] = a.y;
+                if (centre) {
+                    a = ld2(f, dz, dy, 0);
+                    r.e[4] = a.x;
+                    r.e[5] = a.y;
+                }
+                a = ld2(f, dz, dy, 2);
+                r.e[6] = a.x;
+                r.e[7] = a.y;
+                if (outer) {
+                    a = ld2(f, dz, dy, 4);
+                    r.e[8] = a.x;
+                    r.e[9] = a.y;
+                }
+                return r;
+            };
+
+            if constexpr (PK) {
+                static_assert(std::is_same<TS, TW>::value && std::is_same<TS, TA>::value,
+                              "the packed path computes in one type");
+                using P = PairOps<TS>;
+                if (valid0) {
+                    const int zo = z0 + oo;
+                    const V NEG1 = P::bc((TS)-1);
+                    V wv[NF];
+                    if (need_w) {
+                        const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + oo) % NW) * RG::WSLOT_PITCH) +
+                                       ty * TX + 2 * tx;
+    #pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            wv[f] = *reinterpret_cast<const V *>(ws + f * TX * TY);
                     }
-                    g[0] = P::mk(ax[0], ax[1]);
-                    d2[0] = P::mk(bx[0], bx[1]);
-                    V gy, by, gz, bz;
-#pragma unroll
-                    for (int k = 1; k <= 3; ++k) {
-                        const V yp = ld2(f, 0, k, 0), ym = ld2(f, 0, -k, 0);
-                        const V zp = colv[f][3 + k], zm = colv[f][3 - k];
-                        const V dyv = P::fma(ym, NEG1, yp), dzv = P::fma(zm, NEG1, zp);
-                        gy = k == 1 ? P::mul(P::bc(c.D1(1, k)), dyv) : P::fma(P::bc(c.D1(1, k)), dyv, gy);
-                        gz = k == 1 ? P::mul(P::bc(c.D1(2, k)), dzv) : P::fma(P::bc(c.D1(2, k)), dzv, gz);
-                        if (second) {
-                            if (k == 1) {
-                                by = P::mul(P::bc(c.D2c(1)), colv[f][3]);
-                                bz = P::mul(P::bc(c.D2c(2)), colv[f][3]);
+                    // first (and second) derivatives of field f along x, y, z:
+                    // x per point from the loaded row, y and z on the pair
+                    V g[3], d2[3];
+                    auto axial = [&](int f, bool second) {
+                        Row<TS> r0 = row(f, 0, 0, false, true);
+                        r0.e[4] = C(f, 3).x;
+                        r0.e[5] = C(f, 3).y;
+                        TS ax[2], bx[2];
+    #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            ax[j] = (TS)0;
+                            bx[j] = c.D2c(0) * r0.e[4 + j];
+    #pragma unroll
+                            for (int k = 1; k <= 3; ++k) {
+                                const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
+                                ax[j] += c.D1(0, k) * (xp - xm);
+                                if (second)
+                                    bx[j] += c.D2(0, k) * (xp + xm);
                             }
-                            by = P::fma(P::bc(c.D2(1, k)), P::add(yp, ym), by);
-                            bz = P::fma(P::bc(c.D2(2, k)), P::add(zp, zm), bz);
                         }
-                    }
-                    g[1] = gy;
-                    g[2] = gz;
-                    if (second) {
-                        d2[1] = by;
-                        d2[2] = bz;
-                    }
-                };
-                // Eq. 8 in the (x, y) or (x, z) plane, per point, packed at the end
-                auto mix_x = [&](int f, bool in_y) -> V {
-                    Row<TS> rp[3], rm[3];
-#pragma unroll
-                    for (int k = 1; k <= 3; ++k) {
-                        const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
-                        rp[k - 1] = row(f, dz, dy, false, k == 3);
-                        rm[k - 1] = row(f, -dz, -dy, false, k == 3);
-                    }
-                    if (in_y) {
-                        V a = ld2(f, 0, 1, 0);
-                        rp[0].e[4] = a.x;
-                        rp[0].e[5] = a.y;
-                        a = ld2(f, 0, -1, 0);
-                        rm[0].e[4] = a.x;
-                        rm[0].e[5] = a.y;
-                    } else {
-                        rp[0].e[4] = colv[f][4].x;
-                        rp[0].e[5] = colv[f][4].y;
-                        rm[0].e[4] = colv[f][2].x;
-                        rm[0].e[5] = colv[f][2].y;
-                    }
-                    TS res[2];
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        TS a = (TS)0;
-#pragma unroll
-                        for (int k = 1; k <= 3; ++k) {
-                            const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
-                            const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
-                            a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
-                        }
-                        res[j] = a;
-                    }
-                    return P::mk(res[0], res[1]);
-                };
-                const V NU = P::bc(c.nu), NU3 = P::bc(c.nu3);
-                const V uc[3] = {colv[1][3], colv[2][3], colv[3][3]};
-                V acc[4], gl[3];
-                V dv = P::bc((TS)0);
-                axial(0, false);
-                gl[0] = g[0];
-                gl[1] = g[1];
-                gl[2] = g[2];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    axial(1 + i, true);
-                    V adv = P::mul(uc[0], g[0]);
-                    adv = P::fma(uc[1], g[1], adv);
-                    adv = P::fma(uc[2], g[2], adv);
-                    const V lap = P::add(P::add(d2[0], d2[1]), d2[2]);
-                    V sg = P::mul(g[0], gl[0]);
-                    sg = P::fma(g[1], gl[1], sg);
-                    sg = P::fma(g[2], gl[2], sg);
-                    V ai = P::mul(NU, P::add(lap, sg));
-                    if (i > 0)
-                        ai = P::add(ai, acc[1 + i]);
-                    ai = P::fma(adv, NEG1, ai);
-                    if (MIXED)
-                        ai = P::fma(NU3, d2[i], ai);
-                    acc[1 + i] = ai;
-                    const V nugl = P::mul(NU, gl[i]);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        if (a == i)
-                            acc[1 + a] = P::fma(g[a], nugl, acc[1 + a]);
-                        else if (a > i && i == 0)
-                            acc[1 + a] = P::mul(g[a], nugl);  // first contribution
-                        else
-                            acc[1 + a] = P::fma(g[a], nugl, acc[1 + a]);
-                    }
-                    dv = P::add(dv, g[i]);
-                    if (MIXED) {
-                        // D_ij u_i enters d_j (div u) for j != i; the pairs
-                        // with z come from the forward accumulators
-                        if (i == 0)
-                            acc[2] = P::fma(NU3, mix_x(1, true), acc[2]);  // D_xy u_x -> y
-                        else if (i == 1)
-                            acc[1] = P::fma(NU3, mix_x(2, true), acc[1]);  // D_xy u_y -> x
-                    }
-                }
-                if (MIXED) {
-                    acc[1] = P::fma(NU3, acx[0], acc[1]);  // D_xz u_z
-                    acc[2] = P::fma(NU3, acy[0], acc[2]);  // D_yz u_z
-                    acc[3] = P::fma(NU3, acz[0], acc[3]);  // D_xz u_x + D_yz u_y
-                }
-                V rs = P::bc((TS)0);
-                if (NF == 5) {
-                    axial(4, false);
-                    V t = P::mul(uc[0], g[0]);
-                    t = P::fma(uc[1], g[1], t);
-                    t = P::fma(uc[2], g[2], t);
-                    rs = P::mul(t, NEG1);
-                }
-                {
-                    V ug = P::mul(uc[0], gl[0]);
-                    ug = P::fma(uc[1], gl[1], ug);
-                    ug = P::fma(uc[2], gl[2], ug);
-                    acc[0] = P::mul(P::add(ug, dv), NEG1);
-                    const V NCS2 = P::bc(-c.cs2);
-                    const V t = P::mul(P::bc(-c.nu23), dv);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        acc[1 + a] = P::fma(t, gl[a], P::fma(NCS2, gl[a], acc[1 + a]));
-                }
-                if (!MIXED) {
-                    const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
-                    *reinterpret_cast<V *>(divf + gi) = dv;
-                    if (gdx)
-                        *reinterpret_cast<V *>(divf + gi + gdx) = dv;
-                    if (gdy) {
-                        *reinterpret_cast<V *>(divf + gi + gdy) = dv;
-                        if (gdx)
-                            *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dv;
-                    }
-                }
-                const V DT = P::bc(dt), ALPHA = P::bc(alpha), BETA = P::bc(beta);
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const V r = f < 4 ? acc[f] : rs;
-                    const V wn = first ? P::mul(DT, r) : P::fma(DT, r, P::mul(ALPHA, wv[f]));
-                    const V o2 = P::fma(BETA, wn, colv[f][3]);
-                    if (!last)
-                        *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = wn;
-                    TS *op = out + f * Ls.fpitch + go_s;
-                    *reinterpret_cast<V *>(op) = o2;
-                    if (gdx)
-                        *reinterpret_cast<V *>(op + gdx) = o2;
-                    if (gdy) {
-                        *reinterpret_cast<V *>(op + gdy) = o2;
-                        if (gdx)
-                            *reinterpret_cast<V *>(op + gdy + gdx) = o2;
-                    }
-                }
-            }
-        } else {
-            if (valid0) {
-                const int zo = z0 + o;
-                TW wv[NF][2];
-                if (need_w) {
-                    const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + o) % NW) * RG::WSLOT_PITCH) +
-                                   ty * TX + 2 * tx;
-    #pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        const VW t = *reinterpret_cast<const VW *>(ws + f * TX * TY);
-                        wv[f][0] = t.x;
-                        wv[f][1] = t.y;
-                    }
-                }
-
-                // first derivatives along x, y, z of field f for both points, plus
-                // second derivatives when `second`; centre values from colv[f][3]
-                TS g[2][3], d2[2][3];
-                auto axial = [&](int f, bool second) {
-                    Row<TS> r0 = row(f, 0, 0, false, true);
-                    r0.e[4] = colv[f][3].x;
-                    r0.e[5] = colv[f][3].y;
-                    V yp[3], ym[3];
-    #pragma unroll
-                    for (int k = 1; k <= 3; ++k) {
-                        yp[k - 1] = ld2(f, 0, k, 0);
-                        ym[k - 1] = ld2(f, 0, -k, 0);
-                    }
-    #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const TS cc = j ? colv[f][3].y : colv[f][3].x;
-                        TS ax = (TS)0, ay = (TS)0, az = (TS)0;
-                        TS bx = c.D2c(0) * cc, by = c.D2c(1) * cc, bz = c.D2c(2) * cc;
+                        g[0] = P::mk(ax[0], ax[1]);
+                        d2[0] = P::mk(bx[0], bx[1]);
+                        V gy, by, gz, bz;
     #pragma unroll
                         for (int k = 1; k <= 3; ++k) {
-                            const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
-                            const TS ypv = j ? yp[k - 1].y : yp[k - 1].x;
-                            const TS ymv = j ? ym[k - 1].y : ym[k - 1].x;
-                            const TS zp = j ? colv[f][3 + k].y : colv[f][3 + k].x;
-                            const TS zm = j ? colv[f][3 - k].y : colv[f][3 - k].x;
-                            ax += c.D1(0, k) * (xp - xm);
-                            ay += c.D1(1, k) * (ypv - ymv);
-                            az += c.D1(2, k) * (zp - zm);
+                            const V yp = ld2(f, 0, k, 0), ym = ld2(f, 0, -k, 0);
+                            const V zp = C(f, 3 + k), zm = C(f, 3 - k);
+                            const V dyv = P::fma(ym, NEG1, yp), dzv = P::fma(zm, NEG1, zp);
+                            gy = k == 1 ? P::mul(P::bc(c.D1(1, k)), dyv) : P::fma(P::bc(c.D1(1, k)), dyv, gy);
+                            gz = k == 1 ? P::mul(P::bc(c.D1(2, k)), dzv) : P::fma(P::bc(c.D1(2, k)), dzv, gz);
                             if (second) {
-                                bx += c.D2(0, k) * (xp + xm);
-                                by += c.D2(1, k) * (ypv + ymv);
-                                bz += c.D2(2, k) * (zp + zm);
+                                if (k == 1) {
+                                    by = P::mul(P::bc(c.D2c(1)), C(f, 3));
+                                    bz = P::mul(P::bc(c.D2c(2)), C(f, 3));
+                                }
+                                by = P::fma(P::bc(c.D2(1, k)), P::add(yp, ym), by);
+                                bz = P::fma(P::bc(c.D2(2, k)), P::add(zp, zm), bz);
                             }
                         }
-                        g[j][0] = ax;
-                        g[j][1] = ay;
-                        g[j][2] = az;
-                        d2[j][0] = bx;
-                        d2[j][1] = by;
-                        d2[j][2] = bz;
-                    }
-                };
-                // Eq. 8 in the (x, y) plane (in_y) or the (x, z) plane: rows or
-                // planes at +-k, x offsets +-k, for both points
-                auto mix_x = [&](int f, bool in_y, TS *res) {
-                    Row<TS> rp[3], rm[3];
-    #pragma unroll
-                    for (int k = 1; k <= 3; ++k) {
-                        const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
-                        rp[k - 1] = row(f, dz, dy, false, k == 3);
-                        rm[k - 1] = row(f, -dz, -dy, false, k == 3);
-                    }
-                    // k = 1 also needs the centre pair: x+1 for point 0, x for point 1
-                    if (in_y) {
-                        V a = ld2(f, 0, 1, 0);
-                        rp[0].e[4] = a.x;
-                        rp[0].e[5] = a.y;
-                        a = ld2(f, 0, -1, 0);
-                        rm[0].e[4] = a.x;
-                        rm[0].e[5] = a.y;
-                    } else {
-                        rp[0].e[4] = colv[f][4].x;
-                        rp[0].e[5] = colv[f][4].y;
-                        rm[0].e[4] = colv[f][2].x;
-                        rm[0].e[5] = colv[f][2].y;
-                    }
-    #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        TS a = (TS)0;
+                        g[1] = gy;
+                        g[2] = gz;
+                        if (second) {
+                            d2[1] = by;
+                            d2[2] = bz;
+                        }
+                    };
+                    // Eq. 8 in the (x, y) or (x, z) plane, per point, packed at the end
+                    auto mix_x = [&](int f, bool in_y) -> V {
+                        Row<TS> rp[3], rm[3];
     #pragma unroll
                         for (int k = 1; k <= 3; ++k) {
-                            const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
-                            const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
-                            a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
+                            const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
+                            rp[k - 1] = row(f, dz, dy, false, k == 3);
+                            rm[k - 1] = row(f, -dz, -dy, false, k == 3);
                         }
-                        res[j] = a;
-                    }
-                };
-                // Eq. 8 in the (y, z) plane: pairs at (dz, dy) = (+-k, +-k)
-                auto mix_yz = [&](int f, TS *res) {
-                    TS a0 = (TS)0, a1 = (TS)0;
+                        if (in_y) {
+                            V a = ld2(f, 0, 1, 0);
+                            rp[0].e[4] = a.x;
+                            rp[0].e[5] = a.y;
+                            a = ld2(f, 0, -1, 0);
+                            rm[0].e[4] = a.x;
+                            rm[0].e[5] = a.y;
+                        } else {
+                            rp[0].e[4] = C(f, 4).x;
+                            rp[0].e[5] = C(f, 4).y;
+                            rm[0].e[4] = C(f, 2).x;
+                            rm[0].e[5] = C(f, 2).y;
+                        }
+                        TS res[2];
     #pragma unroll
-                    for (int k = 1; k <= 3; ++k) {
-                        const V pp = ld2(f, k, k, 0), mp = ld2(f, k, -k, 0);
-                        const V mm = ld2(f, -k, -k, 0), pm = ld2(f, -k, k, 0);
-                        a0 += c.MX(2, k) * ((pp.x - mp.x) + (mm.x - pm.x));
-                        a1 += c.MX(2, k) * ((pp.y - mp.y) + (mm.y - pm.y));
-                    }
-                    res[0] = a0;
-                    res[1] = a1;
-                };
-
-                TS uc[2][3], gl[2][3], acc[2][4], dv[2];
+                        for (int j = 0; j < 2; ++j) {
+                            TS a = (TS)0;
     #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                            for (int k = 1; k <= 3; ++k) {
+                                const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
+                                const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
+                                a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
+                            }
+                            res[j] = a;
+                        }
+                        return P::mk(res[0], res[1]);
+                    };
+                    const V NU = P::bc(c.nu), NU3 = P::bc(c.nu3);
+                    const V uc[3] = {C(1, 3), C(2, 3), C(3, 3)};
+                    V acc[4], gl[3];
+                    V dv = P::bc((TS)0);
+                    axial(0, false);
+                    gl[0] = g[0];
+                    gl[1] = g[1];
+                    gl[2] = g[2];
     #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        uc[j][i] = j ? colv[1 + i][3].y : colv[1 + i][3].x;
-                        acc[j][1 + i] = (TS)0;
-                    }
-                    dv[j] = (TS)0;
-                }
-                // grad lnrho
-                axial(0, false);
-    #pragma unroll
-                for (int j = 0; j < 2; ++j)
-    #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        gl[j][a] = g[j][a];
-                // velocity components
-    #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    axial(1 + i, true);
-    #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const TS adv = uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2];
-                        const TS lap = d2[j][0] + d2[j][1] + d2[j][2];
-                        const TS sg = g[j][0] * gl[j][0] + g[j][1] * gl[j][1] + g[j][2] * gl[j][2];
-                        acc[j][1 + i] += c.nu * (lap + sg) - adv;
+                        axial(1 + i, true);
+                        V adv = P::mul(uc[0], g[0]);
+                        adv = P::fma(uc[1], g[1], adv);
+                        adv = P::fma(uc[2], g[2], adv);
+                        const V lap = P::add(P::add(d2[0], d2[1]), d2[2]);
+                        V sg = P::mul(g[0], gl[0]);
+                        sg = P::fma(g[1], gl[1], sg);
+                        sg = P::fma(g[2], gl[2], sg);
+                        V ai = P::mul(NU, P::add(lap, sg));
+                        if (i > 0)
+                            ai = P::add(ai, acc[1 + i]);
+                        ai = P::fma(adv, NEG1, ai);
                         if (MIXED)
-                            acc[j][1 + i] += c.nu3 * d2[j][i];
+                            ai = P::fma(NU3, d2[i], ai);
+                        acc[1 + i] = ai;
+                        const V nugl = P::mul(NU, gl[i]);
+    #pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (a == i)
+                                acc[1 + a] = P::fma(g[a], nugl, acc[1 + a]);
+                            else if (a > i && i == 0)
+                                acc[1 + a] = P::mul(g[a], nugl);  // first contribution
+                            else
+                                acc[1 + a] = P::fma(g[a], nugl, acc[1 + a]);
+                        }
+                        dv = P::add(dv, g[i]);
+                        if (MIXED) {
+                            // D_ij u_i enters d_j (div u) for j != i; the pairs
+                            // with z come from the forward accumulators
+                            if (i == 0)
+                                acc[2] = P::fma(NU3, mix_x(1, true), acc[2]);  // D_xy u_x -> y
+                            else if (i == 1)
+                                acc[1] = P::fma(NU3, mix_x(2, true), acc[1]);  // D_xy u_y -> x
+                        }
+                    }
+                    if constexpr (MIXED) {
+                        acc[1] = P::fma(NU3, acx[S], acc[1]);  // D_xz u_z
+                        acc[2] = P::fma(NU3, acy[S], acc[2]);  // D_yz u_z
+                        acc[3] = P::fma(NU3, acz[S], acc[3]);  // D_xz u_x + D_yz u_y
+                    }
+                    V rs = P::bc((TS)0);
+                    if (NF == 5) {
+                        axial(4, false);
+                        V t = P::mul(uc[0], g[0]);
+                        t = P::fma(uc[1], g[1], t);
+                        t = P::fma(uc[2], g[2], t);
+                        rs = P::mul(t, NEG1);
+                    }
+                    {
+                        V ug = P::mul(uc[0], gl[0]);
+                        ug = P::fma(uc[1], gl[1], ug);
+                        ug = P::fma(uc[2], gl[2], ug);
+                        acc[0] = P::mul(P::add(ug, dv), NEG1);
+                        const V NCS2 = P::bc(-c.cs2);
+                        const V t = P::mul(P::bc(-c.nu23), dv);
     #pragma unroll
                         for (int a = 0; a < 3; ++a)
-                            acc[j][1 + a] += c.nu * g[j][a] * gl[j][i];
-                        dv[j] += g[j][i];
+                            acc[1 + a] = P::fma(t, gl[a], P::fma(NCS2, gl[a], acc[1 + a]));
                     }
-                    if (MIXED) {
-                        // D_ij u_i enters d_j (div u) for j != i
-                        TS m[2];
-                        if (i == 0) {
-                            mix_x(1, true, m);  // D_xy u_x -> y
+                    if (!MIXED) {
+                        const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+                        *reinterpret_cast<V *>(divf + gi) = dv;
+                        if (gdx)
+                            *reinterpret_cast<V *>(divf + gi + gdx) = dv;
+                        if (gdy) {
+                            *reinterpret_cast<V *>(divf + gi + gdy) = dv;
+                            if (gdx)
+                                *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dv;
+                        }
+                    }
+                    const V DT = P::bc(dt), ALPHA = P::bc(alpha), BETA = P::bc(beta);
     #pragma unroll
-                            for (int j = 0; j < 2; ++j)
-                                acc[j][2] += c.nu3 * m[j];
-                            mix_x(1, false, m);  // D_xz u_x -> z
-    #pragma unroll
-                            for (int j = 0; j < 2; ++j)
-                                acc[j][3] += c.nu3 * m[j];
-                        } else if (i == 1) {
-                            mix_x(2, true, m);  // D_xy u_y -> x
-    #pragma unroll
-                            for (int j = 0; j < 2; ++j)
-                                acc[j][1] += c.nu3 * m[j];
-                            mix_yz(2, m);  // D_yz u_y -> z
-    #pragma unroll
-                            for (int j = 0; j < 2; ++j)
-                                acc[j][3] += c.nu3 * m[j];
-                        } else {
-                            mix_x(3, false, m);  // D_xz u_z -> x
-    #pragma unroll
-                            for (int j = 0; j < 2; ++j)
-                                acc[j][1] += c.nu3 * m[j];
-                            mix_yz(3, m);  // D_yz u_z -> y
-    #pragma unroll
-                            for (int j = 0; j < 2; ++j)
-                                acc[j][2] += c.nu3 * m[j];
+                    for (int f = 0; f < NF; ++f) {
+                        const V r = f < 4 ? acc[f] : rs;
+                        const V wn = first ? P::mul(DT, r) : P::fma(DT, r, P::mul(ALPHA, wv[f]));
+                        const V o2 = P::fma(BETA, wn, C(f, 3));
+                        if (!last)
+                            *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = wn;
+                        TS *op = out + f * Ls.fpitch + go_s;
+                        *reinterpret_cast<V *>(op) = o2;
+                        if (gdx)
+                            *reinterpret_cast<V *>(op + gdx) = o2;
+                        if (gdy) {
+                            *reinterpret_cast<V *>(op + gdy) = o2;
+                            if (gdx)
+                                *reinterpret_cast<V *>(op + gdy + gdx) = o2;
                         }
                     }
                 }
-                TS rs[2] = {(TS)0, (TS)0};
-                if (NF == 5) {
-                    axial(4, false);
-    #pragma unroll
-                    for (int j = 0; j < 2; ++j)
-                        rs[j] = -(uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2]);
-                }
-    #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    acc[j][0] = -(uc[j][0] * gl[j][0] + uc[j][1] * gl[j][1] + uc[j][2] * gl[j][2]) - dv[j];
-    #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        acc[j][1 + a] += -c.cs2 * gl[j][a] - c.nu23 * dv[j] * gl[j][a];
-                }
-                if (!MIXED) {
-                    V dvv;
-                    dvv.x = dv[0];
-                    dvv.y = dv[1];
-                    const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
-                    *reinterpret_cast<V *>(divf + gi) = dvv;
-                    if (gdx)
-                        *reinterpret_cast<V *>(divf + gi + gdx) = dvv;
-                    if (gdy) {
-                        *reinterpret_cast<V *>(divf + gi + gdy) = dvv;
-                        if (gdx)
-                            *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dvv;
+            } else {
+                if (valid0) {
+                    const int zo = z0 + oo;
+                    TW wv[NF][2];
+                    if (need_w) {
+                        const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + oo) % NW) * RG::WSLOT_PITCH) +
+                                       ty * TX + 2 * tx;
+        #pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            const VW t = *reinterpret_cast<const VW *>(ws + f * TX * TY);
+                            wv[f][0] = t.x;
+                            wv[f][1] = t.y;
+                        }
                     }
-                }
-    #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    TS ov[2];
-                    TW wn[2];
-    #pragma unroll
+
+                    // first derivatives along x, y, z of field f for both points, plus
+                    // second derivatives when `second`; centre values from C(f, 3)
+                    TS g[2][3], d2[2][3];
+                    auto axial = [&](int f, bool second) {
+                        Row<TS> r0 = row(f, 0, 0, false, true);
+                        r0.e[4] = C(f, 3).x;
+                        r0.e[5] = C(f, 3).y;
+                        V yp[3], ym[3];
+        #pragma unroll
+                        for (int k = 1; k <= 3; ++k) {
+                            yp[k - 1] = ld2(f, 0, k, 0);
+                            ym[k - 1] = ld2(f, 0, -k, 0);
+                        }
+        #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const TS cc = j ? C(f, 3).y : C(f, 3).x;
+                            TS ax = (TS)0, ay = (TS)0, az = (TS)0;
+                            TS bx = c.D2c(0) * cc, by = c.D2c(1) * cc, bz = c.D2c(2) * cc;
+        #pragma unroll
+                            for (int k = 1; k <= 3; ++k) {
+                                const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
+                                const TS ypv = j ? yp[k - 1].y : yp[k - 1].x;
+                                const TS ymv = j ? ym[k - 1].y : ym[k - 1].x;
+                                const TS zp = j ? C(f, 3 + k).y : C(f, 3 + k).x;
+                                const TS zm = j ? C(f, 3 - k).y : C(f, 3 - k).x;
+                                ax += c.D1(0, k) * (xp - xm);
+                                ay += c.D1(1, k) * (ypv - ymv);
+                                az += c.D1(2, k) * (zp - zm);
+                                if (second) {
+                                    bx += c.D2(0, k) * (xp + xm);
+                                    by += c.D2(1, k) * (ypv + ymv);
+                                    bz += c.D2(2, k) * (zp + zm);
+                                }
+                            }
+                            g[j][0] = ax;
+                            g[j][1] = ay;
+                            g[j][2] = az;
+                            d2[j][0] = bx;
+                            d2[j][1] = by;
+                            d2[j][2] = bz;
+                        }
+                    };
+                    // Eq. 8 in the (x, y) plane (in_y) or the (x, z) plane: rows or
+                    // planes at +-k, x offsets +-k, for both points
+                    auto mix_x = [&](int f, bool in_y, TS *res) {
+                        Row<TS> rp[3], rm[3];
+        #pragma unroll
+                        for (int k = 1; k <= 3; ++k) {
+                            const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
+                            rp[k - 1] = row(f, dz, dy, false, k == 3);
+                            rm[k - 1] = row(f, -dz, -dy, false, k == 3);
+                        }
+                        // k = 1 also needs the centre pair: x+1 for point 0, x for point 1
+                        if (in_y) {
+                            V a = ld2(f, 0, 1, 0);
+                            rp[0].e[4] = a.x;
+                            rp[0].e[5] = a.y;
+                            a = ld2(f, 0, -1, 0);
+                            rm[0].e[4] = a.x;
+                            rm[0].e[5] = a.y;
+                        } else {
+                            rp[0].e[4] = C(f, 4).x;
+                            rp[0].e[5] = C(f, 4).y;
+                            rm[0].e[4] = C(f, 2).x;
+                            rm[0].e[5] = C(f, 2).y;
+                        }
+        #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            TS a = (TS)0;
+        #pragma unroll
+                            for (int k = 1; k <= 3; ++k) {
+                                const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
+                                const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
+                                a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
+                            }
+                            res[j] = a;
+                        }
+                    };
+                    // Eq. 8 in the (y, z) plane: pairs at (dz, dy) = (+-k, +-k)
+                    auto mix_yz = [&](int f, TS *res) {
+                        TS a0 = (TS)0, a1 = (TS)0;
+        #pragma unroll
+                        for (int k = 1; k <= 3; ++k) {
+                            const V pp = ld2(f, k, k, 0), mp = ld2(f, k, -k, 0);
+                            const V mm = ld2(f, -k, -k, 0), pm = ld2(f, -k, k, 0);
+                            a0 += c.MX(2, k) * ((pp.x - mp.x) + (mm.x - pm.x));
+                            a1 += c.MX(2, k) * ((pp.y - mp.y) + (mm.y - pm.y));
+                        }
+                        res[0] = a0;
+                        res[1] = a1;
+                    };
+
+                    TS uc[2][3], gl[2][3], acc[2][4], dv[2];
+        #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        const TS r = f < 4 ? acc[j][f] : rs[j];
-                        TW wo = first ? (TW)0 : wv[f][j];
-                        rk3_update<TA, TW, TS>(first, alpha, beta, dt, (TA)r,
-                                               j ? colv[f][3].y : colv[f][3].x, wo, ov[j]);
-                        wn[j] = wo;
+        #pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            uc[j][i] = j ? C(1 + i, 3).y : C(1 + i, 3).x;
+                            acc[j][1 + i] = (TS)0;
+                        }
+                        dv[j] = (TS)0;
                     }
-                    if (!last) {
-                        VW t;
-                        t.x = wn[0];
-                        t.y = wn[1];
-                        *reinterpret_cast<VW *>(w + f * Lw.fpitch + go_w) = t;
+                    // grad lnrho
+                    axial(0, false);
+        #pragma unroll
+                    for (int j = 0; j < 2; ++j)
+        #pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            gl[j][a] = g[j][a];
+                    // velocity components
+        #pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        axial(1 + i, true);
+        #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const TS adv = uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2];
+                            const TS lap = d2[j][0] + d2[j][1] + d2[j][2];
+                            const TS sg = g[j][0] * gl[j][0] + g[j][1] * gl[j][1] + g[j][2] * gl[j][2];
+                            acc[j][1 + i] += c.nu * (lap + sg) - adv;
+                            if (MIXED)
+                                acc[j][1 + i] += c.nu3 * d2[j][i];
+        #pragma unroll
+                            for (int a = 0; a < 3; ++a)
+                                acc[j][1 + a] += c.nu * g[j][a] * gl[j][i];
+                            dv[j] += g[j][i];
+                        }
+                        if (MIXED) {
+                            // D_ij u_i enters d_j (div u) for j != i
+                            TS m[2];
+                            if (i == 0) {
+                                mix_x(1, true, m);  // D_xy u_x -> y
+        #pragma unroll
+                                for (int j = 0; j < 2; ++j)
+                                    acc[j][2] += c.nu3 * m[j];
+                                mix_x(1, false, m);  // D_xz u_x -> z
+        #pragma unroll
+                                for (int j = 0; j < 2; ++j)
+                                    acc[j][3] += c.nu3 * m[j];
+                            } else if (i == 1) {
+                                mix_x(2, true, m);  // D_xy u_y -> x
+        #pragma unroll
+                                for (int j = 0; j < 2; ++j)
+                                    acc[j][1] += c.nu3 * m[j];
+                                mix_yz(2, m);  // D_yz u_y -> z
+        #pragma unroll
+                                for (int j = 0; j < 2; ++j)
+                                    acc[j][3] += c.nu3 * m[j];
+                            } else {
+                                mix_x(3, false, m);  // D_xz u_z -> x
+        #pragma unroll
+                                for (int j = 0; j < 2; ++j)
+                                    acc[j][1] += c.nu3 * m[j];
+                                mix_yz(3, m);  // D_yz u_z -> y
+        #pragma unroll
+                                for (int j = 0; j < 2; ++j)
+                                    acc[j][2] += c.nu3 * m[j];
+                            }
+                        }
                     }
-                    V o2;
-                    o2.x = ov[0];
-                    o2.y = ov[1];
-                    TS *op = out + f * Ls.fpitch + go_s;
-                    *reinterpret_cast<V *>(op) = o2;
-                    if (gdx)
-                        *reinterpret_cast<V *>(op + gdx) = o2;
-                    if (gdy) {
-                        *reinterpret_cast<V *>(op + gdy) = o2;
+                    TS rs[2] = {(TS)0, (TS)0};
+                    if (NF == 5) {
+                        axial(4, false);
+        #pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            rs[j] = -(uc[j][0] * g[j][0] + uc[j][1] * g[j][1] + uc[j][2] * g[j][2]);
+                    }
+        #pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        acc[j][0] = -(uc[j][0] * gl[j][0] + uc[j][1] * gl[j][1] + uc[j][2] * gl[j][2]) - dv[j];
+        #pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            acc[j][1 + a] += -c.cs2 * gl[j][a] - c.nu23 * dv[j] * gl[j][a];
+                    }
+                    if (!MIXED) {
+                        V dvv;
+                        dvv.x = dv[0];
+                        dvv.y = dv[1];
+                        const long long gi = (long long)zo * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+                        *reinterpret_cast<V *>(divf + gi) = dvv;
                         if (gdx)
-                            *reinterpret_cast<V *>(op + gdy + gdx) = o2;
+                            *reinterpret_cast<V *>(divf + gi + gdx) = dvv;
+                        if (gdy) {
+                            *reinterpret_cast<V *>(divf + gi + gdy) = dvv;
+                            if (gdx)
+                                *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dvv;
+                        }
+                    }
+        #pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        TS ov[2];
+                        TW wn[2];
+        #pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const TS r = f < 4 ? acc[j][f] : rs[j];
+                            TW wo = first ? (TW)0 : wv[f][j];
+                            rk3_update<TA, TW, TS>(first, alpha, beta, dt, (TA)r,
+                                                   j ? C(f, 3).y : C(f, 3).x, wo, ov[j]);
+                            wn[j] = wo;
+                        }
+                        if (!last) {
+                            VW t;
+                            t.x = wn[0];
+                            t.y = wn[1];
+                            *reinterpret_cast<VW *>(w + f * Lw.fpitch + go_w) = t;
+                        }
+                        V o2;
+                        o2.x = ov[0];
+                        o2.y = ov[1];
+                        TS *op = out + f * Ls.fpitch + go_s;
+                        *reinterpret_cast<V *>(op) = o2;
+                        if (gdx)
+                            *reinterpret_cast<V *>(op + gdx) = o2;
+                        if (gdy) {
+                            *reinterpret_cast<V *>(op + gdy) = o2;
+                            if (gdx)
+                                *reinterpret_cast<V *>(op + gdy + gdx) = o2;
+                        }
                     }
                 }
             }
-        }
         go_s += Ls.plane;
         go_w += Lw.plane;
+    };
+
+#pragma unroll 1
+    for (int o = 0; o < nout; o += U) {
+        // all threads are done with the previous group: the slots of planes
+        // below the oldest one still read are free, and a timeout seen by
+        // any thread ends the CTA for everyone
+        if (__syncthreads_or(timeout))
+            break;
+        if (threadIdx.x == 0) {
+            tiled::fence_proxy_async();
+            const int jend = min(o + LAG + NS, nplanes);
+#pragma unroll 1
+            for (int j = issued; j < jend; ++j)
+                issue(j);
+            issued = max(issued, jend);
+            if (need_w) {
+                const int tend = min(o + NW, nout);
+#pragma unroll 1
+                for (int t = wissued; t < tend; ++t)
+                    issue_w(t);
+                wissued = max(wissued, tend);
+            }
+        }
+        plane(o, std::integral_constant<int, 0>{});
+        if constexpr (U > 1) {
+            if (o + 1 < nout)
+                plane(o + 1, std::integral_constant<int, 1>{});
+        }
+        if constexpr (U > 2) {
+            if (o + 2 < nout)
+                plane(o + 2, std::integral_constant<int, 2>{});
+        }
+        static_assert(U >= 1 && U <= 3, "one to three output planes per iteration");
 #pragma unroll
         for (int f = 0; f < NF; ++f)
 #pragma unroll
             for (int k = 0; k < 6; ++k)
-                colv[f][k] = colv[f][k + 1];
+                colv[f][k] = colv[f][k + U];
         if constexpr (FWD) {
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                acx[m] = acx[m + 1];
-                acy[m] = acy[m + 1];
-                acz[m] = acz[m + 1];
+            for (int m = 0; m < W; ++m) {
+                acx[m] = m + U < W ? acx[m + U] : PairOps<TS>::bc((TS)0);
+                acy[m] = m + U < W ? acy[m + U] : PairOps<TS>::bc((TS)0);
+                acz[m] = m + U < W ? acz[m + U] : PairOps<TS>::bc((TS)0);
             }
-            acx[6] = acy[6] = acz[6] = PairOps<TS>::bc((TS)0);
         }
     }
     const bool bad = __syncthreads_or(timeout);
@@ -816,14 +859,15 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 }
 
 // Single box: one CTA per (tile, z-chunk).
-template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK>
-__global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
+template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK, int U,
+          int MINB>
+__global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
     const Layout Lw, const Coef<TS> c, const RKStage st, const int zc, const int tiles_x,
     int *__restrict__ dev_error, const int skip_plane)
 {
-    using RG = Ring<TS, TW, NF, TX, TY, NS>;
+    using RG = Ring<TS, TW, NF, TX, TY, NS, U + 2>;
     extern __shared__ __align__(128) unsigned char smem[];
     init_barriers(reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF), NS + RG::NW);
     const int x0 = (blockIdx.x % tiles_x) * TX;
@@ -831,7 +875,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
+    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
                                                   (TA)st.alpha, (TA)st.beta, (TA)st.dt,
                                                   st.first != 0, st.last != 0, x0, y0, z0, nout,
                                                   jrun, wrun, smem, dev_error,
@@ -840,7 +884,8 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_px2(
 
 }  // namespace tiled2
 
-template <class TS, class TW, class TA, int TX, int TY, int NS, bool PK = false>
+template <class TS, class TW, class TA, int TX, int TY, int NS, bool PK = false, int U = 1,
+          int MINB = 1>
 cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
                            int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
@@ -861,8 +906,8 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
     cudaError_t e;
 #define GBFD_LAUNCH2(NFV, MIX)                                                                    \
     do {                                                                                          \
-        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK>;                      \
-        constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS>::BYTES;                          \
+        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB>;             \
+        constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS, U + 2>::BYTES;                   \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \

@@ -1,7 +1,9 @@
 // Tiled substep instantiations with FP32 storage and FP32 arithmetic: the
 // one-point-per-thread kernel (variants 0-3), the paired-load
 // two-points-per-thread kernel (variants 4-6) and the same with the two
-// points' arithmetic in packed FP32x2 instructions (variant 7).
+// points' arithmetic in packed FP32x2 instructions (variants 7-10: one, two
+// or three output planes per loop iteration; variant 10 with a five-slot
+// ring and registers capped for three CTAs per SM).
 #include "tiled2_impl.cuh"
 
 namespace gbfd {
@@ -46,9 +48,22 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         e = launch_px2_cfg<TS, TW, TA, 64, 8, 9>(b, c, st, nf, form, t.zc, v, dev_error, cache,
                                                  stream, launches);
         break;
-    default:
+    case 7:
         e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true>(b, c, st, nf, form, t.zc, v, dev_error,
                                                        cache, stream, launches);
+        break;
+    case 8:
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2>(b, c, st, nf, form, t.zc, v, dev_error,
+                                                          cache, stream, launches);
+        break;
+    case 9:
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 7, true, 3>(b, c, st, nf, form, t.zc, v, dev_error,
+                                                          cache, stream, launches);
+        break;
+    default:
+        // five-slot ring, registers capped for three CTAs per SM
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 5, true, 1, 3>(b, c, st, nf, form, t.zc, v,
+                                                             dev_error, cache, stream, launches);
         break;
     }
     if (e != cudaSuccess || form == 0)
