@@ -107,15 +107,20 @@ gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_by
 gbfd_status gbfd_destroy(gbfd_ctx *ctx);
 
 /* Copy a full state into the solver.  `src` holds nfields*nz*ny*nx values,
- * FP64 if src_is_fp64 else FP32, in host memory (src_on_device = 0; pinned
- * memory makes the copy asynchronous) or device memory (src_on_device = 1).
- * Values are converted to the storage precision.  The host buffer may be
- * reused once the call's work on the stream has completed. */
+ * FP64 if src_is_fp64 else FP32, in host memory (src_on_device = 0) or
+ * device memory (src_on_device = 1).  Pinned host memory mapped into the
+ * device address space is read in place by the copy kernel over the
+ * CPU-GPU link (asynchronous, no staging copy); pageable host memory is
+ * staged through the workspace.  Values are converted to the storage
+ * precision.  The host buffer may be reused once the call's work on the
+ * stream has completed. */
 gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, int src_is_fp64);
 
 /* Copy the current state out, same layout as gbfd_set_state.  A host
  * destination is complete when the call returns (the stream is
- * synchronised); a device destination is written asynchronously. */
+ * synchronised); pinned host memory is written in place by the copy kernel,
+ * pageable memory through the workspace.  A device destination is written
+ * asynchronously. */
 gbfd_status gbfd_get_state(gbfd_ctx *ctx, void *dst, int dst_on_device, int dst_is_fp64);
 
 /* Advance `nsteps` >= 0 full RK3 steps of length dt (> 0, finite): three
@@ -171,7 +176,15 @@ gbfd_status gbfd_diagnostics_noalloc(const void *state, int state_is_fp64, int n
  * memory, the default), 1 = simple one-thread-per-point kernels reading
  * global memory.  GBFD_OPT_TILE_CONFIG: index into the tiled kernels' tile
  * table, -1 = built-in default.  Out-of-range values -> INVALID_ARG. */
-enum { GBFD_OPT_KERNEL_PATH = 1, GBFD_OPT_TILE_CONFIG = 2, GBFD_OPT_FAULT_SKIP_COPY = 3 };
+enum {
+    GBFD_OPT_KERNEL_PATH = 1,
+    GBFD_OPT_TILE_CONFIG = 2,
+    GBFD_OPT_FAULT_SKIP_COPY = 3,
+    GBFD_OPT_HOST_PATH = 4
+};
+/* GBFD_OPT_HOST_PATH: 0 (default) = gbfd_set_state / gbfd_get_state access
+ * pinned host buffers in place from the copy kernels; 1 = always copy host
+ * buffers through the workspace with cudaMemcpyAsync. */
 /* GBFD_OPT_FAULT_SKIP_COPY (tests only): value j >= 0 makes the first CTA of
  * the two-points-per-thread tiled kernel skip the TMA copy of its local plane
  * j, so its bounded mbarrier wait gives up after about 2 s, the launch ends

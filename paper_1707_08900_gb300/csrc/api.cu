@@ -39,6 +39,7 @@ struct gbfd_ctx {
     int kernel_path;  // 0 = tiled when supported, 1 = simple
     int tile_cfg;     // index into the tiled kernel's tile table (-1 = default)
     int fault_skip;   // test-only fault injection (-1 = off)
+    int host_path;    // 0 = pinned host buffers accessed in place, 1 = always staged
     TmapCache tmaps;  // encoded TMA descriptors of the two state buffers
     bool broken;
     Coef<double> c64;
@@ -49,6 +50,20 @@ struct gbfd_ctx {
 namespace {
 
 thread_local char g_init_err[512];
+
+// Device address of a pinned (page-locked) host buffer that is mapped into
+// the device address space, or NULL for pageable host memory.  The copy
+// kernels then read or write such a buffer in place over the CPU-GPU link,
+// with no staging copy.
+const void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
 
 void set_err(gbfd_ctx *c, const char *fmt, ...)
 {
@@ -364,6 +379,7 @@ gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_by
     c->kernel_path = 0;
     c->tile_cfg = -1;
     c->fault_skip = -1;
+    c->host_path = 0;
     memset(&c->tmaps, 0, sizeof c->tmaps);
     c->broken = false;
     const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
@@ -398,6 +414,11 @@ gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value)
             break;
         ctx->kernel_path = (int)value;
         return GBFD_OK;
+    case GBFD_OPT_HOST_PATH:
+        if (value != 0 && value != 1)
+            break;
+        ctx->host_path = (int)value;
+        return GBFD_OK;
     case GBFD_OPT_FAULT_SKIP_COPY:
         if (value < -1 || value > 1000000)
             break;
@@ -427,7 +448,10 @@ gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, in
     const size_t n = (size_t)ctx->nf * ctx->p.nx * ctx->p.ny * ctx->p.nz;
     const size_t bytes = n * (src_is_fp64 ? 8 : 4);
     const void *from = src;
-    if (!src_on_device) {
+    const void *mapped = (!src_on_device && ctx->host_path == 0) ? mapped_host(src) : nullptr;
+    if (mapped) {
+        from = mapped;
+    } else if (!src_on_device) {
         cudaError_t e =
             cudaMemcpyAsync(ctx->staging, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
         if (e != cudaSuccess)
@@ -454,7 +478,8 @@ gbfd_status gbfd_get_state(gbfd_ctx *ctx, void *dst, int dst_on_device, int dst_
     }
     const size_t n = (size_t)ctx->nf * ctx->p.nx * ctx->p.ny * ctx->p.nz;
     const size_t bytes = n * (dst_is_fp64 ? 8 : 4);
-    void *to = dst_on_device ? dst : (void *)ctx->staging;
+    void *mapped = (!dst_on_device && ctx->host_path == 0) ? (void *)mapped_host(dst) : nullptr;
+    void *to = dst_on_device ? dst : (mapped ? mapped : (void *)ctx->staging);
     int nl = 0;
     cudaError_t e = launch_gather(ctx->state_region[ctx->cur] + ctx->Ls.origin, ctx->Ls, to,
                                   dst_is_fp64, ctx->nf, ctx->stream, &nl);
@@ -462,9 +487,11 @@ gbfd_status gbfd_get_state(gbfd_ctx *ctx, void *dst, int dst_on_device, int dst_
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "get_state gather");
     if (!dst_on_device) {
-        e = cudaMemcpyAsync(dst, ctx->staging, bytes, cudaMemcpyDeviceToHost, ctx->stream);
-        if (e != cudaSuccess)
-            return cuda_fail(ctx, e, "get_state copy");
+        if (!mapped) {
+            e = cudaMemcpyAsync(dst, ctx->staging, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "get_state copy");
+        }
         e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess)
             return cuda_fail(ctx, e, "get_state sync");

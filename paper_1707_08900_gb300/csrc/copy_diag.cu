@@ -1,6 +1,8 @@
 // State copies into/out of the padded layout and the FP64 diagnostics
 // reductions (mass, kinetic energy, max |u| for the time-step rule, per-field
 // rms and max, non-finite flag).
+#include <cstdint>
+
 #include "kernels.cuh"
 
 namespace gbfd {
@@ -13,51 +15,137 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-// Every padded cell (interior and ghost) of every field from the compact
-// source; ghosts take the periodic image.
-template <class TD, class TSrc>
-__global__ void k_scatter(const TSrc *__restrict__ src, TD *__restrict__ dst, Layout L)
+// Four consecutive values moved with 16-byte accesses (one float4, or two
+// double2), converted on the way.
+template <class T>
+struct Quad {
+    T v[4];
+};
+template <class T>
+__device__ __forceinline__ Quad<T> load_quad(const T *p);
+template <>
+__device__ __forceinline__ Quad<float> load_quad(const float *p)
 {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y;
-    const int z = blockIdx.z % L.nz;
-    const int f = blockIdx.z / L.nz;
-    if (X >= L.nx + 2 * GX)
-        return;
-    const int x = wrapi(X - GX, L.nx);
-    const int y = wrapi(Y - GY, L.ny);
-    const long long s = (((long long)f * L.nz + z) * L.ny + y) * L.nx + x;
-    dst[(long long)f * L.fpitch + (long long)z * L.plane + (long long)Y * L.P + X] = (TD)src[s];
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    return {{a.x, a.y, a.z, a.w}};
+}
+template <>
+__device__ __forceinline__ Quad<double> load_quad(const double *p)
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return {{a.x, a.y, b.x, b.y}};
+}
+template <class T>
+__device__ __forceinline__ void store_quad(T *p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void store_quad(float *p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store_quad(double *p, const double (&v)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
-template <class TS, class TD>
-__global__ void k_gather(const TS *__restrict__ src, TD *__restrict__ dst, Layout L)
+constexpr int COPY_WARPS = 8;  // rows per block: one warp per row
+
+// Every padded row (interior and ghost rows, interior and ghost columns) of
+// every field from the compact source; ghosts take the periodic image.  One
+// warp per destination row; VEC: source rows 16-byte aligned (nx % 4 == 0
+// and an aligned base), so the interior moves in 16-byte accesses.  The
+// source may be device memory or pinned host memory mapped into the device
+// address space.
+template <class TD, class TSrc, bool VEC>
+__global__ void __launch_bounds__(32 * COPY_WARPS) k_scatter(const TSrc *__restrict__ src,
+                                                            TD *__restrict__ dst, Layout L,
+                                                            long long nrows)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    const int z = blockIdx.z % L.nz;
-    const int f = blockIdx.z / L.nz;
-    if (x >= L.nx)
+    const long long row = (long long)blockIdx.x * COPY_WARPS + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (row >= nrows)
         return;
-    const long long d = (((long long)f * L.nz + z) * L.ny + y) * L.nx + x;
-    dst[d] = (TD)src[lidx(L, f, z, y, x)];
+    const int Y = (int)(row % L.rows);
+    const long long fz = row / L.rows;
+    const int z = (int)(fz % L.nz), f = (int)(fz / L.nz);
+    const int y = wrapi(Y - GY, L.ny);
+    const TSrc *s = src + (((long long)f * L.nz + z) * L.ny + y) * L.nx;
+    TD *d = dst + (long long)f * L.fpitch + (long long)z * L.plane + (long long)Y * L.P;
+    if (VEC) {
+        for (int x = 4 * lane; x < L.nx; x += 4 * 32) {
+            const Quad<TSrc> q = load_quad(s + x);
+            const TD v[4] = {(TD)q.v[0], (TD)q.v[1], (TD)q.v[2], (TD)q.v[3]};
+            store_quad(d + GX + x, v);
+        }
+    } else {
+        for (int x = lane; x < L.nx; x += 32)
+            d[GX + x] = (TD)s[x];
+    }
+    if (lane < 2 * GX) {
+        const int X = lane < GX ? lane : L.nx + lane;
+        d[X] = (TD)s[wrapi(X - GX, L.nx)];
+    }
+}
+
+// Interior rows back to the compact layout; one warp per row.
+template <class TS, class TD, bool VEC>
+__global__ void __launch_bounds__(32 * COPY_WARPS) k_gather(const TS *__restrict__ src,
+                                                           TD *__restrict__ dst, Layout L,
+                                                           long long nrows)
+{
+    const long long row = (long long)blockIdx.x * COPY_WARPS + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (row >= nrows)
+        return;
+    const int y = (int)(row % L.ny);
+    const long long fz = row / L.ny;
+    const int z = (int)(fz % L.nz), f = (int)(fz / L.nz);
+    const TS *s = src + lidx(L, f, z, y, 0);
+    TD *d = dst + row * L.nx;
+    if (VEC) {
+        for (int x = 4 * lane; x < L.nx; x += 4 * 32) {
+            const Quad<TS> q = load_quad(s + x);
+            const TD v[4] = {(TD)q.v[0], (TD)q.v[1], (TD)q.v[2], (TD)q.v[3]};
+            store_quad(d + x, v);
+        }
+    } else {
+        for (int x = lane; x < L.nx; x += 32)
+            d[x] = (TD)s[x];
+    }
+}
+
+// 16-byte accesses need every row start aligned: the compact side's base
+// and row length (nx % 4 == 0 keeps rows of 4- and 8-byte values on 16-byte
+// boundaries once the base is), the padded side's interior rows are 128-byte
+// aligned by construction.
+inline bool quad_ok(const void *compact, int nx)
+{
+    return ((uintptr_t)compact % 16) == 0 && nx % 4 == 0;
 }
 
 template <class TD, class TSrc>
 cudaError_t scatter_t(const TSrc *src, TD *dst, const Layout &L, int nf, cudaStream_t stream)
 {
-    dim3 block(128);
-    dim3 grid((L.nx + 2 * GX + 127) / 128, L.ny + 2 * GY, nf * L.nz);
-    k_scatter<TD, TSrc><<<grid, block, 0, stream>>>(src, dst, L);
+    const long long nrows = (long long)nf * L.nz * L.rows;
+    const dim3 grid((unsigned)((nrows + COPY_WARPS - 1) / COPY_WARPS)), block(32 * COPY_WARPS);
+    if (quad_ok(src, L.nx))
+        k_scatter<TD, TSrc, true><<<grid, block, 0, stream>>>(src, dst, L, nrows);
+    else
+        k_scatter<TD, TSrc, false><<<grid, block, 0, stream>>>(src, dst, L, nrows);
     return cudaGetLastError();
 }
 
 template <class TS, class TD>
 cudaError_t gather_t(const TS *src, TD *dst, const Layout &L, int nf, cudaStream_t stream)
 {
-    dim3 block(128);
-    dim3 grid((L.nx + 127) / 128, L.ny, nf * L.nz);
-    k_gather<TS, TD><<<grid, block, 0, stream>>>(src, dst, L);
+    const long long nrows = (long long)nf * L.nz * L.ny;
+    const dim3 grid((unsigned)((nrows + COPY_WARPS - 1) / COPY_WARPS)), block(32 * COPY_WARPS);
+    if (quad_ok(dst, L.nx))
+        k_gather<TS, TD, true><<<grid, block, 0, stream>>>(src, dst, L, nrows);
+    else
+        k_gather<TS, TD, false><<<grid, block, 0, stream>>>(src, dst, L, nrows);
     return cudaGetLastError();
 }
 

@@ -382,24 +382,22 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                     // x per point from the loaded row, y and z on the pair
                     V g[3], d2[3];
                     auto axial = [&](int f, bool second) {
-                        Row<TS> r0 = row(f, 0, 0, false, true);
-                        r0.e[4] = C(f, 3).x;
-                        r0.e[5] = C(f, 3).y;
-                        TS ax[2], bx[2];
-    #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            ax[j] = (TS)0;
-                            bx[j] = c.D2c(0) * r0.e[4 + j];
-    #pragma unroll
-                            for (int k = 1; k <= 3; ++k) {
-                                const TS xp = r0.e[4 + j + k], xm = r0.e[4 + j - k];
-                                ax[j] += c.D1(0, k) * (xp - xm);
-                                if (second)
-                                    bx[j] += c.D2(0, k) * (xp + xm);
-                            }
+                        // the x row as pairs at -4, -2, 0, +2, +4: the +-2
+                        // arms of both points line up with the pairs (packed),
+                        // the odd +-1 and +-3 arms do not (per point)
+                        const V m4 = ld2(f, 0, 0, -4), m2 = ld2(f, 0, 0, -2);
+                        const V p2 = ld2(f, 0, 0, 2), p4 = ld2(f, 0, 0, 4);
+                        const V cc = C(f, 3);
+                        const TS e1 = m4.y, e2 = m2.x, e3 = m2.y, e4 = cc.x, e5 = cc.y;
+                        const TS e6 = p2.x, e7 = p2.y, e8 = p4.x;
+                        const V ax = P::mk(c.D1(0, 1) * (e5 - e3) + c.D1(0, 3) * (e7 - e1),
+                                           c.D1(0, 1) * (e6 - e4) + c.D1(0, 3) * (e8 - e2));
+                        g[0] = P::fma(P::bc(c.D1(0, 2)), P::fma(m2, NEG1, p2), ax);
+                        if (second) {
+                            const V bx = P::mk(c.D2c(0) * e4 + c.D2(0, 1) * (e5 + e3) + c.D2(0, 3) * (e7 + e1),
+                                               c.D2c(0) * e5 + c.D2(0, 1) * (e6 + e4) + c.D2(0, 3) * (e8 + e2));
+                            d2[0] = P::fma(P::bc(c.D2(0, 2)), P::add(p2, m2), bx);
                         }
-                        g[0] = P::mk(ax[0], ax[1]);
-                        d2[0] = P::mk(bx[0], bx[1]);
                         V gy, by, gz, bz;
     #pragma unroll
                         for (int k = 1; k <= 3; ++k) {
@@ -424,41 +422,32 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                             d2[2] = bz;
                         }
                     };
-                    // Eq. 8 in the (x, y) or (x, z) plane, per point, packed at the end
-                    auto mix_x = [&](int f, bool in_y) -> V {
-                        Row<TS> rp[3], rm[3];
+                    // Eq. 8 in the (x, y) plane: D_xy f = sum_k MX_k [h_k(y+k) - h_k(y-k)]
+                    // with h_k the x-difference f(x+k) - f(x-k) of a row; h_2 is
+                    // packed, h_1 and h_3 straddle the pairs
+                    auto mix_xy = [&](int f) -> V {
+                        V a;
     #pragma unroll
                         for (int k = 1; k <= 3; ++k) {
-                            const int dz = in_y ? 0 : k, dy = in_y ? k : 0;
-                            rp[k - 1] = row(f, dz, dy, false, k == 3);
-                            rm[k - 1] = row(f, -dz, -dy, false, k == 3);
-                        }
-                        if (in_y) {
-                            V a = ld2(f, 0, 1, 0);
-                            rp[0].e[4] = a.x;
-                            rp[0].e[5] = a.y;
-                            a = ld2(f, 0, -1, 0);
-                            rm[0].e[4] = a.x;
-                            rm[0].e[5] = a.y;
-                        } else {
-                            rp[0].e[4] = C(f, 4).x;
-                            rp[0].e[5] = C(f, 4).y;
-                            rm[0].e[4] = C(f, 2).x;
-                            rm[0].e[5] = C(f, 2).y;
-                        }
-                        TS res[2];
+                            V h[2];
     #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            TS a = (TS)0;
-    #pragma unroll
-                            for (int k = 1; k <= 3; ++k) {
-                                const TS pp = rp[k - 1].e[4 + j + k], mp = rp[k - 1].e[4 + j - k];
-                                const TS mm = rm[k - 1].e[4 + j - k], pm = rm[k - 1].e[4 + j + k];
-                                a += c.MX(in_y ? 0 : 1, k) * ((pp - mp) + (mm - pm));
+                            for (int sgn = 0; sgn < 2; ++sgn) {
+                                const int dy = sgn ? -k : k;
+                                const V m2 = ld2(f, 0, dy, -2), p2 = ld2(f, 0, dy, 2);
+                                if (k == 1) {
+                                    const V cc = ld2(f, 0, dy, 0);
+                                    h[sgn] = P::mk(cc.y - m2.y, p2.x - cc.x);
+                                } else if (k == 2) {
+                                    h[sgn] = P::fma(m2, NEG1, p2);
+                                } else {
+                                    const V m4 = ld2(f, 0, dy, -4), p4 = ld2(f, 0, dy, 4);
+                                    h[sgn] = P::mk(p2.y - m4.y, p4.x - m2.x);
+                                }
                             }
-                            res[j] = a;
+                            const V d = P::fma(h[1], NEG1, h[0]);
+                            a = k == 1 ? P::mul(P::bc(c.MX(0, k)), d) : P::fma(P::bc(c.MX(0, k)), d, a);
                         }
-                        return P::mk(res[0], res[1]);
+                        return a;
                     };
                     const V NU = P::bc(c.nu), NU3 = P::bc(c.nu3);
                     const V uc[3] = {C(1, 3), C(2, 3), C(3, 3)};
@@ -500,9 +489,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                             // D_ij u_i enters d_j (div u) for j != i; the pairs
                             // with z come from the forward accumulators
                             if (i == 0)
-                                acc[2] = P::fma(NU3, mix_x(1, true), acc[2]);  // D_xy u_x -> y
+                                acc[2] = P::fma(NU3, mix_xy(1), acc[2]);  // D_xy u_x -> y
                             else if (i == 1)
-                                acc[1] = P::fma(NU3, mix_x(2, true), acc[1]);  // D_xy u_y -> x
+                                acc[1] = P::fma(NU3, mix_xy(2), acc[1]);  // D_xy u_y -> x
                         }
                     }
                     if constexpr (MIXED) {

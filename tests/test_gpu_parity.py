@@ -299,3 +299,55 @@ def test_full_size_window_against_oracle(n, precision):
         err = rel_l2(gw, ref)
         tol = FP64_TOL if precision == "fp64" else FP32_TOL
         assert np.all(err <= tol), (lo, err)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_host_paths_agree(precision):
+    """gbfd_set_state / gbfd_get_state through every host route give the same
+    bits: pinned host buffers accessed in place by the copy kernels (16-byte
+    aligned, and misaligned by one element so the per-element path runs),
+    pageable host memory, the staged copy (GBFD_OPT_HOST_PATH = 1) and device
+    memory."""
+    from paper_1707_08900_gb300 import gbfd
+    shape = (12, 20, 28)  # ghost rows wrap; row counts not multiples of the copy block
+    st = inputs.random_state(shape, 5)
+    full = (st.shape[0],) + shape
+    n = st.size
+
+    def pinned(dtype, off):
+        return torch.empty(n + 1, dtype=dtype).pin_memory()[off:off + n].view(full)
+
+    results = {}
+    for path in (1, 0):
+        s = _solver(shape, precision=precision)
+        s.set_option(gbfd.GBFD_OPT_HOST_PATH, path)
+        for dtype in (torch.float32, torch.float64):
+            for off in (0, 1):
+                src = pinned(dtype, off)
+                src.copy_(torch.from_numpy(st))
+                s.set_state(src)
+                s.rk3_step(1e-3, 1)
+                r64, r32 = [], []
+                for odt, acc in ((torch.float64, r64), (torch.float32, r32)):
+                    for ooff in (0, 1):
+                        o = pinned(odt, ooff)
+                        o.fill_(float("nan"))
+                        s.get_state(out=o)
+                        acc.append(o.numpy().copy())
+                r64.append(s.get_state(fp64=True))
+                r32.append(s.get_state(fp64=False))
+                dev = torch.empty(full, dtype=torch.float64, device="cuda")
+                s.get_state(out=dev)
+                torch.cuda.synchronize()
+                r64.append(dev.cpu().numpy())
+                for r in r64[1:]:
+                    assert np.array_equal(r, r64[0])
+                for r in r32:
+                    assert np.array_equal(r, r64[0].astype(np.float32))
+                results[(path, dtype, off)] = r64[0]
+        s.close()
+    for dtype in (torch.float32, torch.float64):
+        base = results[(1, dtype, 0)]
+        assert np.all(np.isfinite(base))
+        for key in ((1, dtype, 1), (0, dtype, 0), (0, dtype, 1)):
+            assert np.array_equal(results[key], base), key
