@@ -60,7 +60,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_batch_substep(
         const Layout L = B->L;
         const float dt = dts[item.x];
         const int nout = min(zc, L.nz - item.w);
-        if (!tiled2::run_column<float, float, float, NF, true, TX, TY, NS, true, U>(
+        if (!tiled2::run_column<float, float, float, NF, true, TX, TY, NS, true, U, false>(
                 &B->tm_state[parity], &B->tm_w, B->state[parity ^ 1], B->w, nullptr, L, L, c,
                 (float)st.alpha, (float)st.beta, dt, st.first != 0, st.last != 0, item.y, item.z,
                 item.w, nout, jrun, wrun, smem, dev_error))

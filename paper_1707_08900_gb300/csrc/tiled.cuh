@@ -16,6 +16,7 @@ struct TileConfig {
     int px;      // points per thread along x (1, or 2 with paired loads)
     int pk;      // 0: scalar arithmetic; n > 0: packed FP32x2 arithmetic with
                  // n output planes per loop iteration
+    int tm;      // 1: in-plane work at plane arrival, results carried through TMEM
 };
 
 // Number of z-chunk lengths offered per (tx, ty, ns) variant; table index

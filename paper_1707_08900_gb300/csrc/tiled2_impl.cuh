@@ -110,7 +110,7 @@ __device__ __forceinline__ void init_barriers(uint64_t *bars, int n)
 // advanced on return.  Returns false when a bounded wait gave up (after
 // recording it and draining the copies in flight).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK,
-          int U, class CoefT>
+          int U, bool WG, class CoefT>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            TS *__restrict__ out, TW *__restrict__ w,
                                            TS *__restrict__ divf, const Layout &Ls,
@@ -121,7 +121,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                                            unsigned char *smem, int *dev_error,
                                            const int skip_plane = -1)
 {
-    using RG = Ring<TS, TW, NF, TX, TY, NS, U + 2>;
+    // WG: u-tilde read straight from global memory (no u-tilde ring)
+    static_assert(!WG || PK, "global u-tilde reads only in the packed form");
+    using RG = Ring<TS, TW, NF, TX, TY, NS, WG ? 0 : U + 2>;
     using tiled::mbar_wait;
     using V = typename V2<TS>::t;
     using VW = typename V2<TW>::t;
@@ -159,10 +161,12 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         tiled::tma_load_4d(smem + slot * RG::SLOT_PITCH, tmap, &bars[slot], x0, y0, z, 0);
     };
     auto issue_w = [&](int o) {
-        const int slot = (wrun + o) % NW;
-        tiled::mbar_expect_tx(&wbars[slot], RG::WSLOT_BYTES);
-        tiled::tma_load_4d(wsm + slot * RG::WSLOT_PITCH, wmap, &wbars[slot], x0 + GX, y0 + GY,
-                           z0 + o, 0);
+        if constexpr (!WG) {
+            const int slot = (wrun + o) % NW;
+            tiled::mbar_expect_tx(&wbars[slot], RG::WSLOT_BYTES);
+            tiled::tma_load_4d(wsm + slot * RG::WSLOT_PITCH, wmap, &wbars[slot], x0 + GX, y0 + GY,
+                               z0 + o, 0);
+        }
     };
     // The forward-accumulated and 19-point forms read only the centre plane
     // and the arriving plane from shared memory, so the ring need not keep
@@ -177,7 +181,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         for (int j = 0; j < NS && j < nplanes; ++j)
             issue(j);
         issued = min(NS, nplanes);
-        if (need_w) {
+        if (need_w && !WG) {
 #pragma unroll 1
             for (int o = 0; o < NW && o < nout; ++o)
                 issue_w(o);
@@ -309,7 +313,17 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         if (!mbar_wait(&bars[qn % NS], (qn / NS) & 1))
             timeout = true;
         waited = oo + 2 * R + 1;
-        if (need_w) {
+        V wg[WG ? NF : 1];
+        (void)wg;
+        if constexpr (WG) {
+            // u-tilde of this plane from global memory, issued before the
+            // stencil work so its latency overlaps it
+            if (need_w && valid0) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    wg[f] = *reinterpret_cast<const V *>(w + f * Lw.fpitch + go_w);
+            }
+        } else if (need_w) {
             const int qw = wrun + oo;
             if (!mbar_wait(&wbars[qw % NW], (qw / NW) & 1))
                 timeout = true;
@@ -371,7 +385,11 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                     const int zo = z0 + oo;
                     const V NEG1 = P::bc((TS)-1);
                     V wv[NF];
-                    if (need_w) {
+                    if constexpr (WG) {
+    #pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            wv[f] = wg[f];
+                    } else if (need_w) {
                         const TW *ws = reinterpret_cast<const TW *>(wsm + ((wrun + oo) % NW) * RG::WSLOT_PITCH) +
                                        ty * TX + 2 * tx;
     #pragma unroll
@@ -801,7 +819,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
             for (int j = issued; j < jend; ++j)
                 issue(j);
             issued = max(issued, jend);
-            if (need_w) {
+            if (need_w && !WG) {
                 const int tend = min(o + NW, nout);
 #pragma unroll 1
                 for (int t = wissued; t < tend; ++t)
@@ -839,8 +857,10 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         // drain the copies still in flight into this CTA's shared memory
         for (int j = waited; j < issued; ++j)
             (void)mbar_wait(&bars[(jrun + j) % NS], ((jrun + j) / NS) & 1);
-        for (int o = wwaited; o < wissued; ++o)
-            (void)mbar_wait(&wbars[(wrun + o) % NW], ((wrun + o) / NW) & 1);
+        if constexpr (!WG) {
+            for (int o = wwaited; o < wissued; ++o)
+                (void)mbar_wait(&wbars[(wrun + o) % NW], ((wrun + o) / NW) & 1);
+        }
     }
     jrun += nplanes;
     wrun += need_w ? nout : 0;
@@ -849,14 +869,14 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 
 // Single box: one CTA per (tile, z-chunk).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK, int U,
-          int MINB>
+          int MINB, bool WG>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
     const Layout Lw, const Coef<TS> c, const RKStage st, const int zc, const int tiles_x,
     int *__restrict__ dev_error, const int skip_plane)
 {
-    using RG = Ring<TS, TW, NF, TX, TY, NS, U + 2>;
+    using RG = Ring<TS, TW, NF, TX, TY, NS, WG ? 0 : U + 2>;
     extern __shared__ __align__(128) unsigned char smem[];
     init_barriers(reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF), NS + RG::NW);
     const int x0 = (blockIdx.x % tiles_x) * TX;
@@ -864,7 +884,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
+    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U, WG>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
                                                   (TA)st.alpha, (TA)st.beta, (TA)st.dt,
                                                   st.first != 0, st.last != 0, x0, y0, z0, nout,
                                                   jrun, wrun, smem, dev_error,
@@ -874,7 +894,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
 }  // namespace tiled2
 
 template <class TS, class TW, class TA, int TX, int TY, int NS, bool PK = false, int U = 1,
-          int MINB = 1>
+          int MINB = 1, bool WG = false>
 cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
                            int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
@@ -895,8 +915,8 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
     cudaError_t e;
 #define GBFD_LAUNCH2(NFV, MIX)                                                                    \
     do {                                                                                          \
-        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB>;             \
-        constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS, U + 2>::BYTES;                   \
+        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB, WG>;         \
+        constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS, WG ? 0 : U + 2>::BYTES;          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \

@@ -3,8 +3,10 @@
 // two-points-per-thread kernel (variants 4-6) and the same with the two
 // points' arithmetic in packed FP32x2 instructions (variants 7-10: one, two
 // or three output planes per loop iteration; variant 10 with a five-slot
-// ring and registers capped for three CTAs per SM).
-#include "tiled2_impl.cuh"
+// ring and registers capped for three CTAs per SM) and, for the 55-point
+// form, the kernel that does the in-plane work at plane arrival and carries
+// its results through TMEM (variants 11-12).
+#include "tiled3_impl.cuh"
 
 namespace gbfd {
 
@@ -60,10 +62,43 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         e = launch_px2_cfg<TS, TW, TA, 32, 8, 7, true, 3>(b, c, st, nf, form, t.zc, v, dev_error,
                                                           cache, stream, launches);
         break;
-    default:
+    case 10:
         // five-slot ring, registers capped for three CTAs per SM
         e = launch_px2_cfg<TS, TW, TA, 32, 8, 5, true, 1, 3>(b, c, st, nf, form, t.zc, v,
                                                              dev_error, cache, stream, launches);
+        break;
+    case 13:
+        // six-slot ring, u-tilde read from global memory, three CTAs per SM
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 6, true, 1, 3, true>(b, c, st, nf, form, t.zc, v,
+                                                                   dev_error, cache, stream,
+                                                                   launches);
+        break;
+    case 14:
+        // the default kernel with u-tilde read from global memory
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2, 1, true>(b, c, st, nf, form, t.zc, v,
+                                                                   dev_error, cache, stream,
+                                                                   launches);
+        break;
+    case 15:
+        e = launch_px2_cfg<TS, TW, TA, 32, 16, 8, true, 2>(b, c, st, nf, form, t.zc, v, dev_error,
+                                                           cache, stream, launches);
+        break;
+    case 16:
+        e = launch_px2_cfg<TS, TW, TA, 64, 8, 8, true, 2>(b, c, st, nf, form, t.zc, v, dev_error,
+                                                          cache, stream, launches);
+        break;
+    default:  // 11, 12
+        // in-plane work at arrival, carried through TMEM (55-point form; the
+        // 19-point form runs the two-plane packed kernel on the same tile)
+        if (form != 0)
+            e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2>(b, c, st, nf, form, t.zc, v,
+                                                              dev_error, cache, stream, launches);
+        else if (t.ns == 4)
+            e = launch_tm_cfg<32, 8, 4>(b, c, st, nf, t.zc, v, dev_error, cache, stream,
+                                        launches);
+        else
+            e = launch_tm_cfg<32, 8, 6>(b, c, st, nf, t.zc, v, dev_error, cache, stream,
+                                        launches);
         break;
     }
     if (e != cudaSuccess || form == 0)
