@@ -101,18 +101,20 @@ __device__ __forceinline__ void fence_smem_to_async()
 }
 
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per
-// thread) into r[0..15].
+// thread) into r[0..15].  The wait sits in the same statement as the load:
+// the destination registers are not valid before it completes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *r)
 {
     uint32_t v[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
           "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i)
         r[i] = __uint_as_float(v[i]);

@@ -16,12 +16,14 @@
 //     - the per-plane differences h_k = f(x+k) - f(x-k), g_k = f(y+k) -
 //       f(y-k) of the z-paired cross terms, accumulated forward into the
 //       register windows of the outputs k planes below and above,
-//   and stores the 36 in-plane results of its two points into its own TMEM
-//   lane (a ring of four plane slots);
+//   and from these the whole part of the right-hand side (Eqs. 1-3) that
+//   needs no z derivative; it stores that part and the five in-plane
+//   quantities the z part multiplies (20 floats for its two points) into
+//   its own TMEM lane (a ring of four plane slots);
 // * three planes later plane p is the centre of output plane p: the thread
-//   loads the in-plane results back from TMEM, takes the z derivatives from
-//   its register column window, and applies the right-hand side (Eqs. 1-3,
-//   grouped as in the two-point kernel) and the RK3 update (Eq. 10).
+//   loads them back from TMEM, takes the z derivatives from its register
+//   column window, completes the right-hand side and applies the RK3
+//   update (Eq. 10).
 // Shared memory therefore holds only the arriving planes, and each row of
 // the halo box is read once per plane instead of twice.
 #pragma once
@@ -34,23 +36,22 @@ namespace tiled3 {
 
 using tiled2::PairOps;
 
-__device__ __forceinline__ void tm_st32(uint32_t taddr, const float *v)
+// Warp-collective TMEM accesses of the 32x32b shape: each thread moves n
+// consecutive 32-bit columns of its own lane.  Each statement also waits for
+// its own completion, so the compiler never sees a load's destination (or a
+// store's source) registers before the hardware is done with them.
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float *v)
 {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {"
-                 "%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-                 "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32"
-                 "};" ::"r"(taddr),
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {"
+                 "%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16"
+                 "};\n\t"
+                 "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
                  "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                  "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
                  "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
                  "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
                  "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-                 "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
-                 "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
-                 "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
-                 "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
-                 "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
-                 "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+                 "r"(__float_as_uint(v[15]))
                  : "memory");
 }
 
@@ -58,29 +59,27 @@ __device__ __forceinline__ void tm_st4(uint32_t taddr, const float *v)
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {"
                  "%1, %2, %3, %4"
-                 "};" ::"r"(taddr),
+                 "};\n\t"
+                 "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
                  "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                  "r"(__float_as_uint(v[3]))
                  : "memory");
 }
 
-__device__ __forceinline__ void tm_ld32(uint32_t taddr, float *v)
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float *v)
 {
-    uint32_t u[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {"
-                 "%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31"
-                 "}, [%32];"
+    uint32_t u[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {"
+                 "%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15"
+                 "}, [%16];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
                  : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]),
                    "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]),
-                   "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]),
-                   "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
-                   "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]),
-                   "=r"(u[30]), "=r"(u[31])
+                   "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
                  : "r"(taddr)
                  : "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < 16; ++i)
         v[i] = __uint_as_float(u[i]);
 }
 
@@ -89,7 +88,8 @@ __device__ __forceinline__ void tm_ld4(uint32_t taddr, float *v)
     uint32_t u[4];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {"
                  "%0, %1, %2, %3"
-                 "}, [%4];"
+                 "}, [%4];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
                  : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3])
                  : "r"(taddr)
                  : "memory");
@@ -98,26 +98,19 @@ __device__ __forceinline__ void tm_ld4(uint32_t taddr, float *v)
         v[i] = __uint_as_float(u[i]);
 }
 
-__device__ __forceinline__ void tm_wait_st()
-{
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tm_wait_ld()
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
-// TMEM columns: per plane slot the in-plane results of one thread's two
-// points, as floats: D1x, D1y of field f at 4f; D2x, D2y of u_i at
-// 4 NF + 4i; D_xy u_x, D_xy u_y at 4 NF + 12.  Four slots of 64 columns.
-template <int NF>
+// TMEM columns: per plane slot, for one thread's two points (pairs), the
+// part of the right-hand side that needs no z derivative and the in-plane
+// quantities the z part multiplies:
+//   P_f (f < NF) at 2f, d_x lnrho at 10, d_y lnrho at 12, the in-plane
+//   divergence d_x u_x + d_y u_y at 14, d_x u_z at 16, d_y u_z at 18.
+// Four slots of 32 columns.
 struct TmLayout {
-    static constexpr int FLOATS = 4 * NF + 16;  // 36 or 32
-    static constexpr int D2 = 4 * NF;
-    static constexpr int XY = 4 * NF + 12;
-    static constexpr int SLOT_COLS = 64;  // slots on 64-column boundaries
+    static constexpr int FLOATS = 20;
+    static constexpr int GLX = 10, GLY = 12, DIV = 14, DZX = 16, DZY = 18;
+    static constexpr int SLOT_COLS = 32;
     static constexpr int NSLOT = 4;
-    static constexpr int COLS = 256;  // allocation: a power of two >= NSLOT * SLOT_COLS
+    static constexpr int COLS = 128;  // allocation: a power of two >= NSLOT * SLOT_COLS
 };
 
 // Shared memory: the two-point ring (state slots, u-tilde slots, mbarriers)
@@ -141,7 +134,7 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
                                               int *dev_error, const int skip_plane = -1)
 {
     using RG = tiled2::Ring<float, float, NF, TX, TY, NS, 3>;
-    using TL = TmLayout<NF>;
+    using TL = TmLayout;
     using V = float2;
     using P = PairOps<float>;
     using tiled::mbar_wait;
@@ -253,8 +246,15 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
 
         // ---- arrival of local plane j (output plane j - 3 relative to z0)
         const bool centre = j >= R && j < nout + R;
+        const V NU = P::bc(c.nu), NU3 = P::bc(c.nu3);
         {
-            float r[TL::FLOATS];
+            // in-plane (x, y) derivatives of each field, combined at once into
+            // the part of the right-hand side they fix (Eqs. 1-3 with
+            // 2 S.grad lnrho written out); u_x, u_y of this plane are its
+            // own column values
+            const V ux = colv[1][6], uy = colv[2][6];
+            const V NU43 = P::bc(c.nu + c.nu3), NU2 = P::bc(2.f * c.nu);
+            V Pf[5], glx, gly, dvxy, dzx, dzy;
             V hxx[3];  // x-differences of u_x, kept for the z-paired term
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -262,6 +262,7 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
                 const V cc = colv[f][6];
                 const bool need_x = centre || f == 1 || f == 3;
                 const bool need_y = centre || f == 2 || f == 3;
+                V d1x, d1y, d2x, d2y, dxy;
                 if (need_x) {
                     const V m4 = at(f, 0, -4), m2 = at(f, 0, -2), p2 = at(f, 0, 2), p4 = at(f, 0, 4);
                     // h_k = f(x+k) - f(x-k) for both points; h_2 lines up
@@ -270,21 +271,16 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
                     const V h2 = P::fma(m2, NEG1, p2);
                     const V h3 = P::mk(p2.y - m4.y, p4.x - m2.x);
                     if (centre) {
-                        V d1 = P::mul(P::bc(c.D1(0, 1)), h1);
-                        d1 = P::fma(P::bc(c.D1(0, 2)), h2, d1);
-                        d1 = P::fma(P::bc(c.D1(0, 3)), h3, d1);
-                        r[4 * f] = d1.x;
-                        r[4 * f + 1] = d1.y;
+                        d1x = P::mul(P::bc(c.D1(0, 1)), h1);
+                        d1x = P::fma(P::bc(c.D1(0, 2)), h2, d1x);
+                        d1x = P::fma(P::bc(c.D1(0, 3)), h3, d1x);
                         if (vel) {
                             const V s1 = P::mk(cc.y + m2.y, p2.x + cc.x);
-                            const V s2 = P::add(p2, m2);
                             const V s3 = P::mk(p2.y + m4.y, p4.x + m2.x);
-                            V d2 = P::mul(P::bc(c.D2c(0)), cc);
-                            d2 = P::fma(P::bc(c.D2(0, 1)), s1, d2);
-                            d2 = P::fma(P::bc(c.D2(0, 2)), s2, d2);
-                            d2 = P::fma(P::bc(c.D2(0, 3)), s3, d2);
-                            r[TL::D2 + 4 * (f - 1)] = d2.x;
-                            r[TL::D2 + 4 * (f - 1) + 1] = d2.y;
+                            d2x = P::mul(P::bc(c.D2c(0)), cc);
+                            d2x = P::fma(P::bc(c.D2(0, 1)), s1, d2x);
+                            d2x = P::fma(P::bc(c.D2(0, 2)), P::add(p2, m2), d2x);
+                            d2x = P::fma(P::bc(c.D2(0, 3)), s3, d2x);
                         }
                     }
                     if (f == 1) {
@@ -303,33 +299,25 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
                     }
                 }
                 if (need_y) {
-                    V yp[3], ym[3];
+                    V yp[3], ym[3], gk[3];
 #pragma unroll
                     for (int k = 1; k <= 3; ++k) {
                         yp[k - 1] = at(f, k, 0);
                         ym[k - 1] = at(f, -k, 0);
+                        gk[k - 1] = P::fma(ym[k - 1], NEG1, yp[k - 1]);
                     }
-                    V gk[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        gk[k] = P::fma(ym[k], NEG1, yp[k]);
                     if (centre) {
-                        V d1 = P::mul(P::bc(c.D1(1, 1)), gk[0]);
-                        d1 = P::fma(P::bc(c.D1(1, 2)), gk[1], d1);
-                        d1 = P::fma(P::bc(c.D1(1, 3)), gk[2], d1);
-                        r[4 * f + 2] = d1.x;
-                        r[4 * f + 3] = d1.y;
+                        d1y = P::mul(P::bc(c.D1(1, 1)), gk[0]);
+                        d1y = P::fma(P::bc(c.D1(1, 2)), gk[1], d1y);
+                        d1y = P::fma(P::bc(c.D1(1, 3)), gk[2], d1y);
                         if (vel) {
-                            V d2 = P::mul(P::bc(c.D2c(1)), cc);
+                            d2y = P::mul(P::bc(c.D2c(1)), cc);
 #pragma unroll
                             for (int k = 1; k <= 3; ++k)
-                                d2 = P::fma(P::bc(c.D2(1, k)), P::add(yp[k - 1], ym[k - 1]), d2);
-                            r[TL::D2 + 4 * (f - 1) + 2] = d2.x;
-                            r[TL::D2 + 4 * (f - 1) + 3] = d2.y;
+                                d2y = P::fma(P::bc(c.D2(1, k)), P::add(yp[k - 1], ym[k - 1]), d2y);
                         }
                         if (f == 1 || f == 2) {
                             // D_xy f = sum_k MX_k [h_k(y+k) - h_k(y-k)], rows y+-k
-                            V a;
 #pragma unroll
                             for (int k = 1; k <= 3; ++k) {
                                 V h[2];
@@ -348,11 +336,9 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
                                     }
                                 }
                                 const V dd = P::fma(h[1], NEG1, h[0]);
-                                a = k == 1 ? P::mul(P::bc(c.MX(0, k)), dd)
-                                           : P::fma(P::bc(c.MX(0, k)), dd, a);
+                                dxy = k == 1 ? P::mul(P::bc(c.MX(0, k)), dd)
+                                             : P::fma(P::bc(c.MX(0, k)), dd, dxy);
                             }
-                            r[TL::XY + 2 * (f - 1)] = a.x;
-                            r[TL::XY + 2 * (f - 1) + 1] = a.y;
                         }
                     }
                     if (f == 2) {
@@ -374,15 +360,66 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
                         }
                     }
                 }
+                if (centre) {
+                    // -u_x d_x f - u_y d_y f: the in-plane advection of every field
+                    const V adv = P::fma(uy, d1y, P::mul(ux, d1x));
+                    if (f == 0) {
+                        glx = d1x;
+                        gly = d1y;
+                        Pf[0] = P::mul(adv, NEG1);
+                    } else if (f == 1) {
+                        // u_x: nu (4/3 D_xx + D_yy) u_x (Laplacian and the diagonal of
+                        // grad div), nu (2 d_x u_x d_x lnrho + d_y u_x d_y lnrho)
+                        Pf[0] = P::fma(d1x, NEG1, Pf[0]);
+                        dvxy = d1x;
+                        V p = P::fma(NU43, d2x, P::fma(NU, d2y, P::mul(adv, NEG1)));
+                        p = P::fma(NU2, P::mul(d1x, glx), p);
+                        Pf[1] = P::fma(NU, P::mul(d1y, gly), p);
+                        // into u_y: nu d_y u_x d_x lnrho + (nu/3) D_xy u_x
+                        Pf[2] = P::fma(NU, P::mul(d1y, glx), P::mul(NU3, dxy));
+                    } else if (f == 2) {
+                        Pf[0] = P::fma(d1y, NEG1, Pf[0]);
+                        dvxy = P::add(dvxy, d1y);
+                        V p = P::fma(NU, d2x, P::fma(NU43, d2y, P::fma(adv, NEG1, Pf[2])));
+                        p = P::fma(NU, P::mul(d1x, glx), p);
+                        Pf[2] = P::fma(NU2, P::mul(d1y, gly), p);
+                        // into u_x: nu d_x u_y d_y lnrho + (nu/3) D_xy u_y
+                        Pf[1] = P::fma(NU, P::mul(d1x, gly), P::fma(NU3, dxy, Pf[1]));
+                    } else if (f == 3) {
+                        V p = P::fma(NU, P::add(d2x, d2y), P::mul(adv, NEG1));
+                        p = P::fma(NU, P::mul(d1x, glx), p);
+                        Pf[3] = P::fma(NU, P::mul(d1y, gly), p);
+                        dzx = d1x;
+                        dzy = d1y;
+                    } else {
+                        Pf[4] = P::mul(adv, NEG1);
+                    }
+                }
             }
             if (centre) {
-                // slot j % 4 last held plane j - 4, read (and waited for) in
-                // iteration j - 1
+                // -c_s^2 d_i lnrho - (2/3) nu (d_x u_x + d_y u_y) d_i lnrho, i = x, y
+                const V NCS2 = P::bc(-c.cs2), N23 = P::bc(-c.nu23);
+                Pf[1] = P::fma(NCS2, glx, P::fma(P::mul(N23, dvxy), glx, Pf[1]));
+                Pf[2] = P::fma(NCS2, gly, P::fma(P::mul(N23, dvxy), gly, Pf[2]));
+                if (NF == 4)
+                    Pf[4] = P::bc(0.f);
+                float r[TL::FLOATS];
+#pragma unroll
+                for (int f = 0; f < 5; ++f) {
+                    r[2 * f] = Pf[f].x;
+                    r[2 * f + 1] = Pf[f].y;
+                }
+                const V rest[5] = {glx, gly, dvxy, dzx, dzy};
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    r[TL::GLX + 2 * i] = rest[i].x;
+                    r[TL::GLX + 2 * i + 1] = rest[i].y;
+                }
+                // slot j % 4 last held plane j - 4, read in iteration j - 1
                 const uint32_t ta = trow + (uint32_t)((j % TL::NSLOT) * TL::SLOT_COLS);
                 __syncwarp();  // the TMEM accesses are warp-collective
-                tm_st32(ta, r);
-                if (TL::FLOATS > 32)
-                    tm_st4(ta + 32, r + 32);
+                tm_st16(ta, r);
+                tm_st4(ta + 16, r + 16);
             }
         }
 
@@ -391,12 +428,9 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
             float qv[TL::FLOATS];
             {
                 __syncwarp();
-                tm_wait_st();
                 const uint32_t ta = trow + (uint32_t)(((o + R) % TL::NSLOT) * TL::SLOT_COLS);
-                tm_ld32(ta, qv);
-                if (TL::FLOATS > 32)
-                    tm_ld4(ta + 32, qv + 32);
-                tm_wait_ld();
+                tm_ld16(ta, qv);
+                tm_ld4(ta + 16, qv + 16);
             }
             V wv[NF];
             if (need_w) {
@@ -411,94 +445,67 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
                     wv[f] = *reinterpret_cast<const V *>(ws + f * TX * TY);
             }
             auto pair = [&](int i) { return P::mk(qv[i], qv[i + 1]); };
-            // derivatives of field f: x, y from TMEM, z from the column window
-            V g[3], d2[3];
-            auto derivs = [&](int f, bool second) {
-                g[0] = pair(4 * f);
-                g[1] = pair(4 * f + 2);
-                V gz, bz;
+            // z derivatives from the column window (centre at position 3)
+            auto dz1 = [&](int f) {
+                V gz;
 #pragma unroll
                 for (int k = 1; k <= 3; ++k) {
-                    const V zp = colv[f][3 + k], zm = colv[f][3 - k];
-                    const V dzv = P::fma(zm, NEG1, zp);
+                    const V dzv = P::fma(colv[f][3 - k], NEG1, colv[f][3 + k]);
                     gz = k == 1 ? P::mul(P::bc(c.D1(2, k)), dzv) : P::fma(P::bc(c.D1(2, k)), dzv, gz);
-                    if (second) {
-                        if (k == 1)
-                            bz = P::mul(P::bc(c.D2c(2)), colv[f][3]);
-                        bz = P::fma(P::bc(c.D2(2, k)), P::add(zp, zm), bz);
-                    }
                 }
-                g[2] = gz;
-                if (second) {
-                    d2[0] = pair(TL::D2 + 4 * (f - 1));
-                    d2[1] = pair(TL::D2 + 4 * (f - 1) + 2);
-                    d2[2] = bz;
-                }
+                return gz;
             };
-            const V NU = P::bc(c.nu), NU3 = P::bc(c.nu3);
-            const V uc[3] = {colv[1][3], colv[2][3], colv[3][3]};
-            V acc[4], gl[3];
-            V dv = P::bc(0.f);
-            derivs(0, false);
-            gl[0] = g[0];
-            gl[1] = g[1];
-            gl[2] = g[2];
+            auto dz2 = [&](int f) {
+                V bz = P::mul(P::bc(c.D2c(2)), colv[f][3]);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                derivs(1 + i, true);
-                V adv = P::mul(uc[0], g[0]);
-                adv = P::fma(uc[1], g[1], adv);
-                adv = P::fma(uc[2], g[2], adv);
-                const V lap = P::add(P::add(d2[0], d2[1]), d2[2]);
-                V sgl = P::mul(g[0], gl[0]);
-                sgl = P::fma(g[1], gl[1], sgl);
-                sgl = P::fma(g[2], gl[2], sgl);
-                V ai = P::mul(NU, P::add(lap, sgl));
-                if (i > 0)
-                    ai = P::add(ai, acc[1 + i]);
-                ai = P::fma(adv, NEG1, ai);
-                ai = P::fma(NU3, d2[i], ai);  // (nu/3) D_ii u_i of grad div u
-                acc[1 + i] = ai;
-                const V nugl = P::mul(NU, gl[i]);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (a > i && i == 0)
-                        acc[1 + a] = P::mul(g[a], nugl);  // first contribution
-                    else
-                        acc[1 + a] = P::fma(g[a], nugl, acc[1 + a]);
-                }
-                dv = P::add(dv, g[i]);
-            }
-            // cross terms of grad div u (Eq. 8): (x, y) from TMEM, z-paired
-            // from the forward accumulators
-            acc[1] = P::fma(NU3, P::add(pair(TL::XY + 2), acx[0]), acc[1]);  // D_xy u_y + D_xz u_z
-            acc[2] = P::fma(NU3, P::add(pair(TL::XY), acy[0]), acc[2]);      // D_xy u_x + D_yz u_z
-            acc[3] = P::fma(NU3, acz[0], acc[3]);                            // D_xz u_x + D_yz u_y
-            V rs = P::bc(0.f);
-            if (NF == 5) {
-                derivs(4, false);
-                V t = P::mul(uc[0], g[0]);
-                t = P::fma(uc[1], g[1], t);
-                t = P::fma(uc[2], g[2], t);
-                rs = P::mul(t, NEG1);
+                for (int k = 1; k <= 3; ++k)
+                    bz = P::fma(P::bc(c.D2(2, k)), P::add(colv[f][3 + k], colv[f][3 - k]), bz);
+                return bz;
+            };
+            const V uz = colv[3][3];
+            const V glx = pair(TL::GLX), gly = pair(TL::GLY);
+            const V glz = dz1(0);
+            const V gzx = dz1(1), gzy = dz1(2), gzz = dz1(3);
+            const V NU2 = P::bc(2.f * c.nu), N23 = P::bc(-c.nu23);
+            const V div = P::add(pair(TL::DIV), gzz);
+            V rr[5];
+            // lnrho: -u_z d_z lnrho - d_z u_z
+            rr[0] = P::fma(uz, P::mul(glz, NEG1), P::fma(gzz, NEG1, pair(0)));
+            // u_x, u_y: -u_z d_z u_i + nu D_zz u_i + nu (d_z u_i + d_i u_z) d_z lnrho
+            //           - (2/3) nu d_z u_z d_i lnrho + (nu/3) (D_iz u_z)
+            {
+                V p = P::fma(uz, P::mul(gzx, NEG1), pair(2));
+                p = P::fma(NU, dz2(1), p);
+                p = P::fma(NU, P::mul(P::add(gzx, pair(TL::DZX)), glz), p);
+                p = P::fma(P::mul(N23, gzz), glx, p);
+                rr[1] = P::fma(NU3, acx[0], p);
             }
             {
-                V ug = P::mul(uc[0], gl[0]);
-                ug = P::fma(uc[1], gl[1], ug);
-                ug = P::fma(uc[2], gl[2], ug);
-                acc[0] = P::mul(P::add(ug, dv), NEG1);
-                const V NCS2 = P::bc(-c.cs2);
-                const V t = P::mul(P::bc(-c.nu23), dv);
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    acc[1 + a] = P::fma(t, gl[a], P::fma(NCS2, gl[a], acc[1 + a]));
+                V p = P::fma(uz, P::mul(gzy, NEG1), pair(4));
+                p = P::fma(NU, dz2(2), p);
+                p = P::fma(NU, P::mul(P::add(gzy, pair(TL::DZY)), glz), p);
+                p = P::fma(P::mul(N23, gzz), gly, p);
+                rr[2] = P::fma(NU3, acy[0], p);
             }
+            // u_z: -u_z d_z u_z - c_s^2 d_z lnrho + (4/3) nu D_zz u_z + (nu/3) (D_xz u_x
+            //      + D_yz u_y) + 2 nu d_z u_z d_z lnrho + nu (d_z u_x d_x lnrho
+            //      + d_z u_y d_y lnrho) - (2/3) nu div u d_z lnrho
+            {
+                V p = P::fma(uz, P::mul(gzz, NEG1), pair(6));
+                p = P::fma(P::bc(-c.cs2), glz, p);
+                p = P::fma(P::bc(c.nu + c.nu3), dz2(3), p);
+                p = P::fma(NU3, acz[0], p);
+                p = P::fma(NU2, P::mul(gzz, glz), p);
+                p = P::fma(NU, P::fma(gzy, gly, P::mul(gzx, glx)), p);
+                rr[3] = P::fma(P::mul(N23, div), glz, p);
+            }
+            if (NF == 5)
+                rr[4] = P::fma(uz, P::mul(dz1(4), NEG1), pair(8));
             if (valid0) {
                 const V DT = P::bc(dt), ALPHA = P::bc(alpha), BETA = P::bc(beta);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    const V rr = f < 4 ? acc[f] : rs;
-                    const V wn = first ? P::mul(DT, rr) : P::fma(DT, rr, P::mul(ALPHA, wv[f]));
+                    const V wn = first ? P::mul(DT, rr[f]) : P::fma(DT, rr[f], P::mul(ALPHA, wv[f]));
                     const V o2 = P::fma(BETA, wn, colv[f][3]);
                     if (!last)
                         *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = wn;
@@ -546,25 +553,23 @@ __device__ __forceinline__ bool run_column_tm(const CUtensorMap *tmap, const CUt
 }
 
 // TMEM for the CTA: warp 0 allocates and frees; the address is shared.
-template <int NF>
 __device__ __forceinline__ uint32_t tmem_acquire(uint32_t *slot)
 {
     if (threadIdx.x < 32)
-        tc::tmem_alloc(slot, TmLayout<NF>::COLS);
+        tc::tmem_alloc(slot, TmLayout::COLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     return *reinterpret_cast<volatile uint32_t *>(slot);
 }
 
-template <int NF>
 __device__ __forceinline__ void tmem_release(uint32_t tmem)
 {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (threadIdx.x < 32)
-        tc::tmem_dealloc(tmem, TmLayout<NF>::COLS);
+        tc::tmem_dealloc(tmem, TmLayout::COLS);
 }
 
 // Single box: one CTA per (tile, z-chunk).
@@ -579,7 +584,7 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_tm(
     using RG = typename RT::RG;
     extern __shared__ __align__(128) unsigned char smem[];
     tiled2::init_barriers(reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF), NS + RG::NW);
-    const uint32_t tmem = tmem_acquire<NF>(reinterpret_cast<uint32_t *>(smem + RT::TM_OFF));
+    const uint32_t tmem = tmem_acquire(reinterpret_cast<uint32_t *>(smem + RT::TM_OFF));
     const int x0 = (blockIdx.x % tiles_x) * TX;
     const int y0 = (blockIdx.x / tiles_x) * TY;
     const int z0 = blockIdx.y * zc;
@@ -589,15 +594,15 @@ __global__ void __launch_bounds__((TX / 2) * TY) k_substep_tm(
                                   (float)st.beta, (float)st.dt, st.first != 0, st.last != 0, x0,
                                   y0, z0, nout, jrun, wrun, smem, tmem, dev_error,
                                   blockIdx.x == 0 && blockIdx.y == 0 ? skip_plane : -1);
-    tmem_release<NF>(tmem);
+    tmem_release(tmem);
 }
 
 }  // namespace tiled3
 
 // Launch of the TMEM-carried 55-point kernel (FP32 storage and arithmetic).
-// The dynamic shared memory is padded so that at most two CTAs share an SM:
-// two 256-column TMEM allocations fill the SM's 512 columns, and a third CTA
-// would wait in tcgen05.alloc for one of them to finish.
+// Each CTA holds 128 TMEM columns, so the four CTAs an SM could hold at most
+// fit in its 512 columns and tcgen05.alloc never waits for another CTA.
+// (Registers, about 240 per thread, allow two.)
 template <int TX, int TY, int NS>
 cudaError_t launch_tm_cfg(const StateBufs &b, const Coef<float> &c, const RKStage &st, int nf,
                           int zc, int cfg_key, int *dev_error, TmapCache *cache,
@@ -613,13 +618,12 @@ cudaError_t launch_tm_cfg(const StateBufs &b, const Coef<float> &c, const RKStag
     const int tiles_y = (b.Ls.ny + TY - 1) / TY;
     const dim3 grid(tiles_x * tiles_y, (b.Ls.nz + zc - 1) / zc);
     const dim3 block((TX / 2) * TY);
-    constexpr int kTwoPerSm = 80 * 1024;  // > 228 KB / 3
+    static_assert(4 * tiled3::TmLayout::COLS <= 512, "TMEM columns per CTA");
     cudaError_t e;
 #define GBFD_LAUNCH_TM(NFV)                                                                       \
     do {                                                                                          \
         auto kern = tiled3::k_substep_tm<NFV, TX, TY, NS>;                                        \
-        constexpr int need = tiled3::RingTm<NFV, TX, TY, NS>::BYTES;                              \
-        constexpr int sm = need > kTwoPerSm ? need : kTwoPerSm;                                   \
+        constexpr int sm = tiled3::RingTm<NFV, TX, TY, NS>::BYTES;                                \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \
