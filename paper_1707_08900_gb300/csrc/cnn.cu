@@ -6,8 +6,9 @@
 //   implicit GEMMs on the tcgen05 tensor cores: M = 128 grid points per tile,
 //   N = output channels, K = 27 taps x input channels; BF16 operands staged
 //   in shared memory as K-major core matrices, FP32 accumulators in TMEM.
-//   The A operand (im2col rows) is gathered per tap straight from the
-//   channels-last activations with periodic wrap; the B operand (weights) is
+//   A tile of 8 x 16 x 2 points and its periodic halo is staged in shared
+//   memory once; the A operand of each tap is a shifted descriptor into it,
+//   so the 27 taps are issued back to back.  The B operand (weights) is
 //   resident in shared memory.  The input gradient is the same kernel with
 //   the weights transposed in channels and flipped in taps.
 // * The weight gradient sums over all grid points (K = points) on CUDA cores
@@ -92,14 +93,32 @@ struct ConvArgs {
     int *dev_error;
 };
 
+// A conv tile is TXT x TYT points in each of ZB consecutive z planes: one
+// M = 128 MMA row block per plane, row r = point (x0 + r % TXT, y0 + r / TXT).
+// The tile's input plus its one-point periodic halo is staged in shared
+// memory once, as 16-byte chunks of 8 channels: chunk c of halo point
+// (hx, hy, hz) at c * CS + ((hz * HY + hy) * HX + hx) * 16.  For tap
+// (dx, dy, dz) the A operand of plane zb is then the same buffer at a shifted
+// start: core matrices of 8 x-consecutive rows (16-byte row stride), row
+// groups one halo row apart (SBO = HX * 16), K chunks CS apart (LBO), so all
+// 27 taps are issued back to back without any further data movement.
+constexpr int TXT = 8, TYT = 16, ZB = 2;
+constexpr int HX = TXT + 2, HY = TYT + 2, HZ = ZB + 2, HPTS = HX * HY * HZ;
+static_assert(TXT * TYT == MT, "one MMA row block per tile plane");
+
 template <int CIN, int N, int EPI>
 struct ConvSmem {
     static constexpr int K = TAPS * CIN;
+    static constexpr int CH8 = CIN / 8;
     static constexpr int B_BYTES = N * K * 2;
-    static constexpr int STAGE = MT * CIN * 2;
+    // chunk stride: 32 bytes past a 128-byte multiple, so the 16-byte
+    // stores of one point's chunks fall in different banks
+    static constexpr int CS = (HPTS * 16 + 127) / 128 * 128 + 32;
     static constexpr int A_OFF = (B_BYTES + 1023) / 1024 * 1024;
-    static constexpr int BAR_OFF = A_OFF + 2 * STAGE;
-    static constexpr int BYTES = BAR_OFF + 64;
+    static constexpr int A_BYTES = CH8 * CS;
+    static constexpr int BAR_OFF = (A_OFF + A_BYTES + 15) / 16 * 16;
+    static constexpr int BYTES = BAR_OFF + 32;
+    static constexpr int TCOLS = ZB * N <= 32 ? 32 : 64;  // TMEM accumulator columns
 };
 
 template <int CIN, int N, int EPI>
@@ -107,10 +126,9 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const ConvArgs a)
 {
     using SM = ConvSmem<CIN, N, EPI>;
     constexpr int K = SM::K;
-    constexpr int KSTEPS = CIN / 16;  // MMAs per tap
-    constexpr int SBO_A = CIN * 16;
+    constexpr int KSTEPS = CIN / 16;  // MMAs per tap and plane
+    constexpr int CH8 = SM::CH8;
     constexpr int SBO_B = K * 16;
-    constexpr int CH8 = CIN / 8;      // 16-byte chunks per point
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sB = smem;
     unsigned char *sA = smem + SM::A_OFF;
@@ -121,131 +139,128 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const ConvArgs a)
         reinterpret_cast<uint4 *>(sB)[i] = reinterpret_cast<const uint4 *>(a.wB)[i];
     if (threadIdx.x == 0) {
         tiled::mbar_init(&bars[0], 1);
-        tiled::mbar_init(&bars[1], 1);
         tiled::fence_mbar_init();
     }
     if (threadIdx.x < 32)
-        tc::tmem_alloc(tslot, 32);
-    tc::fence_smem_to_async();
+        tc::tmem_alloc(tslot, SM::TCOLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     constexpr uint32_t idesc = tc::idesc_bf16_f32(MT, N);
     const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
-    uint32_t ph0 = 0, ph1 = 0;
+    uint32_t ph = 0;
     const int n = a.n;
-    const int n2 = n * n, n3 = n2 * n;
-    const int ntiles = (a.npts + MT - 1) / MT;
+    const long long n3 = (long long)n * n * n;
+    const int nb = (int)(a.npts / n3);
+    const int tx_n = (n + TXT - 1) / TXT, ty_n = (n + TYT - 1) / TYT, tz_n = (n + ZB - 1) / ZB;
+    const int ntiles = nb * tz_n * ty_n * tx_n;
     bool timeout = false;
 
 #pragma unroll 1
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int p = tile * MT + threadIdx.x;
-        const bool valid = p < a.npts;
-        const int pp = valid ? p : 0;
-        const int b = pp / n3;
-        int r = pp - b * n3;
-        const int z = r / n2;
-        r -= z * n2;
-        const int y = r / n;
-        const int x = r - y * n;
-        uint4 v[CH8];
-        auto gather = [&](int tap) {
-            int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-            zz += zz < 0 ? n : 0;
-            zz -= zz >= n ? n : 0;
-            yy += yy < 0 ? n : 0;
-            yy -= yy >= n ? n : 0;
-            xx += xx < 0 ? n : 0;
-            xx -= xx >= n ? n : 0;
-            const long long q = (long long)b * n3 + ((long long)zz * n + yy) * n + xx;
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.x + q * CIN);
+        int r = tile;
+        const int x0 = (r % tx_n) * TXT;
+        r /= tx_n;
+        const int y0 = (r % ty_n) * TYT;
+        r /= ty_n;
+        const int z0 = (r % tz_n) * ZB;
+        const int b = r / tz_n;
+        // the halo box, periodic (tiles may reach past n on small grids)
+        const bf16 *xb = a.x + (long long)b * n3 * CIN;
+        // fully unrolled so that all of a thread's loads are in flight at once
+        constexpr int NLD = (HPTS * CH8 + NTHR - 1) / NTHR;
 #pragma unroll
-            for (int c = 0; c < CH8; ++c)
-                v[c] = valid ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
-        };
-        gather(0);
-#pragma unroll 1
-        for (int tap = 0; tap < TAPS; ++tap) {
-            const int st = tap & 1;
-            if (tap >= 2) {
-                if (!tiled::mbar_wait(&bars[st], st ? ph1 : ph0))
-                    timeout = true;
-                if (st)
-                    ph1 ^= 1;
-                else
-                    ph0 ^= 1;
-            }
-            unsigned char *As = sA + st * SM::STAGE;
-            const int t = threadIdx.x;
-#pragma unroll
-            for (int c = 0; c < CH8; ++c)
-                *reinterpret_cast<uint4 *>(As + (t / 8) * SBO_A + c * 128 + (t % 8) * 16) = v[c];
-            if (tap + 1 < TAPS)
-                gather(tap + 1);
-            tc::fence_smem_to_async();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                tc::fence_after_sync();
-#pragma unroll
-                for (int s = 0; s < KSTEPS; ++s) {
-                    const uint64_t ad = tc::smem_desc(sA_u32 + st * SM::STAGE + s * 256, 128, SBO_A);
-                    const uint64_t bd = tc::smem_desc(sB_u32 + (tap * KSTEPS + s) * 256, 128, SBO_B);
-                    tc::mma_bf16(tmem, ad, bd, idesc, (tap > 0 || s > 0) ? 1u : 0u);
-                }
-                tc::commit(&bars[st]);
-            }
+        for (int it = 0; it < NLD; ++it) {
+            const int i = threadIdx.x + it * NTHR;
+            if (i >= HPTS * CH8)
+                break;
+            const int c = i % CH8, hp = i / CH8;
+            const int hx = hp % HX, hy = (hp / HX) % HY, hz = hp / (HX * HY);
+            const int gx = (x0 - 1 + hx + n) % n, gy = (y0 - 1 + hy + n) % n;
+            const int gz = (z0 - 1 + hz + n) % n;
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(
+                                      xb + (((long long)gz * n + gy) * n + gx) * CIN) +
+                                  c);
+            *reinterpret_cast<uint4 *>(sA + c * SM::CS + hp * 16) = v;
         }
-        // last commits: tap 26 on stage 0, tap 25 on stage 1
-        if (!tiled::mbar_wait(&bars[0], ph0))
-            timeout = true;
-        ph0 ^= 1;
-        if (!tiled::mbar_wait(&bars[1], ph1))
-            timeout = true;
-        ph1 ^= 1;
-        tc::fence_after_sync();
-        float acc[32];
-        const uint32_t taddr = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
-        tc::tmem_ld16(taddr, acc);
-        if (N > 16)
-            tc::tmem_ld16(taddr + 16, acc + 16);
-        if (valid && !timeout) {
-            if (EPI == EPI_GELU) {
-                float4 *hs = reinterpret_cast<float4 *>(a.hsave + (long long)p * N);
-                uint4 *yo = reinterpret_cast<uint4 *>(a.yb + (long long)p * N);
+        // the halo writes (generic proxy) become visible to the tensor core;
+        // every thread is done reading the previous tile's accumulators
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int zb = 0; zb < ZB; ++zb)
+#pragma unroll 1
+                for (int tap = 0; tap < TAPS; ++tap) {
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // 0..2: offset + 1
+                    const uint32_t a0 =
+                        sA_u32 + (uint32_t)((((zb + dz) * HY + dy) * HX + dx) * 16);
 #pragma unroll
-                for (int c = 0; c < N; c += 8) {
-                    float h[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        h[i] = acc[c + i] + __ldg(a.bias + c + i);
-                    hs[c / 4] = make_float4(h[0], h[1], h[2], h[3]);
-                    hs[c / 4 + 1] = make_float4(h[4], h[5], h[6], h[7]);
-                    __nv_bfloat162 o[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        o[i] = __floats2bfloat162_rn(gelu(h[2 * i]), gelu(h[2 * i + 1]));
-                    yo[c / 8] = *reinterpret_cast<uint4 *>(o);
+                    for (int s = 0; s < KSTEPS; ++s) {
+                        const uint64_t ad = tc::smem_desc(a0 + 2 * s * SM::CS, SM::CS, HX * 16);
+                        const uint64_t bd =
+                            tc::smem_desc(sB_u32 + (tap * KSTEPS + s) * 256, 128, SBO_B);
+                        tc::mma_bf16(tmem + zb * N, ad, bd, idesc, (tap > 0 || s > 0) ? 1u : 0u);
+                    }
                 }
-            } else if (EPI == EPI_LINEAR) {
-                float4 *yo = reinterpret_cast<float4 *>(a.yf + (long long)p * 8);
-                yo[0] = make_float4(acc[0] + __ldg(a.bias + 0), acc[1] + __ldg(a.bias + 1),
-                                    acc[2] + __ldg(a.bias + 2), acc[3] + __ldg(a.bias + 3));
-                yo[1] = make_float4(acc[4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
-            } else {
-                const float4 *hp = reinterpret_cast<const float4 *>(a.hprev + (long long)p * N);
-                uint4 *yo = reinterpret_cast<uint4 *>(a.yb + (long long)p * N);
+            tc::commit(&bars[0]);
+        }
+        if (!tiled::mbar_wait(&bars[0], ph))
+            timeout = true;
+        ph ^= 1;
+        tc::fence_after_sync();
+        const int lx = threadIdx.x % TXT, ly = threadIdx.x / TXT;
+        const int x = x0 + lx, y = y0 + ly;
+        const uint32_t taddr = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
+#pragma unroll 1
+        for (int zb = 0; zb < ZB; ++zb) {
+            float acc[32];
+            tc::tmem_ld16(taddr + zb * N, acc);
+            if (N > 16)
+                tc::tmem_ld16(taddr + zb * N + 16, acc + 16);
+            const int z = z0 + zb;
+            const bool valid = x < n && y < n && z < n;
+            const long long p = (long long)b * n3 + ((long long)z * n + y) * n + x;
+            if (valid && !timeout) {
+                if (EPI == EPI_GELU) {
+                    float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * N);
+                    uint4 *yo = reinterpret_cast<uint4 *>(a.yb + p * N);
 #pragma unroll
-                for (int c = 0; c < N; c += 8) {
-                    const float4 h0 = __ldg(hp + c / 4), h1 = __ldg(hp + c / 4 + 1);
-                    const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                    __nv_bfloat162 o[4];
+                    for (int c = 0; c < N; c += 8) {
+                        float h[8];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        o[i] = __floats2bfloat162_rn(acc[c + 2 * i] * gelu_grad(h[2 * i]),
-                                                     acc[c + 2 * i + 1] * gelu_grad(h[2 * i + 1]));
-                    yo[c / 8] = *reinterpret_cast<uint4 *>(o);
+                        for (int i = 0; i < 8; ++i)
+                            h[i] = acc[c + i] + __ldg(a.bias + c + i);
+                        hs[c / 4] = make_float4(h[0], h[1], h[2], h[3]);
+                        hs[c / 4 + 1] = make_float4(h[4], h[5], h[6], h[7]);
+                        __nv_bfloat162 o[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            o[i] = __floats2bfloat162_rn(gelu(h[2 * i]), gelu(h[2 * i + 1]));
+                        yo[c / 8] = *reinterpret_cast<uint4 *>(o);
+                    }
+                } else if (EPI == EPI_LINEAR) {
+                    float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
+                    yo[0] = make_float4(acc[0] + __ldg(a.bias + 0), acc[1] + __ldg(a.bias + 1),
+                                        acc[2] + __ldg(a.bias + 2), acc[3] + __ldg(a.bias + 3));
+                    yo[1] = make_float4(acc[4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
+                } else {
+                    const float4 *hp = reinterpret_cast<const float4 *>(a.hprev + p * N);
+                    uint4 *yo = reinterpret_cast<uint4 *>(a.yb + p * N);
+#pragma unroll
+                    for (int c = 0; c < N; c += 8) {
+                        const float4 h0 = __ldg(hp + c / 4), h1 = __ldg(hp + c / 4 + 1);
+                        const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                        __nv_bfloat162 o[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            o[i] = __floats2bfloat162_rn(acc[c + 2 * i] * gelu_grad(h[2 * i]),
+                                                         acc[c + 2 * i + 1] * gelu_grad(h[2 * i + 1]));
+                        yo[c / 8] = *reinterpret_cast<uint4 *>(o);
+                    }
                 }
             }
         }
@@ -259,7 +274,7 @@ __global__ void __launch_bounds__(NTHR) k_conv_tc(const ConvArgs a)
     __syncthreads();
     tc::fence_after_sync();
     if (threadIdx.x < 32)
-        tc::tmem_dealloc(tmem, 32);
+        tc::tmem_dealloc(tmem, SM::TCOLS);
 }
 
 // Weight (and bias) gradient of one layer, summed over this CTA's share of
@@ -644,8 +659,12 @@ cudaError_t conv(gbfd_cnn *c, const ConvArgs &a)
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
     if (e != cudaSuccess)
         return e;
-    const int ntiles = (a.npts + MT - 1) / MT;
-    k<<<std::min(ntiles, c->grid_conv), NTHR, SM::BYTES, c->stream>>>(a);
+    const int n = a.n;
+    const long long ntiles = (long long)(a.npts / ((long long)n * n * n)) * ((n + ZB - 1) / ZB) *
+                             ((n + TYT - 1) / TYT) * ((n + TXT - 1) / TXT);
+    // three CTAs per SM walking the tiles (measured faster than sizing the
+    // grid to the resident CTAs)
+    k<<<(int)std::min<long long>(ntiles, c->grid_conv), NTHR, SM::BYTES, c->stream>>>(a);
     c->launches++;
     return cudaGetLastError();
 }
