@@ -631,9 +631,10 @@ gbfd_status gbfd_autotune(gbfd_ctx *ctx, int reps, const char *cache_path, int *
     for (char *p = key; *p; ++p)
         if (*p == '"' || *p == '\\')
             *p = '_';
-    // the precision forms compile one tile variant: tune its chunk lengths only
+    // the precision forms compile three kernels (packed two-point with integer
+    // or hardware conversions, one-point): tune those and their chunk lengths
     const bool acc = ctx->p.precision == GBFD_FP32_ACC64 || ctx->p.precision == GBFD_FP32_ACC64_W64;
-    const int count = acc ? kZcChoices : tiled_config_count(ctx->sbytes);
+    const int count = acc ? 3 * kZcChoices : tiled_config_count(ctx->sbytes);
     std::map<std::string, std::pair<int, double>> cache;
     if (cache_path) {
         cache = read_cache(cache_path);

@@ -3,6 +3,8 @@
 // coefficients and the per-point right-hand side of Eqs. 1-3.
 #pragma once
 
+#include <cstdint>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -192,6 +194,60 @@ __device__ __forceinline__ void rk3_update(bool first, TA alpha, TA beta, TA dt,
     TA wn = first ? dt * r : alpha * (TA)w + dt * r;
     w = (TW)wn;
     out = (TS)((TA)u + beta * wn);
+}
+
+// Exact IEEE-754 conversions between binary32 and binary64 done with integer
+// instructions, so that GB300's narrow FP64 pipe is left to the arithmetic.
+// binary32 (sign, 8-bit exponent e, 23-bit fraction m) -> binary64: exponent
+// e + 896 (= e - 127 + 1023), fraction m << 29.  binary64 -> binary32: exponent
+// E - 896, the top 23 fraction bits, rounded to nearest, ties to even, on the
+// 29 dropped bits (a carry out of the fraction bumps the exponent, and past
+// the largest finite value gives infinity, as round-to-nearest requires).
+// Zero, subnormal, infinite and NaN operands, and results below the normal
+// binary32 range, take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_int(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu)
+        return (double)x;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+__device__ __forceinline__ float f64_to_f32_int(double v)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    if (e <= 0 || e >= 255)
+        return __double2float_rn(v);
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1fffffffu;
+    const uint32_t up = (rest > 0x10000000u) || (rest == 0x10000000u && (m & 1u));
+    return __uint_as_float(((hi & 0x80000000u) | ((uint32_t)e << 23) | m) + up);
+}
+
+// Eq. 10 in FP64 for FP32 state: the same arithmetic with explicit fused
+// multiply-adds whichever conversions are used (ICVT: the integer routines
+// above, else the hardware conversions), so the two give identical bits.
+template <bool ICVT, class TW>
+__device__ __forceinline__ void rk3_update_f64(bool first, double alpha, double beta, double dt,
+                                               float r, float u, TW &w, float &out)
+{
+    auto up = [](float v) { return ICVT ? f32_to_f64_int(v) : (double)v; };
+    auto down = [](double v) { return ICVT ? f64_to_f32_int(v) : __double2float_rn(v); };
+    const double rd = up(r);
+    double wd;
+    if constexpr (sizeof(TW) == 8)
+        wd = w;
+    else
+        wd = up(w);
+    const double wn = first ? dt * rd : fma(alpha, wd, dt * rd);
+    if constexpr (sizeof(TW) == 8)
+        w = wn;
+    else
+        w = down(wn);
+    out = down(fma(beta, wn, up(u)));
 }
 
 // Store v at interior (x, y, z) of field f and at its periodic ghost copies.

@@ -110,7 +110,7 @@ __device__ __forceinline__ void init_barriers(uint64_t *bars, int n)
 // advanced on return.  Returns false when a bounded wait gave up (after
 // recording it and draining the copies in flight).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK,
-          int U, bool WG, class CoefT>
+          int U, bool WG, bool ICVT = false, class CoefT>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            TS *__restrict__ out, TW *__restrict__ w,
                                            TS *__restrict__ divf, const Layout &Ls,
@@ -378,13 +378,15 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
             };
 
             if constexpr (PK) {
-                static_assert(std::is_same<TS, TW>::value && std::is_same<TS, TA>::value,
-                              "the packed path computes in one type");
+                // FP32 storage and stencil arithmetic; the Eq. 10 update (u-tilde
+                // and the new state) in TA, u-tilde stored as TW
+                static_assert(std::is_same<TS, float>::value, "the packed path is FP32");
+                constexpr bool UP32 = std::is_same<TA, float>::value && std::is_same<TW, float>::value;
                 using P = PairOps<TS>;
                 if (valid0) {
                     const int zo = z0 + oo;
                     const V NEG1 = P::bc((TS)-1);
-                    V wv[NF];
+                    VW wv[NF];
                     if constexpr (WG) {
     #pragma unroll
                         for (int f = 0; f < NF; ++f)
@@ -394,7 +396,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                                        ty * TX + 2 * tx;
     #pragma unroll
                         for (int f = 0; f < NF; ++f)
-                            wv[f] = *reinterpret_cast<const V *>(ws + f * TX * TY);
+                            wv[f] = *reinterpret_cast<const VW *>(ws + f * TX * TY);
                     }
                     // first (and second) derivatives of field f along x, y, z:
                     // x per point from the loaded row, y and z on the pair
@@ -547,14 +549,31 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                                 *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dv;
                         }
                     }
-                    const V DT = P::bc(dt), ALPHA = P::bc(alpha), BETA = P::bc(beta);
     #pragma unroll
                     for (int f = 0; f < NF; ++f) {
                         const V r = f < 4 ? acc[f] : rs;
-                        const V wn = first ? P::mul(DT, r) : P::fma(DT, r, P::mul(ALPHA, wv[f]));
-                        const V o2 = P::fma(BETA, wn, C(f, 3));
-                        if (!last)
-                            *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = wn;
+                        V o2;
+                        if constexpr (UP32) {
+                            const V DT = P::bc(dt), ALPHA = P::bc(alpha), BETA = P::bc(beta);
+                            const V wn = first ? P::mul(DT, r) : P::fma(DT, r, P::mul(ALPHA, wv[f]));
+                            o2 = P::fma(BETA, wn, C(f, 3));
+                            if (!last)
+                                *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = wn;
+                        } else {
+                            // Eq. 10 in TA for both points (the precision form)
+                            static_assert(std::is_same<TA, double>::value, "FP64 update");
+                            TW wo[2] = {first ? (TW)0 : wv[f].x, first ? (TW)0 : wv[f].y};
+                            TS on[2];
+                            rk3_update_f64<ICVT, TW>(first, alpha, beta, dt, r.x, C(f, 3).x, wo[0], on[0]);
+                            rk3_update_f64<ICVT, TW>(first, alpha, beta, dt, r.y, C(f, 3).y, wo[1], on[1]);
+                            o2 = make_float2(on[0], on[1]);
+                            if (!last) {
+                                VW t;
+                                t.x = wo[0];
+                                t.y = wo[1];
+                                *reinterpret_cast<VW *>(w + f * Lw.fpitch + go_w) = t;
+                            }
+                        }
                         TS *op = out + f * Ls.fpitch + go_s;
                         *reinterpret_cast<V *>(op) = o2;
                         if (gdx)
@@ -869,7 +888,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 
 // Single box: one CTA per (tile, z-chunk).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK, int U,
-          int MINB, bool WG>
+          int MINB, bool WG, bool ICVT>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
@@ -884,7 +903,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U, WG>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
+    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U, WG, ICVT>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
                                                   (TA)st.alpha, (TA)st.beta, (TA)st.dt,
                                                   st.first != 0, st.last != 0, x0, y0, z0, nout,
                                                   jrun, wrun, smem, dev_error,
@@ -894,7 +913,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
 }  // namespace tiled2
 
 template <class TS, class TW, class TA, int TX, int TY, int NS, bool PK = false, int U = 1,
-          int MINB = 1, bool WG = false>
+          int MINB = 1, bool WG = false, bool ICVT = false>
 cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
                            int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
@@ -915,7 +934,7 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
     cudaError_t e;
 #define GBFD_LAUNCH2(NFV, MIX)                                                                    \
     do {                                                                                          \
-        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB, WG>;         \
+        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB, WG, ICVT>;   \
         constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS, WG ? 0 : U + 2>::BYTES;          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \

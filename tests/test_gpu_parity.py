@@ -186,22 +186,23 @@ def test_roll_equivariance_bitwise_fp32():
     assert np.array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_acc64", "fp32_acc64_w64"])
 def test_every_tile_config_matches_oracle(precision):
     """Every entry of the tile table (one and two points per thread, all
-    z-chunk lengths) reproduces the oracle on a ragged grid."""
+    z-chunk lengths) reproduces the oracle on a ragged grid; the precision
+    forms have two kernels (packed two-point, one-point) x 4 chunk lengths."""
     from paper_1707_08900_gb300 import gbfd
     shape = (20, 44, 36)
     g = _grid(shape)
     ph = fd.Physics(cs=1.0, nu=0.01, entropy_mode=1)
     st = inputs.spectrum(shape, 21, mach=0.2, lnrho_rms=1e-2)
-    if precision == "fp32":
+    if precision != "fp64":
         st = st.astype(np.float32).astype(np.float64)
     dt = fd.cfl_dt(st, g, ph, 0.4)
     ref = fd.rk3_step(st, dt, g, ph)
     tol = FP64_TOL if precision == "fp64" else FP32_TOL
     n = 0
-    for cfg in range(256):
+    for cfg in range(8 if precision.startswith("fp32_acc") else 256):
         s = _solver(shape, precision=precision, nu=0.01)
         try:
             s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
@@ -214,7 +215,7 @@ def test_every_tile_config_matches_oracle(precision):
         s.close()
         assert np.all(err <= tol), (cfg, err)
         n += 1
-    assert n >= (8 if precision == "fp64" else 68)
+    assert n >= {"fp64": 8, "fp32": 68}.get(precision, 8)
 
 
 def test_every_tile_config_agrees():
@@ -351,3 +352,33 @@ def test_host_paths_agree(precision):
         assert np.all(np.isfinite(base))
         for key in ((1, dtype, 1), (0, dtype, 0), (0, dtype, 1)):
             assert np.array_equal(results[key], base), key
+
+
+@pytest.mark.parametrize("precision", ["fp32_acc64", "fp32_acc64_w64"])
+@pytest.mark.parametrize("form", ["55p", "19p"])
+def test_integer_conversions_match_hardware_bitwise(precision, form):
+    """The precision form's default kernel converts FP32<->FP64 with integer
+    instructions; table entry 8 is the same kernel with the hardware
+    conversions.  Three RK3 steps must give identical bits, on a normal
+    state and on one salted with zeros, subnormals, values near the FP32
+    range limits and ties of the FP64->FP32 rounding."""
+    from paper_1707_08900_gb300 import gbfd
+    shape = (16, 24, 32)
+    base = inputs.spectrum(shape, 4, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
+    salted = base.copy()
+    flat = salted.reshape(-1)
+    rng = np.random.default_rng(5)
+    special = np.array([0.0, -0.0, 1e-40, -3e-39, 1.1754944e-38, 3.0e38, -3.0e38, 1e-30,
+                        1.0 + 2.0 ** -23, -(1.0 + 2.0 ** -22)], dtype=np.float32)
+    idx = rng.choice(flat.size, 60, replace=False)
+    flat[idx] = np.resize(special, 60)
+    for st in (base, salted):
+        outs = []
+        for cfg in (0, 8):
+            s = _solver(shape, precision=precision, form=form, nu=5e-3)
+            s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
+            s.set_state(st)
+            s.rk3_step(1e-4, 3)
+            outs.append(s.get_state(fp64=False).view(np.uint32))
+            s.close()
+        assert np.array_equal(outs[0], outs[1])
