@@ -44,6 +44,15 @@ def lib():
         L.or_box_filter.argtypes = [_P, _P, _L, _L, _L, _I, _I]
         L.or_set_threads.restype = _I
         L.or_set_threads.argtypes = [_I]
+        _LP = ctypes.POINTER(ctypes.c_long)
+        L.or_forcing_amplitude.restype = _I
+        L.or_forcing_amplitude.argtypes = [_LP, _P, _D, _D, _D, _D, _D, _D, _P]
+        L.or_rhs_forced.restype = _I
+        L.or_rhs_forced.argtypes = [_P, _P, _L, _L, _L, _D, _D, _D, _D, _D, _I, _I, _D, _D, _LP,
+                                    _D, _P]
+        L.or_substep_forced.restype = _I
+        L.or_substep_forced.argtypes = [_P, _P, _P, _P, _I, _D, _I, _L, _L, _L, _D, _D, _D, _D,
+                                        _D, _I, _D, _LP, _D, _P]
         _lib = L
     return _lib
 
@@ -208,3 +217,51 @@ def box_filter(fine, r=4):
     out = np.zeros((nf, nz // r, ny // r, nx // r))
     lib().or_box_filter(_p(f), _p(out), nx, ny, nz, r, nf)
     return out
+
+
+# ---------------------------------------------------------------- forcing
+
+def _kvec(k):
+    a = np.ascontiguousarray(np.asarray(k, dtype=np.int64).reshape(3), dtype=ctypes.c_long)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_long))
+
+
+def forcing_amplitude(k, e, f0, cs, dt, lengths=(2 * np.pi,) * 3):
+    """N f_k of Eq. 21 for integer wave vector k (physical k_i = 2 pi k_i / L_i)
+    and unit vector e (Sect. 6)."""
+    ka, kp = _kvec(k)
+    ev = _f64(np.asarray(e, dtype=np.float64).reshape(3))
+    out = np.zeros(3)
+    if lib().or_forcing_amplitude(kp, _p(ev), f0, cs, dt, *lengths, _p(out)):
+        raise ValueError("f_k undefined: k is zero or parallel to e")
+    return out
+
+
+def rhs_forced(state, grid, phys, dt, f0, k, phi, e, form=FORM_55P):
+    """d(state)/dt of Eqs. 1-3 with the forcing of Eqs. 20-21 for one step."""
+    st = _f64(state)
+    out = np.zeros_like(st)
+    ka, kp = _kvec(k)
+    ev = _f64(np.asarray(e, dtype=np.float64).reshape(3))
+    if lib().or_rhs_forced(_p(st), _p(out), *grid.dims()[:6], phys.cs, phys.nu,
+                           phys.entropy_mode, form, dt, f0, kp, phi, _p(ev)):
+        raise ValueError("f_k undefined")
+    return out
+
+
+def rk3_step_forced(state, dt, grid, phys, f0, ks, phis, es, form=FORM_55P):
+    """len(phis) RK3 steps; step i is forced with ks[i], phis[i], es[i]."""
+    st = _f64(state).copy()
+    w = np.zeros_like(st)
+    divf = np.zeros(grid.shape)
+    for i in range(len(phis)):
+        ka, kp = _kvec(ks[i])
+        ev = _f64(np.asarray(es[i], dtype=np.float64).reshape(3))
+        for s in range(3):
+            out = np.zeros_like(st)
+            if lib().or_substep_forced(_p(st), _p(w), _p(out), _p(divf), s, dt, form,
+                                       *grid.dims()[:6], phys.cs, phys.nu, phys.entropy_mode,
+                                       f0, kp, float(phis[i]), _p(ev)):
+                raise ValueError("f_k undefined")
+            st = out
+    return st

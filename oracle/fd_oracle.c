@@ -17,7 +17,12 @@
  *   - nested first derivatives ....... Eq. 9  (19-point form: D1 of the
  *                                      stored D1-divergence)
  *   - continuity ..................... Eq. 1, log-density form
- *   - momentum ....................... Eq. 2 with the body force f = 0
+ *   - momentum ....................... Eq. 2; the body force f = 0, or the
+ *                                      non-helical random-k forcing of
+ *                                      Sect. 6 (Eqs. 20-21) for one step:
+ *                                      f = N f_k cos(k.x + phi),
+ *                                      N = f0 c_s sqrt(|k| c_s / dt),
+ *                                      f_k = k x e / sqrt(|k|^2 - (k.e)^2)
  *   - traceless rate of strain ....... Eq. 3
  *   - 2N-storage RK3 ................. Eq. 10, Algorithm 2 (55-point,
  *                                      single pass) and Algorithm 3 with
@@ -206,13 +211,60 @@ typedef struct {
     int nfields;
 } phys_t;
 
+/* The external force of Eq. 2 for one time step, Sect. 6 (Eqs. 20-21):
+ * f(x) = Re{ N f_k exp(i k.x + i phi) } = N f_k cos(k.x + phi), f_k real. */
+typedef struct {
+    int on;
+    double k[3];   /* wave vector, physical units */
+    double phi;    /* phase */
+    double amp[3]; /* N f_k */
+} forcing_t;
+
+/* N f_k of Eq. 21 for the integer wave vector kint (physical k_i =
+ * 2 pi kint_i / L_i), the unit vector e, the scale f0, the sound speed and
+ * the time step:  N = f0 c_s sqrt(|k| c_s / dt),
+ * f_k = (k x e) / sqrt(|k|^2 - (k.e)^2).  Returns 0, or -1 when k is zero
+ * or parallel to e (f_k undefined). */
+int or_forcing_amplitude(const long *kint, const double *e, double f0, double cs, double dt,
+                         double lx, double ly, double lz, double *amp)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    const double k[3] = {two_pi * (double)kint[0] / lx, two_pi * (double)kint[1] / ly,
+                         two_pi * (double)kint[2] / lz};
+    const double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const double ke = k[0] * e[0] + k[1] * e[1] + k[2] * e[2];
+    const double den2 = kk - ke * ke;
+    if (!(kk > 0.0) || !(den2 > 1e-24 * kk))
+        return -1;
+    const double kn = sqrt(kk);
+    const double N = f0 * cs * sqrt(kn * cs / dt);
+    const double kxe[3] = {k[1] * e[2] - k[2] * e[1], k[2] * e[0] - k[0] * e[2],
+                           k[0] * e[1] - k[1] * e[0]};
+    const double den = sqrt(den2);
+    for (int i = 0; i < 3; ++i)
+        amp[i] = N * kxe[i] / den;
+    return 0;
+}
+
+static int make_forcing(forcing_t *fo, const long *kint, double phi, const double *e, double f0,
+                        double cs, double dt, double lx, double ly, double lz)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    fo->on = 1;
+    fo->k[0] = two_pi * (double)kint[0] / lx;
+    fo->k[1] = two_pi * (double)kint[1] / ly;
+    fo->k[2] = two_pi * (double)kint[2] / lz;
+    fo->phi = phi;
+    return or_forcing_amplitude(kint, e, f0, cs, dt, lx, ly, lz, fo->amp);
+}
+
 /* Terms of Eqs. 1-3 at point p that need only first and second derivatives
  * along the axes (everything except the grad(div u) term of Eq. 2).
  * rhs[0] = d lnrho/dt, rhs[1..3] = du_i/dt without (nu/3) grad(div u),
  * rhs[4] = ds/dt (when carried).  Also returns div u and the first
  * derivatives it was built from. */
 static void rhs_axial(const double *state, const grid_t *g, const phys_t *ph, const long *p,
-                      double *rhs)
+                      const forcing_t *fo, double *rhs)
 {
     const long n = g->npts;
     const double *lnrho = state;
@@ -253,6 +305,15 @@ static void rhs_axial(const double *state, const grid_t *g, const phys_t *ph, co
             sgl += S[i][j] * glnrho[j];
         }
         rhs[1 + i] = -adv - ph->cs2 * glnrho[i] + ph->nu * (lap + 2.0 * sgl);
+    }
+
+    /* Eq. 2's f: the forcing of Eq. 20 at x = (x_i, y_j, z_l) = grid point p */
+    if (fo && fo->on) {
+        const double phase = fo->k[0] * (double)p[0] * g->h[0] + fo->k[1] * (double)p[1] * g->h[1] +
+                             fo->k[2] * (double)p[2] * g->h[2] + fo->phi;
+        const double cph = cos(phase);
+        for (int i = 0; i < 3; ++i)
+            rhs[1 + i] += fo->amp[i] * cph;
     }
 
     /* passive entropy: ds/dt = -u . grad s */
@@ -301,8 +362,9 @@ static phys_t make_phys(double cs, double nu, int entropy_mode)
 /* Full right-hand side d(state)/dt of Eqs. 1-3 on the whole grid.
  * form 0: 55-point (grad div u from Eqs. 7-8);
  * form 1: 19-point (grad div u as D1 of the D1-divergence, Eq. 9). */
-void or_rhs(const double *state, double *rhs, long nx, long ny, long nz, double lx, double ly,
-            double lz, double cs, double nu, int entropy_mode, int form)
+static void rhs_grid(const double *state, double *rhs, long nx, long ny, long nz, double lx,
+                     double ly, double lz, double cs, double nu, int entropy_mode, int form,
+                     const forcing_t *fo)
 {
     grid_t g = make_grid(nx, ny, nz, lx, ly, lz);
     phys_t ph = make_phys(cs, nu, entropy_mode);
@@ -323,7 +385,7 @@ void or_rhs(const double *state, double *rhs, long nx, long ny, long nz, double 
                 long p[3] = {x, y, z};
                 long c = at(&g, p);
                 double r[5], gd[3];
-                rhs_axial(state, &g, &ph, p, r);
+                rhs_axial(state, &g, &ph, p, fo, r);
                 if (form == 1) {
                     for (int i = 0; i < 3; ++i)
                         gd[i] = d1(divf, &g, p, i);
@@ -336,6 +398,27 @@ void or_rhs(const double *state, double *rhs, long nx, long ny, long nz, double 
                     rhs[f * n + c] = r[f];
             }
     free(divf);
+}
+
+void or_rhs(const double *state, double *rhs, long nx, long ny, long nz, double lx, double ly,
+            double lz, double cs, double nu, int entropy_mode, int form)
+{
+    rhs_grid(state, rhs, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, form, NULL);
+}
+
+/* The right-hand side with the forcing of Sect. 6 (Eqs. 20-21) for wave
+ * vector kint (integers, k_i = 2 pi kint_i / L_i), phase phi, unit vector e,
+ * scale f0 and time step dt (N depends on dt).  Returns -1 when f_k is
+ * undefined (k zero or parallel to e). */
+int or_rhs_forced(const double *state, double *rhs, long nx, long ny, long nz, double lx,
+                  double ly, double lz, double cs, double nu, int entropy_mode, int form,
+                  double dt, double f0, const long *kint, double phi, const double *e)
+{
+    forcing_t fo;
+    if (make_forcing(&fo, kint, phi, e, f0, cs, dt, lx, ly, lz))
+        return -1;
+    rhs_grid(state, rhs, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, form, &fo);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -364,8 +447,9 @@ static inline void rk3_update(int s, double dt, double r, double in, double *w, 
 
 /* One substep s (0, 1, 2) of Algorithm 2 (55-point, single pass): reads
  * `in` and `w` (the 2N register, u-tilde), writes `out` and `w`. */
-void or_substep55(const double *in, double *w, double *out, int s, double dt, long nx, long ny,
-                  long nz, double lx, double ly, double lz, double cs, double nu, int entropy_mode)
+static void substep55(const double *in, double *w, double *out, int s, double dt, long nx,
+                      long ny, long nz, double lx, double ly, double lz, double cs, double nu,
+                      int entropy_mode, const forcing_t *fo)
 {
     grid_t g = make_grid(nx, ny, nz, lx, ly, lz);
     phys_t ph = make_phys(cs, nu, entropy_mode);
@@ -377,7 +461,7 @@ void or_substep55(const double *in, double *w, double *out, int s, double dt, lo
                 long p[3] = {x, y, z};
                 long c = at(&g, p);
                 double r[5], gd[3];
-                rhs_axial(in, &g, &ph, p, r);
+                rhs_axial(in, &g, &ph, p, fo, r);
                 graddiv55(in, &g, p, gd);
                 for (int i = 0; i < 3; ++i)
                     r[1 + i] += (ph.nu / 3.0) * gd[i];
@@ -391,9 +475,9 @@ void or_substep55(const double *in, double *w, double *out, int s, double dt, lo
  * velocity gets the partial update without (nu/3) grad(div u); pass 2
  * adds dt (nu/3) grad(div u) to w and beta dt (nu/3) grad(div u) to out,
  * with grad taken by Eq. 6 on the stored divergence (Eq. 9). */
-void or_substep19(const double *in, double *w, double *out, double *divf, int s, double dt,
-                  long nx, long ny, long nz, double lx, double ly, double lz, double cs, double nu,
-                  int entropy_mode)
+static void substep19(const double *in, double *w, double *out, double *divf, int s, double dt,
+                      long nx, long ny, long nz, double lx, double ly, double lz, double cs,
+                      double nu, int entropy_mode, const forcing_t *fo)
 {
     grid_t g = make_grid(nx, ny, nz, lx, ly, lz);
     phys_t ph = make_phys(cs, nu, entropy_mode);
@@ -407,7 +491,7 @@ void or_substep19(const double *in, double *w, double *out, double *divf, int s,
                 long c = at(&g, p);
                 double r[5];
                 divf[c] = divergence(in, &g, p);
-                rhs_axial(in, &g, &ph, p, r);
+                rhs_axial(in, &g, &ph, p, fo, r);
                 for (int f = 0; f < ph.nfields; ++f)
                     rk3_update(s, dt, r[f], in[f * n + c], &w[f * n + c], &out[f * n + c]);
             }
@@ -424,6 +508,38 @@ void or_substep19(const double *in, double *w, double *out, double *divf, int s,
                     out[(1 + i) * n + c] += RK3_BETA[s] * dt * (ph.nu / 3.0) * gdi;
                 }
             }
+}
+
+void or_substep55(const double *in, double *w, double *out, int s, double dt, long nx, long ny,
+                  long nz, double lx, double ly, double lz, double cs, double nu, int entropy_mode)
+{
+    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL);
+}
+
+void or_substep19(const double *in, double *w, double *out, double *divf, int s, double dt,
+                  long nx, long ny, long nz, double lx, double ly, double lz, double cs, double nu,
+                  int entropy_mode)
+{
+    substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL);
+}
+
+/* One substep with the forcing of the current time step (k, phi and e are
+ * fixed over the step's three substeps; N uses the step's dt).  form 0:
+ * Algorithm 2, form 1: Algorithm 3 (divf is then required).  Returns -1
+ * when f_k is undefined. */
+int or_substep_forced(const double *in, double *w, double *out, double *divf, int s, double dt,
+                      int form, long nx, long ny, long nz, double lx, double ly, double lz,
+                      double cs, double nu, int entropy_mode, double f0, const long *kint,
+                      double phi, const double *e)
+{
+    forcing_t fo;
+    if (make_forcing(&fo, kint, phi, e, f0, cs, dt, lx, ly, lz))
+        return -1;
+    if (form == 1)
+        substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo);
+    else
+        substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

@@ -23,6 +23,12 @@ only the shear wave and the explosion shell):
 * ``explosion``: radial Gaussian velocity shell, u = u_ampl exp(-(r - r_s)^2
   / (2 d^2)) e_r about the box centre (Sect. 6; the printed exponent lacks
   its minus sign).
+* ``forcing_sequence``: the random draws of the non-helical forcing (Sect.
+  6): per time step an integer wave vector picked uniformly from the
+  isotropic set of all integer vectors with kmin <= |k| <= kmax, a phase
+  uniform in [0, 2 pi), and a unit vector e perpendicular to k (uniform
+  direction in that plane).  Only the draws live here; the forcing itself
+  (N, f_k, the field) is computed by the solver and the oracle.
 """
 import os
 
@@ -142,3 +148,35 @@ def random_state(shape, seed, scale=0.05, nfields=5):
     """Plain seeded normal noise on every field (edge-case parity inputs)."""
     rng = np.random.default_rng(seed)
     return scale * rng.standard_normal((nfields,) + tuple(shape))
+
+
+def forcing_set(kmin, kmax):
+    """All integer wave vectors with kmin <= |k| <= kmax (isotropic set)."""
+    r = int(np.floor(kmax))
+    ks = []
+    for kz in range(-r, r + 1):
+        for ky in range(-r, r + 1):
+            for kx in range(-r, r + 1):
+                m2 = kx * kx + ky * ky + kz * kz
+                if kmin * kmin <= m2 <= kmax * kmax and m2 > 0:
+                    ks.append((kx, ky, kz))
+    return np.array(ks, dtype=np.int64)
+
+
+def forcing_sequence(seed, nsteps, kmin=1.0, kmax=2.0):
+    """(k[nsteps, 3] int, phi[nsteps], e[nsteps, 3]) for `nsteps` forced steps."""
+    rng = np.random.default_rng(seed)
+    pool = forcing_set(kmin, kmax)
+    ks = pool[rng.integers(0, len(pool), size=nsteps)]
+    phis = rng.uniform(0.0, TWO_PI, size=nsteps)
+    es = np.zeros((nsteps, 3))
+    for i in range(nsteps):
+        kh = ks[i] / np.linalg.norm(ks[i])
+        while True:
+            v = rng.standard_normal(3)
+            v -= np.dot(v, kh) * kh
+            nv = np.linalg.norm(v)
+            if nv > 1e-3:
+                es[i] = v / nv
+                break
+    return ks, phis, es
