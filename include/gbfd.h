@@ -144,6 +144,22 @@ gbfd_status gbfd_diagnostics(gbfd_ctx *ctx, gbfd_diag *out);
  * rule; this is the helper used by the benchmarks).  Synchronises. */
 gbfd_status gbfd_cfl_dt(gbfd_ctx *ctx, double cfl, double cnu, double *dt_out);
 
+/* nsteps RK3 steps with the non-helical random-k body force of Sect. 6
+ * (Eqs. 20-21) in Eq. 2: step n adds f(x) = N f_k cos(k.x + phi) to the
+ * momentum equation, with the integer wave vector k[3n..3n+2] (physical
+ * k_i = 2 pi k_i / L_i), phase phi[n], unit vector e[3n..3n+2] (not parallel
+ * to k), N = f0 c_s sqrt(|k| c_s / dt) and f_k = (k x e) / sqrt(|k|^2 -
+ * (k.e)^2); k, phi and e stay fixed over the step's three substeps.  The
+ * paper draws k from an isotropic set kmin <= |k| <= kmax and phi, e at
+ * random every step; the caller supplies the draws.  k, phi, e are host
+ * arrays of 3n, n and 3n values.  Each step first fills per-axis phase
+ * tables in the workspace (one small launch).  Every precision and form is
+ * supported; the FP32 tile table's entries all run the default kernel when
+ * forced.  Errors: INVALID_ARG (dt <= 0 or not finite, nsteps < 0, NULL
+ * arrays, k = 0, k parallel to e, phi not finite), CUDA. */
+gbfd_status gbfd_rk3_step_forced(gbfd_ctx *ctx, double dt, int nsteps, double f0, const int *k,
+                                 const double *phi, const double *e);
+
 /* Wait for the context's stream and report any device-side error
  * (bounded waits that gave up -> TIMEOUT; CUDA errors -> CUDA). */
 gbfd_status gbfd_sync(gbfd_ctx *ctx);

@@ -40,6 +40,8 @@ struct gbfd_ctx {
     int tile_cfg;     // index into the tiled kernel's tile table (-1 = default)
     int fault_skip;   // test-only fault injection (-1 = off)
     int host_path;    // 0 = pinned host buffers accessed in place, 1 = always staged
+    Forcing fo;       // forcing of the step being taken (fo.on = 0: none)
+    double2 *ftab;    // its per-axis phase tables (workspace)
     TmapCache tmaps;  // encoded TMA descriptors of the two state buffers
     bool broken;
     Coef<double> c64;
@@ -133,7 +135,7 @@ bool validate(const gbfd_params *p, char *why, size_t n)
 
 struct Plan {
     Layout Ls, Lw, Ld;
-    size_t off_state[2], off_w, off_div, off_staging, off_part, off_out, off_err, total;
+    size_t off_state[2], off_w, off_div, off_staging, off_part, off_out, off_err, off_ftab, total;
     int ndiag;
 };
 
@@ -165,6 +167,8 @@ Plan make_plan(const gbfd_params *p)
     off = align256(off + 16 * sizeof(double));
     pl.off_err = off;
     off = align256(off + 256);
+    pl.off_ftab = off;  // forcing phase tables, (nx + ny + nz) complex FP64
+    off = align256(off + (size_t)(p->nx + p->ny + p->nz) * 16);
     pl.total = off;
     return pl;
 }
@@ -251,6 +255,7 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
     StateBufs b = bufs(c);
     RKStage st = make_stage(s, dt, c->p.nu);
     st.fault_skip_plane = c->fault_skip;
+    st.fo = c->fo;
     int n = 0;
     cudaError_t e = cudaSuccess;
     const bool tiled = c->kernel_path == 0;
@@ -373,6 +378,8 @@ gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_by
     c->diag_part = (double *)(c->ws + pl.off_part);
     c->diag_out = (double *)(c->ws + pl.off_out);
     c->dev_error = (int *)(c->ws + pl.off_err);
+    c->ftab = (double2 *)(c->ws + pl.off_ftab);
+    memset(&c->fo, 0, sizeof c->fo);
     c->ndiag = pl.ndiag;
     c->cur = 0;
     c->launches = 0;
@@ -526,6 +533,68 @@ gbfd_status gbfd_rk3_step(gbfd_ctx *ctx, double dt, int nsteps)
             if (st != GBFD_OK)
                 return st;
         }
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_rk3_step_forced(gbfd_ctx *ctx, double dt, int nsteps, double f0, const int *k,
+                                 const double *phi, const double *e)
+{
+    gbfd_status st = check_ctx(ctx);
+    if (st != GBFD_OK)
+        return st;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt) || !std::isfinite(f0)) {
+        set_err(ctx, "rk3_step_forced: dt %g / nsteps %d / f0 %g rejected", dt, nsteps, f0);
+        return GBFD_ERR_INVALID_ARG;
+    }
+    if (nsteps > 0 && (!k || !phi || !e)) {
+        set_err(ctx, "rk3_step_forced: k, phi and e must not be NULL");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    const double L[3] = {ctx->p.lx, ctx->p.ly, ctx->p.lz};
+    for (int n = 0; n < nsteps; ++n) {
+        // Eq. 21: N = f0 c_s sqrt(|k| c_s / dt), f_k = (k x e) / sqrt(|k|^2 - (k.e)^2),
+        // with the physical wave vector k_i = 2 pi kint_i / L_i
+        const int *ki = k + 3 * n;
+        const double *ei = e + 3 * n;
+        double kp[3], kk = 0.0, ke = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            kp[a] = two_pi * (double)ki[a] / L[a];
+            kk += kp[a] * kp[a];
+            ke += kp[a] * ei[a];
+        }
+        const double den2 = kk - ke * ke;
+        if (!(kk > 0.0) || !(den2 > 1e-24 * kk) || !std::isfinite(phi[n])) {
+            set_err(ctx, "rk3_step_forced: step %d: k zero or parallel to e, or phi not finite", n);
+            return GBFD_ERR_INVALID_ARG;
+        }
+        const double N = f0 * ctx->p.cs * std::sqrt(std::sqrt(kk) * ctx->p.cs / dt);
+        const double kxe[3] = {kp[1] * ei[2] - kp[2] * ei[1], kp[2] * ei[0] - kp[0] * ei[2],
+                               kp[0] * ei[1] - kp[1] * ei[0]};
+        const double den = std::sqrt(den2);
+        Forcing fo;
+        fo.on = 1;
+        for (int a = 0; a < 3; ++a)
+            fo.amp[a] = N * kxe[a] / den;
+        fo.tx = ctx->ftab;
+        fo.ty = ctx->ftab + ctx->p.nx;
+        fo.tz = ctx->ftab + ctx->p.nx + ctx->p.ny;
+        int nl = 0;
+        cudaError_t ce = launch_forcing_tables(ki[0], ki[1], ki[2], phi[n], ctx->p.nx, ctx->p.ny,
+                                               ctx->p.nz, ctx->ftab, ctx->stream, &nl);
+        ctx->launches += nl;
+        if (ce != cudaSuccess)
+            return cuda_fail(ctx, ce, "forcing tables");
+        ctx->fo = fo;
+        for (int s = 0; s < 3; ++s) {
+            st = do_substep(ctx, s, dt);
+            if (st != GBFD_OK)
+                break;
+        }
+        memset(&ctx->fo, 0, sizeof ctx->fo);
+        if (st != GBFD_OK)
+            return st;
+    }
     return GBFD_OK;
 }
 

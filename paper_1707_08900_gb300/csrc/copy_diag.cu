@@ -1,6 +1,7 @@
 // State copies into/out of the padded layout and the FP64 diagnostics
 // reductions (mass, kinetic energy, max |u| for the time-step rule, per-field
 // rms and max, non-finite flag).
+#include <cmath>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -270,6 +271,47 @@ cudaError_t launch_gather(const void *src, const Layout &L, void *dst, int dst_f
                         : gather_t((const double *)src, (float *)dst, L, nf, stream);
     return dst_fp64 ? gather_t((const float *)src, (double *)dst, L, nf, stream)
                     : gather_t((const float *)src, (float *)dst, L, nf, stream);
+}
+
+namespace {
+
+__global__ void k_forcing_tables(int kx, int ky, int kz, double cphi, double sphi, int nx, int ny,
+                                 int nz, double2 *__restrict__ tab)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx + ny + nz)
+        return;
+    int n, k, idx;
+    if (i < nx) {
+        n = nx, k = kx, idx = i;
+    } else if (i < nx + ny) {
+        n = ny, k = ky, idx = i - nx;
+    } else {
+        n = nz, k = kz, idx = i - nx - ny;
+    }
+    // exact integer reduction of the phase k idx / n (in turns)
+    long long m = ((long long)k * idx) % n;
+    m += m < 0 ? n : 0;
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)n, &sn, &cs);
+    if (i < nx) {
+        const double c2 = cs * cphi - sn * sphi, s2 = sn * cphi + cs * sphi;
+        cs = c2;
+        sn = s2;
+    }
+    tab[i] = make_double2(cs, sn);
+}
+
+}  // namespace
+
+cudaError_t launch_forcing_tables(int kx, int ky, int kz, double phi, int nx, int ny, int nz,
+                                  double2 *tab, cudaStream_t stream, int *launches)
+{
+    const int n = nx + ny + nz;
+    k_forcing_tables<<<(n + 255) / 256, 256, 0, stream>>>(kx, ky, kz, cos(phi), sin(phi), nx, ny,
+                                                           nz, tab);
+    *launches += 1;
+    return cudaGetLastError();
 }
 
 int diag_blocks(const Layout &L)

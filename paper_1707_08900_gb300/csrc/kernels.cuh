@@ -5,7 +5,26 @@
 
 namespace gbfd {
 
-// Per-substep scalars of Eq. 10.
+// The body force f of Eq. 2 for the current time step: the non-helical
+// forcing of Sect. 6 (Eqs. 20-21), f_i(x) = amp_i cos(k.x + phi) with
+// amp = N f_k.  cos(k.x + phi) = Re(tx[x] ty[y] tz[z]) from per-axis phase
+// tables ta[n] = exp(2 pi i (k_a n mod N_a) / N_a), tx also carrying
+// exp(i phi), so the phase is reduced exactly in integers.
+struct Forcing {
+    int on;
+    double amp[3];
+    const double2 *tx, *ty, *tz;
+};
+
+template <class T>
+__device__ __forceinline__ T forcing_cos(const Forcing &F, int x, int y, int z)
+{
+    const double2 a = __ldg(F.tx + x), b = __ldg(F.ty + y), c = __ldg(F.tz + z);
+    const double re = a.x * b.x - a.y * b.y, im = a.x * b.y + a.y * b.x;
+    return (T)(re * c.x - im * c.y);
+}
+
+// Per-substep scalars of Eq. 10 (and the step's forcing).
 struct RKStage {
     double alpha, beta, dt;
     double nu3;  // nu / 3, used by the second pass of the 19-point form
@@ -16,6 +35,7 @@ struct RKStage {
     int fault_skip_plane;  // test only: CTA 0 of the tiled kernel never copies
                            // this local plane (-1: off); its bounded wait must
                            // give up and report GBFD_ERR_TIMEOUT
+    Forcing fo;            // fo.on = 0: f = 0
 };
 
 inline RKStage make_stage(int s, double dt, double nu)
@@ -29,6 +49,9 @@ inline RKStage make_stage(int s, double dt, double nu)
     st.last = (s == 2);
     st.fault_skip_plane = -1;
     st.s = s;
+    st.fo.on = 0;
+    st.fo.amp[0] = st.fo.amp[1] = st.fo.amp[2] = 0.0;
+    st.fo.tx = st.fo.ty = st.fo.tz = nullptr;
     return st;
 }
 
@@ -44,6 +67,11 @@ cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKS
 
 // State copies between a compact [f][z][y][x] staging buffer (FP64 or FP32)
 // and the padded layout (ghosts filled on the way in).
+// Per-axis phase tables of the forcing (see Forcing): tab[0..nx) for x with
+// the phase phi, then ny entries for y, then nz for z.
+cudaError_t launch_forcing_tables(int kx, int ky, int kz, double phi, int nx, int ny, int nz,
+                                  double2 *tab, cudaStream_t stream, int *launches);
+
 cudaError_t launch_scatter(const void *src, int src_fp64, void *dst, const Layout &L, int nf,
                            cudaStream_t stream, int *launches);
 cudaError_t launch_gather(const void *src, const Layout &L, void *dst, int dst_fp64, int nf,

@@ -60,6 +60,12 @@ __global__ void __launch_bounds__(128) k_substep_simple(const TS *__restrict__ i
     gather_derivs<TS, NF, MIXED>(A, c, d);
     TS r[5];
     rhs_point<TS, NF>(d, c, r);
+    if (st.fo.on) {
+        const TS fc = forcing_cos<TS>(st.fo, x, y, z);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            r[1 + i] += (TS)st.fo.amp[i] * fc;
+    }
     if (!MIXED) {
         TS div = d.gu[0][0] + d.gu[1][1] + d.gu[2][2];
         store_ghosted(divf, Ls, 0, z, y, x, div);

@@ -110,7 +110,7 @@ __device__ __forceinline__ void init_barriers(uint64_t *bars, int n)
 // advanced on return.  Returns false when a bounded wait gave up (after
 // recording it and draining the copies in flight).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK,
-          int U, bool WG, bool ICVT = false, class CoefT>
+          int U, bool WG, bool ICVT = false, bool FORCE = false, class CoefT>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            TS *__restrict__ out, TW *__restrict__ w,
                                            TS *__restrict__ divf, const Layout &Ls,
@@ -119,7 +119,8 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                                            const bool last, const int x0, const int y0,
                                            const int z0, const int nout, int &jrun, int &wrun,
                                            unsigned char *smem, int *dev_error,
-                                           const int skip_plane = -1)
+                                           const int skip_plane = -1,
+                                           const Forcing *fo = nullptr)
 {
     // WG: u-tilde read straight from global memory (no u-tilde ring)
     static_assert(!WG || PK, "global u-tilde reads only in the packed form");
@@ -143,6 +144,16 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     // element offset of point (x, y) in a field of a slot; even, so pairs align
     const int toff = (ty + GY) * BX + (2 * tx + GX);
     const bool need_w = !first;
+    // FORCE: the body force of Eq. 2 (Sect. 6); the column's x-y phase factor
+    // Re/Im of tx[x] ty[y] for both points, times tz[z] per plane
+    float2 fxy0 = make_float2(0.f, 0.f), fxy1 = make_float2(0.f, 0.f);
+    if constexpr (FORCE) {
+        if (valid0) {
+            const double2 a0 = __ldg(fo->tx + x), a1 = __ldg(fo->tx + x + 1), b = __ldg(fo->ty + y);
+            fxy0 = make_float2((float)(a0.x * b.x - a0.y * b.y), (float)(a0.x * b.y + a0.y * b.x));
+            fxy1 = make_float2((float)(a1.x * b.x - a1.y * b.y), (float)(a1.x * b.y + a1.y * b.x));
+        }
+    }
 
     // every thread is done with the previous column's slots
     __syncthreads();
@@ -549,6 +560,15 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                                 *reinterpret_cast<V *>(divf + gi + gdy + gdx) = dv;
                         }
                     }
+                    if constexpr (FORCE) {
+                        // f_i = amp_i cos(k.x + phi)
+                        const double2 cz = __ldg(fo->tz + zo);
+                        const float czr = (float)cz.x, czi = (float)cz.y;
+                        const V fc = P::mk(fxy0.x * czr - fxy0.y * czi, fxy1.x * czr - fxy1.y * czi);
+    #pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            acc[1 + a] = P::fma(P::bc((float)fo->amp[a]), fc, acc[1 + a]);
+                    }
     #pragma unroll
                     for (int f = 0; f < NF; ++f) {
                         const V r = f < 4 ? acc[f] : rs;
@@ -888,7 +908,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 
 // Single box: one CTA per (tile, z-chunk).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK, int U,
-          int MINB, bool WG, bool ICVT>
+          int MINB, bool WG, bool ICVT, bool FORCE>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
@@ -903,17 +923,17 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U, WG, ICVT>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
+    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U, WG, ICVT, FORCE>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
                                                   (TA)st.alpha, (TA)st.beta, (TA)st.dt,
                                                   st.first != 0, st.last != 0, x0, y0, z0, nout,
                                                   jrun, wrun, smem, dev_error,
-                                                  blockIdx.x == 0 && blockIdx.y == 0 ? skip_plane : -1);
+                                                  blockIdx.x == 0 && blockIdx.y == 0 ? skip_plane : -1, &st.fo);
 }
 
 }  // namespace tiled2
 
 template <class TS, class TW, class TA, int TX, int TY, int NS, bool PK = false, int U = 1,
-          int MINB = 1, bool WG = false, bool ICVT = false>
+          int MINB = 1, bool WG = false, bool ICVT = false, bool FORCE_OK = false>
 cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
                            int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
@@ -932,15 +952,29 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
     TW *w = (TW *)b.w;
     TS *divf = (TS *)b.div;
     cudaError_t e;
-#define GBFD_LAUNCH2(NFV, MIX)                                                                    \
+    // a forced step needs the forcing instantiation (FORCE_OK variants only)
+    if (st.fo.on && !FORCE_OK)
+        return cudaErrorNotSupported;
+#define GBFD_LAUNCH2_K(NFV, MIX, FRC)                                                             \
     do {                                                                                          \
-        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB, WG, ICVT>;   \
+        auto kern =                                                                               \
+            tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB, WG, ICVT, FRC>;  \
         constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS, WG ? 0 : U + 2>::BYTES;          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \
         kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, divf, b.Ls, b.Lw, c, st, zc,       \
                                           tiles_x, dev_error, skip_plane);                        \
+    } while (0)
+#define GBFD_LAUNCH2(NFV, MIX)                                                                    \
+    do {                                                                                          \
+        if constexpr (FORCE_OK) {                                                                 \
+            if (st.fo.on) {                                                                       \
+                GBFD_LAUNCH2_K(NFV, MIX, true);                                                   \
+                break;                                                                            \
+            }                                                                                     \
+        }                                                                                         \
+        GBFD_LAUNCH2_K(NFV, MIX, false);                                                          \
     } while (0)
     if (form == 0) {
         if (nf == 5)
@@ -954,6 +988,7 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
             GBFD_LAUNCH2(4, false);
     }
 #undef GBFD_LAUNCH2
+#undef GBFD_LAUNCH2_K
     *launches += 1;
     return cudaGetLastError();
 }

@@ -19,9 +19,11 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     cudaError_t e;
     // FP64 u-tilde doubles its ring: a 6-slot state ring keeps two CTAs per SM
     constexpr int NSP = sizeof(TW) == 8 ? 6 : 8;
-    const int v = (idx / kZcChoices) % 3;
+    int v = (idx / kZcChoices) % 3;
+    if (st.fo.on && v == 2)
+        v = 0;  // forced steps: the packed kernel with the forcing instantiation
     if (v == 0)
-        e = launch_px2_cfg<TS, TW, TA, 32, 8, NSP, true, 2, 1, false, true>(
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, NSP, true, 2, 1, false, true, true>(
             b, c, st, nf, form, t.zc, 0, dev_error, cache, stream, launches);
     else if (v == 1)
         e = launch_tiled_cfg<TS, TW, TA, 32, 8, 9>(b, c, st, nf, form, t.zc, 1, dev_error, cache,

@@ -19,7 +19,9 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     // z-chunk 32 (fastest at 256^3 and 512^3 on GB300 in the tile sweep)
     const int idx = cfg < 0 ? kDefaultF32 : cfg;
     const TileConfig t = tiled_config(4, idx);
-    const int v = idx / kZcChoices;
+    // a forced step (Sect. 6 forcing) runs on the default kernel, whatever
+    // the tile table entry
+    const int v = st.fo.on ? kDefaultF32 / kZcChoices : idx / kZcChoices;
     cudaError_t e;
     switch (v) {
     case 0:
@@ -55,8 +57,8 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
                                                        cache, stream, launches);
         break;
     case 8:
-        e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2>(b, c, st, nf, form, t.zc, v, dev_error,
-                                                          cache, stream, launches);
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2, 1, false, false, true>(
+            b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
         break;
     case 9:
         e = launch_px2_cfg<TS, TW, TA, 32, 8, 7, true, 3>(b, c, st, nf, form, t.zc, v, dev_error,

@@ -28,7 +28,7 @@ FORMS = {"55p": GBFD_55P, "19p": GBFD_19P}
 
 # exported symbols of include/gbfd.h (checked by the ABI test)
 EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state",
-           "gbfd_get_state", "gbfd_rk3_step", "gbfd_substep", "gbfd_diagnostics", "gbfd_cfl_dt",
+           "gbfd_get_state", "gbfd_rk3_step", "gbfd_rk3_step_forced", "gbfd_substep", "gbfd_diagnostics", "gbfd_cfl_dt",
            "gbfd_sync", "gbfd_set_option", "gbfd_launch_count", "gbfd_last_error",
            "gbfd_status_string", "gbfd_diagnostics_noalloc", "gbfd_autotune",
            "gbfd_batch_workspace_bytes", "gbfd_batch_init", "gbfd_batch_destroy",
@@ -94,6 +94,10 @@ def load(path=None):
     L.gbfd_set_state.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int]
     L.gbfd_get_state.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int]
     L.gbfd_rk3_step.argtypes = [_VP, ctypes.c_double, ctypes.c_int]
+    L.gbfd_rk3_step_forced.argtypes = [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
     L.gbfd_substep.argtypes = [_VP, ctypes.c_int, ctypes.c_double]
     L.gbfd_diagnostics.argtypes = [_VP, ctypes.POINTER(gbfd_diag)]
     L.gbfd_cfl_dt.argtypes = [_VP, ctypes.c_double, ctypes.c_double,
@@ -189,6 +193,19 @@ def gbfd_get_state(ctx, dst_ptr, dst_on_device, dst_is_fp64):
 
 def gbfd_rk3_step(ctx, dt, nsteps):
     _check(load().gbfd_rk3_step(ctx, float(dt), int(nsteps)), ctx)
+
+
+def gbfd_rk3_step_forced(ctx, dt, f0, k, phi, e):
+    """len(phi) forced RK3 steps: k (n, 3) integers, phi (n,), e (n, 3)."""
+    k = np.ascontiguousarray(np.asarray(k).reshape(-1, 3), dtype=np.int32)
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(-1))
+    e = np.ascontiguousarray(np.asarray(e, dtype=np.float64).reshape(-1, 3))
+    n = phi.shape[0]
+    assert k.shape[0] == n and e.shape[0] == n
+    _check(load().gbfd_rk3_step_forced(
+        ctx, float(dt), int(n), float(f0), k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
 
 
 def gbfd_substep(ctx, s, dt):
@@ -321,6 +338,10 @@ class Solver:
 
     def rk3_step(self, dt, nsteps=1):
         gbfd_rk3_step(self.ctx, dt, nsteps)
+
+    def rk3_step_forced(self, dt, f0, k, phi, e):
+        """Forced RK3 steps (Sect. 6): one step per entry of phi."""
+        gbfd_rk3_step_forced(self.ctx, dt, f0, k, phi, e)
 
     def substep(self, s, dt):
         gbfd_substep(self.ctx, s, dt)
