@@ -167,8 +167,8 @@ Plan make_plan(const gbfd_params *p)
     off = align256(off + 16 * sizeof(double));
     pl.off_err = off;
     off = align256(off + 256);
-    pl.off_ftab = off;  // forcing phase tables, (nx + ny + nz) complex FP64
-    off = align256(off + (size_t)(p->nx + p->ny + p->nz) * 16);
+    pl.off_ftab = off;  // forcing phase tables, (nx + ny + nz) complex FP64, then FP32
+    off = align256(off + (size_t)(p->nx + p->ny + p->nz) * 24);
     pl.total = off;
     return pl;
 }
@@ -574,14 +574,20 @@ gbfd_status gbfd_rk3_step_forced(gbfd_ctx *ctx, double dt, int nsteps, double f0
         const double den = std::sqrt(den2);
         Forcing fo;
         fo.on = 1;
-        for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a) {
             fo.amp[a] = N * kxe[a] / den;
+            fo.amp32[a] = (float)fo.amp[a];
+        }
         fo.tx = ctx->ftab;
         fo.ty = ctx->ftab + ctx->p.nx;
         fo.tz = ctx->ftab + ctx->p.nx + ctx->p.ny;
+        float2 *t32 = reinterpret_cast<float2 *>(ctx->ftab + ctx->p.nx + ctx->p.ny + ctx->p.nz);
+        fo.tx32 = t32;
+        fo.ty32 = t32 + ctx->p.nx;
+        fo.tz32 = t32 + ctx->p.nx + ctx->p.ny;
         int nl = 0;
         cudaError_t ce = launch_forcing_tables(ki[0], ki[1], ki[2], phi[n], ctx->p.nx, ctx->p.ny,
-                                               ctx->p.nz, ctx->ftab, ctx->stream, &nl);
+                                               ctx->p.nz, ctx->ftab, t32, ctx->stream, &nl);
         ctx->launches += nl;
         if (ce != cudaSuccess)
             return cuda_fail(ctx, ce, "forcing tables");

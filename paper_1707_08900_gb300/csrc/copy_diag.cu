@@ -276,7 +276,7 @@ cudaError_t launch_gather(const void *src, const Layout &L, void *dst, int dst_f
 namespace {
 
 __global__ void k_forcing_tables(int kx, int ky, int kz, double cphi, double sphi, int nx, int ny,
-                                 int nz, double2 *__restrict__ tab)
+                                 int nz, double2 *__restrict__ tab, float2 *__restrict__ tab32)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx + ny + nz)
@@ -300,16 +300,18 @@ __global__ void k_forcing_tables(int kx, int ky, int kz, double cphi, double sph
         sn = s2;
     }
     tab[i] = make_double2(cs, sn);
+    tab32[i] = make_float2((float)cs, (float)sn);
 }
 
 }  // namespace
 
 cudaError_t launch_forcing_tables(int kx, int ky, int kz, double phi, int nx, int ny, int nz,
-                                  double2 *tab, cudaStream_t stream, int *launches)
+                                  double2 *tab, float2 *tab32, cudaStream_t stream,
+                                  int *launches)
 {
     const int n = nx + ny + nz;
     k_forcing_tables<<<(n + 255) / 256, 256, 0, stream>>>(kx, ky, kz, cos(phi), sin(phi), nx, ny,
-                                                           nz, tab);
+                                                           nz, tab, tab32);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -13,7 +13,9 @@ namespace gbfd {
 struct Forcing {
     int on;
     double amp[3];
+    float amp32[3];                    // amp rounded to FP32
     const double2 *tx, *ty, *tz;
+    const float2 *tx32, *ty32, *tz32;  // the same tables rounded to FP32
 };
 
 template <class T>
@@ -52,6 +54,7 @@ inline RKStage make_stage(int s, double dt, double nu)
     st.fo.on = 0;
     st.fo.amp[0] = st.fo.amp[1] = st.fo.amp[2] = 0.0;
     st.fo.tx = st.fo.ty = st.fo.tz = nullptr;
+    st.fo.tx32 = st.fo.ty32 = st.fo.tz32 = nullptr;
     return st;
 }
 
@@ -68,9 +71,10 @@ cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKS
 // State copies between a compact [f][z][y][x] staging buffer (FP64 or FP32)
 // and the padded layout (ghosts filled on the way in).
 // Per-axis phase tables of the forcing (see Forcing): tab[0..nx) for x with
-// the phase phi, then ny entries for y, then nz for z.
+// the phase phi, then ny entries for y, then nz for z; tab32 the same in FP32.
 cudaError_t launch_forcing_tables(int kx, int ky, int kz, double phi, int nx, int ny, int nz,
-                                  double2 *tab, cudaStream_t stream, int *launches);
+                                  double2 *tab, float2 *tab32, cudaStream_t stream,
+                                  int *launches);
 
 cudaError_t launch_scatter(const void *src, int src_fp64, void *dst, const Layout &L, int nf,
                            cudaStream_t stream, int *launches);

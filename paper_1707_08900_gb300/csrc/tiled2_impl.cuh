@@ -149,9 +149,10 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     float2 fxy0 = make_float2(0.f, 0.f), fxy1 = make_float2(0.f, 0.f);
     if constexpr (FORCE) {
         if (valid0) {
-            const double2 a0 = __ldg(fo->tx + x), a1 = __ldg(fo->tx + x + 1), b = __ldg(fo->ty + y);
-            fxy0 = make_float2((float)(a0.x * b.x - a0.y * b.y), (float)(a0.x * b.y + a0.y * b.x));
-            fxy1 = make_float2((float)(a1.x * b.x - a1.y * b.y), (float)(a1.x * b.y + a1.y * b.x));
+            const float2 a0 = __ldg(fo->tx32 + x), a1 = __ldg(fo->tx32 + x + 1);
+            const float2 b = __ldg(fo->ty32 + y);
+            fxy0 = make_float2(a0.x * b.x - a0.y * b.y, a0.x * b.y + a0.y * b.x);
+            fxy1 = make_float2(a1.x * b.x - a1.y * b.y, a1.x * b.y + a1.y * b.x);
         }
     }
 
@@ -562,12 +563,12 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                     }
                     if constexpr (FORCE) {
                         // f_i = amp_i cos(k.x + phi)
-                        const double2 cz = __ldg(fo->tz + zo);
-                        const float czr = (float)cz.x, czi = (float)cz.y;
+                        const float2 cz = __ldg(fo->tz32 + zo);
+                        const float czr = cz.x, czi = cz.y;
                         const V fc = P::mk(fxy0.x * czr - fxy0.y * czi, fxy1.x * czr - fxy1.y * czi);
     #pragma unroll
                         for (int a = 0; a < 3; ++a)
-                            acc[1 + a] = P::fma(P::bc((float)fo->amp[a]), fc, acc[1 + a]);
+                            acc[1 + a] = P::fma(P::bc(fo->amp32[a]), fc, acc[1 + a]);
                     }
     #pragma unroll
                     for (int f = 0; f < NF; ++f) {
