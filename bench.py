@@ -328,6 +328,17 @@ def run_ours(args):
             "forcing": "k from 1 <= |k| <= 2 (k_f 1.53), f0 0.02, nu 1.4e-4, new k/phi/e per step"}
         s.close()
 
+    # ---- radial explosion (Sect. 6, Eq. 19): seven-axis asymmetry at t = 0.5,
+    # nu = 1e-3 (Re = u_ampl d_shell / nu = 200), both stencil forms
+    from paper_1707_08900_gb300 import explosion
+    for form_e in ("55p", "19p"):
+        ex = explosion.run(n=SHAPE[0], nu=1e-3, t_end=0.5, precision="fp32", form=form_e,
+                           samples=1)
+        extra[f"explosion_{form_e}"] = {"Re": ex["Re"], "t": ex["history"][-1]["t"],
+                                        "steps": ex["steps"],
+                                        "delta_sum_rho": ex["history"][-1]["delta_rho"],
+                                        "delta_sum_u": ex["history"][-1]["delta_u"]}
+
     # ---- precision form: FP32 stencil, FP64 RK3 registers
     kacc = max(3, args.steps // 4)
     s = make("fp32_acc64", "55p")

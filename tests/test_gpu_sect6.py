@@ -1,7 +1,7 @@
-"""GPU parity of the forced steps (Sect. 6, Eqs. 20-21) against the FP64
-oracle, through the C ABI.  Bars as in the unforced parity tests: FP64
-relative L2 <= 1e-12 per field; FP32 forms <= 1e-5 per step from the
-FP32-rounded state."""
+"""GPU tests of the paper's physics test cases (Sect. 6) through the C ABI:
+the forced steps (Eqs. 20-21) and the radial explosion (Eq. 19) against the
+FP64 oracle.  Bars as in the unforced parity tests: FP64 relative L2 <= 1e-12
+per field; FP32 forms <= 1e-5 per step from the FP32-rounded state."""
 import numpy as np
 import pytest
 
@@ -107,3 +107,32 @@ def test_zero_amplitude_is_the_unforced_step_and_bad_args():
         a.rk3_step_forced(-0.01, 0.1, ks, phis, es)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,form", [("fp64", "55p"), ("fp64", "19p"), ("fp32", "55p")])
+def test_explosion_on_the_gpu(precision, form):
+    """The explosion test (Sect. 6, Eq. 19): the GPU run matches the oracle
+    and keeps the x/y/z and the diagonal integrals equal among themselves."""
+    from paper_1707_08900_gb300 import explosion, gbfd
+    n = 32
+    g = fd.Grid(n, n, n)
+    ph = fd.Physics(cs=1.0, nu=5e-3, entropy_mode=1)
+    st = inputs.explosion((n, n, n))
+    if precision != "fp64":
+        st = st.astype(np.float32).astype(np.float64)
+    dt = fd.cfl_dt(st, g, ph, 0.4)
+    frm = fd.FORM_55P if form == "55p" else fd.FORM_19P
+    ref = fd.rk3_step(st, dt, g, ph, form=frm, nsteps=12)
+    s = gbfd.Solver((n, n, n), precision=precision, form=form, nu=5e-3)
+    s.set_state(st)
+    s.rk3_step(dt, 12)
+    got = s.get_state()
+    s.close()
+    tol = FP64_TOL if precision == "fp64" else 12 * FP32_TOL
+    assert np.all(_rel(got, ref)[:4] <= tol)
+    sym = 1e-12 if precision == "fp64" else 1e-5
+    for v in explosion.axis_integrals(got):
+        scale = np.abs(v).max()
+        assert np.ptp(v[:3]) <= sym * scale and np.ptp(v[3:]) <= sym * scale, v
+    np.testing.assert_allclose(explosion.asymmetry(got), explosion.asymmetry(ref),
+                               rtol=1e-3 if precision == "fp32" else 1e-9)
