@@ -382,3 +382,30 @@ def test_integer_conversions_match_hardware_bitwise(precision, form):
             outs.append(s.get_state(fp64=False).view(np.uint32))
             s.close()
         assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_acc64", "fp32_acc64_w64"])
+def test_config3_window_against_oracle(precision):
+    """512^3 precision-study workload (k^-5/3 over 1 <= k <= 16, Mach 0.3,
+    lnrho 1e-2, seed 2): one GPU step checked against the FP64 oracle on two
+    64^3 windows (plus the 9-cell halo the three substeps need)."""
+    n, m, h = 512, 64, 9
+    shape = (n, n, n)
+    st = inputs.spectrum(shape, 2, p=-5.0 / 3.0, k1=1, k2=16, mach=0.3, lnrho_rms=1e-2)
+    if precision != "fp64":
+        st = st.astype(np.float32).astype(np.float64)
+    s = _solver(shape, precision=precision, nu=5e-3)
+    s.set_state(st)
+    dt = s.cfl_dt(0.4)
+    s.rk3_step(dt, 1)
+    got = s.get_state()
+    s.close()
+    hh = 2 * np.pi / n
+    for lo in ((0, 0, 0), (n // 2 - 5, n - 20, 7)):
+        win = _window(st, [l - h for l in lo], m + 2 * h)
+        g = fd.Grid(m + 2 * h, m + 2 * h, m + 2 * h, *(hh * (m + 2 * h),) * 3)
+        ref = fd.rk3_step(win, dt, g, fd.Physics(cs=1.0, nu=5e-3, entropy_mode=1))
+        ref = ref[:, h:h + m, h:h + m, h:h + m]
+        err = rel_l2(_window(got, lo, m), ref)
+        tol = FP64_TOL if precision == "fp64" else FP32_TOL
+        assert np.all(err <= tol), (lo, err)
