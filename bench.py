@@ -286,7 +286,21 @@ def run_ours(args):
                      "flops_per_update": 3 * FLOPS_55_SUBSTEP},
         "hbm_frac": round(npts * ALG_BYTES_55[8] / (ms64 / k64 * 1e-3) / 1e9 / peak_gbs, 4),
     }
+    # error of the FP32 forms against this FP64 run: same initial state, same steps
+    ref64 = s.get_state()
     s.close()
+    nerr = 2 + k64
+    errs = {}
+    for prec in ("fp32", "fp32_acc64"):
+        s2 = make(prec, "55p")
+        s2.rk3_step(dt, nerr)
+        x = s2.get_state()
+        s2.close()
+        errs[prec] = [float(np.linalg.norm((x[f] - ref64[f]).ravel())
+                            / np.linalg.norm(ref64[f].ravel())) for f in range(4)]
+    del ref64
+    extra["error_vs_fp64"] = {"steps": nerr, "grid": "256^3",
+                              "rel_l2_lnrho_ux_uy_uz": errs}
     extra["fp32_vs_fp64_speedup"] = round(value / world / v64, 2)
 
     # ---- FP32, 19-point two-pass form
