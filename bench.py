@@ -259,12 +259,12 @@ def run_ours(args):
     avg_launch_s = ms * 1e-3 / launches
     alg_per_launch = npts * ALG_BYTES_55[4] / 3.0
     achieved = alg_per_launch / avg_launch_s / 1e9
-    traffic = profile_traffic("substep55_fp32_packed_256")
+    traffic = profile_traffic("substep55_fp32_lag_tmem_256")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs, "unit": "GB/s",
                 "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": "k_substep_px2<float,5,55p,32x8,packed,U=2> (3 launches per step)",
+                "kernel": "k_substep_lag<float,5,55p,32x8,packed,U=2,TMEM> (3 launches per step)",
                 "alg_bytes_per_launch": alg_per_launch,
                 "frac_of_8TBs_nominal": round(achieved / 8000.0, 4)}
     s.close()
@@ -476,7 +476,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": "256^3", "form": "55-point fused",
-                   "precision": "fp32", "fields": NF, "tile": "default (32x8, two points per thread, packed FP32x2, zc 32)",
+                   "precision": "fp32", "fields": NF, "tile": "default (32x8, two points per thread, packed FP32x2, output lagged 3 planes with pending RHS in TMEM, zc 32)",
                    "l2": "inputs larger than L2: 3 x 335 MB padded FP32 state buffers",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,

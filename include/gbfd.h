@@ -120,7 +120,9 @@ gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, in
  * destination is complete when the call returns (the stream is
  * synchronised); pinned host memory is written in place by the copy kernel,
  * pageable memory through the workspace.  A device destination is written
- * asynchronously. */
+ * asynchronously.  Errors: INVALID_ARG (dst NULL), CUDA; with a host
+ * destination also TIMEOUT, as gbfd_sync reports it (the state copied out is
+ * then not to be trusted). */
 gbfd_status gbfd_get_state(gbfd_ctx *ctx, void *dst, int dst_on_device, int dst_is_fp64);
 
 /* Advance `nsteps` >= 0 full RK3 steps of length dt (> 0, finite): three

@@ -17,16 +17,19 @@ struct TileConfig {
     int pk;      // 0: scalar arithmetic; n > 0: packed FP32x2 arithmetic with
                  // n output planes per loop iteration
     int tm;      // 1: in-plane work at plane arrival, results carried through TMEM
+    int lag;     // 1: output planes finished three planes behind the in-plane work
 };
 
 // Number of z-chunk lengths offered per (tx, ty, ns) variant; table index
 // i is variant i / kZcChoices with the (i % kZcChoices)-th chunk length.
 constexpr int kZcChoices = 4;
 
-// Default FP32 table entry: variant 8 (32 x 8, two points per thread,
-// packed FP32x2 arithmetic, z-paired mixed terms accumulated forward, two
-// output planes per loop iteration) with the first z-chunk length.
-constexpr int kDefaultF32 = 8 * kZcChoices;
+// Default FP32 table entry: variant 19 (32 x 8, two points per thread,
+// packed FP32x2 arithmetic, each plane's x/y arm differences feeding the
+// z-paired mixed terms of the planes around it, output planes finished three
+// planes behind the in-plane work with their pending right-hand sides in
+// TMEM, two steps per loop iteration) with the first z-chunk length.
+constexpr int kDefaultF32 = 19 * kZcChoices;
 
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);

@@ -1,12 +1,16 @@
 // Tiled substep instantiations with FP32 storage and FP32 arithmetic: the
 // one-point-per-thread kernel (variants 0-3), the paired-load
 // two-points-per-thread kernel (variants 4-6) and the same with the two
-// points' arithmetic in packed FP32x2 instructions (variants 7-10: one, two
-// or three output planes per loop iteration; variant 10 with a five-slot
-// ring and registers capped for three CTAs per SM) and, for the 55-point
-// form, the kernel that does the in-plane work at plane arrival and carries
-// its results through TMEM (variants 11-12).
+// points' arithmetic in packed FP32x2 instructions (variants 7-10 and 13-16:
+// one, two or three output planes per loop iteration, ring lengths,
+// u-tilde from global memory, larger tiles) and, for the 55-point form, the
+// kernel that does the in-plane work at plane arrival and carries its
+// results through TMEM (variants 11-12) and the kernel that finishes output
+// planes three planes behind the in-plane work (variants 17-19: two or one
+// steps per iteration, pending right-hand sides in registers or, 19, the
+// default, in TMEM).
 #include "tiled3_impl.cuh"
+#include "tiled4_impl.cuh"
 
 namespace gbfd {
 
@@ -16,7 +20,8 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
                                  cudaStream_t stream, int *launches)
 {
     // default: two points per thread in packed arithmetic, 32 x 8 tile,
-    // z-chunk 32 (fastest at 256^3 and 512^3 on GB300 in the tile sweep)
+    // lagged output with TMEM, z-chunk 32 (fastest at 256^3 and 512^3 on
+    // GB300 in the tile sweep)
     const int idx = cfg < 0 ? kDefaultF32 : cfg;
     const TileConfig t = tiled_config(4, idx);
     // a forced step (Sect. 6 forcing) runs on the default kernel, whatever
@@ -88,6 +93,25 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     case 16:
         e = launch_px2_cfg<TS, TW, TA, 64, 8, 8, true, 2>(b, c, st, nf, form, t.zc, v, dev_error,
                                                           cache, stream, launches);
+        break;
+    case 17:
+    case 18:
+    case 19:
+        // output planes finished three planes behind the in-plane work
+        // (55-point form; the 19-point form runs the two-plane packed kernel,
+        // forcing included, as variant 8 does)
+        if (form != 0)
+            e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2, 1, false, false, true>(
+                b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
+        else if (v == 17)
+            e = launch_lag_cfg<TW, TA, 32, 8, 8, 2>(b, c, st, nf, t.zc, v, dev_error, cache,
+                                                     stream, launches);
+        else if (v == 19)
+            e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, true>(b, c, st, nf, t.zc, v, dev_error, cache,
+                                                           stream, launches);
+        else
+            e = launch_lag_cfg<TW, TA, 32, 8, 8, 1>(b, c, st, nf, t.zc, v, dev_error, cache,
+                                                     stream, launches);
         break;
     default:  // 11, 12
         // in-plane work at arrival, carried through TMEM (55-point form; the

@@ -22,16 +22,25 @@ def _gpu():
     build.build()
 
 
-def test_bounded_wait_times_out_and_context_recovers():
+@pytest.mark.parametrize("cfg,report", [(-1, "sync"), (-1, "get_state"), (68, "sync"),
+                                        (76, "get_state")])
+def test_bounded_wait_times_out_and_context_recovers(cfg, report):
+    """The default kernel and the lagged-output kernels (registers, tensor
+    memory); the timeout is reported by gbfd_sync or by gbfd_get_state to
+    host memory, which waits for the stream too."""
     from paper_1707_08900_gb300 import gbfd
     shape = (16, 16, 32)
     st = inputs.spectrum(shape, 12, mach=0.1, lnrho_rms=1e-3).astype(np.float32)
     s = gbfd.Solver(shape, precision="fp32", nu=5e-3)
+    s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
     s.set_state(st)
     s.set_option(gbfd.GBFD_OPT_FAULT_SKIP_COPY, 8)
     s.substep(0, 0.01)
     with pytest.raises(gbfd.GbfdError) as err:
-        s.sync()
+        if report == "sync":
+            s.sync()
+        else:
+            s.get_state()
     assert err.value.status == 4  # GBFD_ERR_TIMEOUT
     s.set_option(gbfd.GBFD_OPT_FAULT_SKIP_COPY, -1)
     s.sync()  # the error word was cleared

@@ -171,14 +171,19 @@ def test_diagnostics_match_oracle():
     s.close()
 
 
-def test_roll_equivariance_bitwise_fp32():
+@pytest.mark.parametrize("cfg", [-1, 32, 68, 73, 76])
+def test_roll_equivariance_bitwise_fp32(cfg):
     """Rolling the input rolls the output bit for bit: every point runs the
-    same arithmetic whatever tile, chunk or periodic edge it falls in."""
+    same arithmetic whatever tile, chunk or periodic edge it falls in (the
+    default kernel, the two-plane packed kernel, and the lagged-output kernel
+    with two and one steps per iteration)."""
+    from paper_1707_08900_gb300 import gbfd
     shape = (40, 48, 64)
     st = inputs.spectrum(shape, 8, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
     outs = []
     for roll in ((0, 0, 0), (5, -9, 13)):
         s = _solver(shape, precision="fp32", nu=5e-3)
+        s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
         s.set_state(np.roll(st, roll, axis=(1, 2, 3)))
         s.rk3_step(0.01, 2)
         outs.append(np.roll(s.get_state(fp64=False), [-r for r in roll], axis=(1, 2, 3)))
@@ -216,6 +221,34 @@ def test_every_tile_config_matches_oracle(precision):
         assert np.all(err <= tol), (cfg, err)
         n += 1
     assert n >= {"fp64": 8, "fp32": 68}.get(precision, 8)
+
+
+@pytest.mark.parametrize("shape", [(21, 20, 24), (17, 12, 16), (9, 16, 32)])
+def test_lagged_output_kernel_on_ragged_chunks(shape):
+    """The kernel that finishes output planes three planes behind the
+    in-plane work (table variants 17 and 18: two and one steps per loop
+    iteration; 19: pending right-hand sides in tensor memory) on z-chunks of odd length and of length 1, where its epilogue
+    steps (the halo planes above the chunk) fall on either step of an
+    iteration; both entropy modes."""
+    from paper_1707_08900_gb300 import gbfd
+    g = _grid(shape)
+    for em in (1, 0):
+        ph = fd.Physics(cs=1.0, nu=0.01, entropy_mode=em)
+        st = inputs.spectrum(shape, 5, mach=0.2, lnrho_rms=1e-2).astype(np.float32).astype(np.float64)
+        if em == 0:
+            st = np.ascontiguousarray(st[:4])
+        dt = fd.cfl_dt(st, g, ph, 0.4)
+        ref = fd.rk3_step(st, dt, g, ph)
+        for v in (17, 18, 19):
+            for zi in range(4):
+                s = _solver(shape, precision="fp32", nu=0.01, entropy_mode=em)
+                s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, 4 * v + zi)
+                s.set_state(st)
+                s.rk3_step(dt, 1)
+                got = s.get_state()
+                s.close()
+                err = rel_l2(got, ref)
+                assert np.all(err <= FP32_TOL), (v, zi, em, err)
 
 
 def test_every_tile_config_agrees():
