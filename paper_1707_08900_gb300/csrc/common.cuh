@@ -127,6 +127,36 @@ inline Coef<T> make_coef(double hx, double hy, double hz, double cs, double nu)
     return c;
 }
 
+// True when the weights are the same on every axis (equal grid spacing);
+// cubic_of then carries exactly the same values in the isotropic form.
+template <class T>
+inline bool coef_is_cubic(const Coef<T> &c)
+{
+    bool iso = c.d2c[1] == c.d2c[0] && c.d2c[2] == c.d2c[0];
+    for (int k = 0; k < 3; ++k)
+        iso = iso && c.d1[1][k] == c.d1[0][k] && c.d1[2][k] == c.d1[0][k] &&
+              c.d2[1][k] == c.d2[0][k] && c.d2[2][k] == c.d2[0][k] &&
+              c.mx[1][k] == c.mx[0][k] && c.mx[2][k] == c.mx[0][k];
+    return iso;
+}
+
+template <class T>
+inline CubicCoef<T> cubic_of(const Coef<T> &c)
+{
+    CubicCoef<T> q;
+    for (int k = 0; k < 3; ++k) {
+        q.d1[k] = c.d1[0][k];
+        q.d2[k] = c.d2[0][k];
+        q.mx[k] = c.mx[0][k];
+    }
+    q.d2c = c.d2c[0];
+    q.cs2 = c.cs2;
+    q.nu = c.nu;
+    q.nu3 = c.nu3;
+    q.nu23 = c.nu23;
+    return q;
+}
+
 template <class T>
 inline CubicCoef<T> make_cubic_coef(double h, double cs, double nu)
 {

@@ -909,11 +909,11 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 
 // Single box: one CTA per (tile, z-chunk).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK, int U,
-          int MINB, bool WG, bool ICVT, bool FORCE>
+          int MINB, bool WG, bool ICVT, bool FORCE, class CoefT = Coef<TS>>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
-    const Layout Lw, const Coef<TS> c, const RKStage st, const int zc, const int tiles_x,
+    const Layout Lw, const CoefT c, const RKStage st, const int zc, const int tiles_x,
     int *__restrict__ dev_error, const int skip_plane)
 {
     using RG = Ring<TS, TW, NF, TX, TY, NS, WG ? 0 : U + 2>;
@@ -933,8 +933,12 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
 
 }  // namespace tiled2
 
+// ISO_OK (bit 0: 19-point form, bit 1: 55-point form): with equal spacing on
+// every axis, launch the instantiation that takes the isotropic weights
+// (CubicCoef: 10 stencil weights instead of 30).
 template <class TS, class TW, class TA, int TX, int TY, int NS, bool PK = false, int U = 1,
-          int MINB = 1, bool WG = false, bool ICVT = false, bool FORCE_OK = false>
+          int MINB = 1, bool WG = false, bool ICVT = false, bool FORCE_OK = false,
+          int ISO_OK = 0>
 cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,
                            int form, int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
@@ -956,16 +960,28 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
     // a forced step needs the forcing instantiation (FORCE_OK variants only)
     if (st.fo.on && !FORCE_OK)
         return cudaErrorNotSupported;
-#define GBFD_LAUNCH2_K(NFV, MIX, FRC)                                                             \
+    const bool iso = ISO_OK != 0 && coef_is_cubic(c);
+    const CubicCoef<TS> cc = cubic_of(c);
+#define GBFD_LAUNCH2_KC(NFV, MIX, FRC, CT, CV)                                                    \
     do {                                                                                          \
-        auto kern =                                                                               \
-            tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB, WG, ICVT, FRC>;  \
+        auto kern = tiled2::k_substep_px2<TS, TW, TA, NFV, MIX, TX, TY, NS, PK, U, MINB, WG,     \
+                                          ICVT, FRC, CT>;                                         \
         constexpr int sm = tiled2::Ring<TS, TW, NFV, TX, TY, NS, WG ? 0 : U + 2>::BYTES;          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \
-        kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, divf, b.Ls, b.Lw, c, st, zc,       \
+        kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, divf, b.Ls, b.Lw, CV, st, zc,      \
                                           tiles_x, dev_error, skip_plane);                        \
+    } while (0)
+#define GBFD_LAUNCH2_K(NFV, MIX, FRC)                                                             \
+    do {                                                                                          \
+        if constexpr ((ISO_OK & ((MIX) ? 2 : 1)) != 0) {                                          \
+            if (iso) {                                                                            \
+                GBFD_LAUNCH2_KC(NFV, MIX, FRC, CubicCoef<TS>, cc);                                \
+                break;                                                                            \
+            }                                                                                     \
+        }                                                                                         \
+        GBFD_LAUNCH2_KC(NFV, MIX, FRC, Coef<TS>, c);                                              \
     } while (0)
 #define GBFD_LAUNCH2(NFV, MIX)                                                                    \
     do {                                                                                          \
@@ -990,6 +1006,7 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
     }
 #undef GBFD_LAUNCH2
 #undef GBFD_LAUNCH2_K
+#undef GBFD_LAUNCH2_KC
     *launches += 1;
     return cudaGetLastError();
 }

@@ -631,12 +631,15 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 }
 
 // Single box: one CTA per (tile, z-chunk).
+// CoefT: Coef<float>, or CubicCoef<float> when the grid spacing is the same on
+// every axis (10 stencil weights instead of 30, few enough to stay in uniform
+// registers).
 template <class TW, class TA, int NF, int TX, int TY, int NS, int U, int MINB, bool ICVT,
-          bool FORCE, bool TM>
+          bool FORCE, bool TM, class CoefT>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     float *__restrict__ out, TW *__restrict__ w, const Layout Ls, const Layout Lw,
-    const Coef<float> c, const RKStage st, const int zc, const int tiles_x,
+    const CoefT c, const RKStage st, const int zc, const int tiles_x,
     int *__restrict__ dev_error, const int skip_plane)
 {
     using RG = RingL<TW, NF, TX, TY, NS, U>;
@@ -693,15 +696,28 @@ cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKSta
     float *out = (float *)b.out;
     TW *w = (TW *)b.w;
     cudaError_t e;
-#define GBFD_LAUNCH_LAG(NFV, FRC)                                                                 \
+    // equal spacing on every axis: the isotropic weights (same values)
+    const bool iso = TM && coef_is_cubic(c);
+    const CubicCoef<float> cc = cubic_of(c);
+#define GBFD_LAUNCH_LAG_C(NFV, FRC, CT, CV)                                                       \
     do {                                                                                          \
-        auto kern = tiled4::k_substep_lag<TW, TA, NFV, TX, TY, NS, U, MINB, ICVT, FRC, TM>;       \
+        auto kern = tiled4::k_substep_lag<TW, TA, NFV, TX, TY, NS, U, MINB, ICVT, FRC, TM, CT>;   \
         constexpr int sm = tiled4::RingL<TW, NFV, TX, TY, NS, U>::BYTES;                          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
             return e;                                                                             \
-        kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, b.Ls, b.Lw, c, st, zc, tiles_x,    \
+        kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, b.Ls, b.Lw, CV, st, zc, tiles_x,   \
                                           dev_error, skip_plane);                                 \
+    } while (0)
+#define GBFD_LAUNCH_LAG(NFV, FRC)                                                                 \
+    do {                                                                                          \
+        if constexpr (TM) {                                                                       \
+            if (iso) {                                                                            \
+                GBFD_LAUNCH_LAG_C(NFV, FRC, CubicCoef<float>, cc);                                \
+                break;                                                                            \
+            }                                                                                     \
+        }                                                                                         \
+        GBFD_LAUNCH_LAG_C(NFV, FRC, Coef<float>, c);                                              \
     } while (0)
     if (nf == 5) {
         if (st.fo.on)
@@ -715,6 +731,7 @@ cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKSta
             GBFD_LAUNCH_LAG(4, false);
     }
 #undef GBFD_LAUNCH_LAG
+#undef GBFD_LAUNCH_LAG_C
     *launches += 1;
     return cudaGetLastError();
 }

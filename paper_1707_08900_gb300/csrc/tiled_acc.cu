@@ -23,7 +23,7 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     if (st.fo.on && v == 2)
         v = 0;  // forced steps: the packed kernel with the forcing instantiation
     if (v == 0)
-        e = launch_px2_cfg<TS, TW, TA, 32, 8, NSP, true, 2, 1, false, true, true>(
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, NSP, true, 2, 1, false, true, true, 2>(
             b, c, st, nf, form, t.zc, 0, dev_error, cache, stream, launches);
     else if (v == 1)
         e = launch_tiled_cfg<TS, TW, TA, 32, 8, 9>(b, c, st, nf, form, t.zc, 1, dev_error, cache,

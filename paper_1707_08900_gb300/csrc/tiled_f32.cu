@@ -101,7 +101,7 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         // (55-point form; the 19-point form runs the two-plane packed kernel,
         // forcing included, as variant 8 does)
         if (form != 0)
-            e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2, 1, false, false, true>(
+            e = launch_px2_cfg<TS, TW, TA, 32, 8, 8, true, 2, 1, false, false, true, 1>(
                 b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
         else if (v == 17)
             e = launch_lag_cfg<TW, TA, 32, 8, 8, 2>(b, c, st, nf, t.zc, v, dev_error, cache,

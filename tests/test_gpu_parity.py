@@ -171,18 +171,21 @@ def test_diagnostics_match_oracle():
     s.close()
 
 
-@pytest.mark.parametrize("cfg", [-1, 32, 68, 73, 76])
-def test_roll_equivariance_bitwise_fp32(cfg):
+@pytest.mark.parametrize("cfg,iso", [(-1, False), (-1, True), (32, False), (68, False),
+                                     (73, False), (76, False), (76, True)])
+def test_roll_equivariance_bitwise_fp32(cfg, iso):
     """Rolling the input rolls the output bit for bit: every point runs the
     same arithmetic whatever tile, chunk or periodic edge it falls in (the
     default kernel, the two-plane packed kernel, and the lagged-output kernel
-    with two and one steps per iteration)."""
+    with two and one steps per iteration; `iso`: equal spacing on every axis,
+    where the default kernel runs with the isotropic stencil weights)."""
     from paper_1707_08900_gb300 import gbfd
     shape = (40, 48, 64)
+    lengths = (64 * 0.1, 48 * 0.1, 40 * 0.1) if iso else (2 * np.pi,) * 3
     st = inputs.spectrum(shape, 8, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
     outs = []
     for roll in ((0, 0, 0), (5, -9, 13)):
-        s = _solver(shape, precision="fp32", nu=5e-3)
+        s = _solver(shape, precision="fp32", nu=5e-3, lengths=lengths)
         s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
         s.set_state(np.roll(st, roll, axis=(1, 2, 3)))
         s.rk3_step(0.01, 2)
@@ -223,15 +226,20 @@ def test_every_tile_config_matches_oracle(precision):
     assert n >= {"fp64": 8, "fp32": 68}.get(precision, 8)
 
 
+@pytest.mark.parametrize("iso", [False, True])
 @pytest.mark.parametrize("shape", [(21, 20, 24), (17, 12, 16), (9, 16, 32)])
-def test_lagged_output_kernel_on_ragged_chunks(shape):
+def test_lagged_output_kernel_on_ragged_chunks(shape, iso):
     """The kernel that finishes output planes three planes behind the
     in-plane work (table variants 17 and 18: two and one steps per loop
-    iteration; 19: pending right-hand sides in tensor memory) on z-chunks of odd length and of length 1, where its epilogue
-    steps (the halo planes above the chunk) fall on either step of an
-    iteration; both entropy modes."""
+    iteration; 19: pending right-hand sides in tensor memory) on z-chunks of
+    odd length and of length 1, where its epilogue steps (the halo planes
+    above the chunk) fall on either step of an iteration; both entropy
+    modes; unequal spacings, and equal ones (`iso`), where variant 19 runs
+    with the isotropic stencil weights."""
     from paper_1707_08900_gb300 import gbfd
-    g = _grid(shape)
+    nz, ny, nx = shape
+    lengths = (nx * 0.2, ny * 0.2, nz * 0.2) if iso else (2 * np.pi,) * 3
+    g = _grid(shape, lengths)
     for em in (1, 0):
         ph = fd.Physics(cs=1.0, nu=0.01, entropy_mode=em)
         st = inputs.spectrum(shape, 5, mach=0.2, lnrho_rms=1e-2).astype(np.float32).astype(np.float64)
@@ -241,7 +249,7 @@ def test_lagged_output_kernel_on_ragged_chunks(shape):
         ref = fd.rk3_step(st, dt, g, ph)
         for v in (17, 18, 19):
             for zi in range(4):
-                s = _solver(shape, precision="fp32", nu=0.01, entropy_mode=em)
+                s = _solver(shape, precision="fp32", nu=0.01, entropy_mode=em, lengths=lengths)
                 s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, 4 * v + zi)
                 s.set_state(st)
                 s.rk3_step(dt, 1)
