@@ -118,7 +118,7 @@ gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, in
 
 /* Copy the current state out, same layout as gbfd_set_state.  A host
  * destination is complete when the call returns (the stream is
- * synchronised); pinned host memory is written in place by the copy kernel,
+ * synchronised; unless GBFD_OPT_HOST_ASYNC is set); pinned host memory is written in place by the copy kernel,
  * pageable memory through the workspace.  A device destination is written
  * asynchronously.  Errors: INVALID_ARG (dst NULL), CUDA; with a host
  * destination also TIMEOUT, as gbfd_sync reports it (the state copied out is
@@ -198,11 +198,18 @@ enum {
     GBFD_OPT_KERNEL_PATH = 1,
     GBFD_OPT_TILE_CONFIG = 2,
     GBFD_OPT_FAULT_SKIP_COPY = 3,
-    GBFD_OPT_HOST_PATH = 4
+    GBFD_OPT_HOST_PATH = 4,
+    GBFD_OPT_HOST_ASYNC = 5
 };
 /* GBFD_OPT_HOST_PATH: 0 (default) = gbfd_set_state / gbfd_get_state access
  * pinned host buffers in place from the copy kernels; 1 = always copy host
  * buffers through the workspace with cudaMemcpyAsync. */
+/* GBFD_OPT_HOST_ASYNC: 0 (default) = gbfd_get_state to host memory returns
+ * with the copy complete; 1 = it only enqueues the copy on the context's
+ * stream (with pinned host memory it then overlaps other streams' work; with
+ * pageable memory the CUDA runtime may still wait).  The buffer is complete
+ * once the stream reaches that point (gbfd_sync, which also reports a device
+ * TIMEOUT, or any wait on the stream). */
 /* GBFD_OPT_FAULT_SKIP_COPY (tests only): value j >= 0 makes the first CTA of
  * the two-points-per-thread tiled kernel skip the TMA copy of its local plane
  * j, so its bounded mbarrier wait gives up after about 2 s, the launch ends

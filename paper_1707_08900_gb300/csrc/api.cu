@@ -40,6 +40,7 @@ struct gbfd_ctx {
     int tile_cfg;     // index into the tiled kernel's tile table (-1 = default)
     int fault_skip;   // test-only fault injection (-1 = off)
     int host_path;    // 0 = pinned host buffers accessed in place, 1 = always staged
+    int host_async;   // 1 = gbfd_get_state to host memory does not wait for the stream
     Forcing fo;       // forcing of the step being taken (fo.on = 0: none)
     double2 *ftab;    // its per-axis phase tables (workspace)
     TmapCache tmaps;  // encoded TMA descriptors of the two state buffers
@@ -387,6 +388,7 @@ gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_by
     c->tile_cfg = -1;
     c->fault_skip = -1;
     c->host_path = 0;
+    c->host_async = 0;
     memset(&c->tmaps, 0, sizeof c->tmaps);
     c->broken = false;
     const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
@@ -425,6 +427,11 @@ gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value)
         if (value != 0 && value != 1)
             break;
         ctx->host_path = (int)value;
+        return GBFD_OK;
+    case GBFD_OPT_HOST_ASYNC:
+        if (value != 0 && value != 1)
+            break;
+        ctx->host_async = (int)value;
         return GBFD_OK;
     case GBFD_OPT_FAULT_SKIP_COPY:
         if (value < -1 || value > 1000000)
@@ -499,6 +506,8 @@ gbfd_status gbfd_get_state(gbfd_ctx *ctx, void *dst, int dst_on_device, int dst_
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e, "get_state copy");
         }
+        if (ctx->host_async)
+            return GBFD_OK;  // complete once the stream reaches this point
         // the stream is waited for anyway: report a bounded wait that gave up
         // in the steps that produced this state, as gbfd_sync does
         return gbfd_sync(ctx);

@@ -21,6 +21,7 @@ STATUS = {0: "GBFD_OK", 1: "GBFD_ERR_INVALID_ARG", 2: "GBFD_ERR_WORKSPACE", 3: "
 GBFD_FP64, GBFD_FP32, GBFD_FP32_ACC64, GBFD_FP32_ACC64_W64 = 0, 1, 2, 3
 GBFD_55P, GBFD_19P = 0, 1
 GBFD_OPT_KERNEL_PATH, GBFD_OPT_TILE_CONFIG, GBFD_OPT_FAULT_SKIP_COPY, GBFD_OPT_HOST_PATH = 1, 2, 3, 4
+GBFD_OPT_HOST_ASYNC = 5
 
 PRECISIONS = {"fp64": GBFD_FP64, "fp32": GBFD_FP32, "fp32_acc64": GBFD_FP32_ACC64,
               "fp32_acc64_w64": GBFD_FP32_ACC64_W64}

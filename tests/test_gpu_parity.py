@@ -259,6 +259,62 @@ def test_lagged_output_kernel_on_ragged_chunks(shape, iso):
                 assert np.all(err <= FP32_TOL), (v, zi, em, err)
 
 
+@pytest.mark.parametrize("iso", [False, True])
+def test_lagged_kernel_tmem_and_isotropic_paths_are_bit_identical(iso):
+    """The lagged-output kernel keeps its pending right-hand sides in
+    registers (table 68) or in TMEM (table 76, which on equal spacings also
+    takes the isotropic weights): storage does not round and the weights
+    are the same values, so the two give the same bits."""
+    from paper_1707_08900_gb300 import gbfd
+    shape = (24, 40, 64)
+    lengths = (64 * 0.1, 40 * 0.1, 24 * 0.1) if iso else (2 * np.pi,) * 3
+    st = inputs.spectrum(shape, 14, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
+    outs = []
+    for cfg in (68, 76):
+        s = _solver(shape, precision="fp32", nu=5e-3, lengths=lengths)
+        s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
+        s.set_state(st)
+        s.rk3_step(0.005, 2)
+        outs.append(s.get_state(fp64=False))
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_pipelined_async_contexts_match_the_sequential_path():
+    """Several contexts on several streams taking independent steps in turn,
+    with staged copies and gbfd_get_state only enqueueing its copy
+    (GBFD_OPT_HOST_ASYNC), give the bits of the synchronous single-context
+    path once their streams are waited for."""
+    from paper_1707_08900_gb300 import gbfd
+    shape = (32, 24, 48)
+    st = inputs.spectrum(shape, 6, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
+    host_in = torch.from_numpy(st).pin_memory()
+    ref = _solver(shape, precision="fp32", nu=5e-3)
+    ref.set_state(host_in)
+    dt = ref.cfl_dt(0.4)
+    ref.rk3_step(dt, 1)
+    want = ref.get_state(fp64=False)
+    ref.close()
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    ctxs = []
+    for k in range(3):
+        s = gbfd.Solver(shape, precision="fp32", nu=5e-3, stream=streams[k])
+        s.set_option(gbfd.GBFD_OPT_HOST_PATH, 1)
+        s.set_option(gbfd.GBFD_OPT_HOST_ASYNC, 1)
+        ctxs.append(s)
+    outs = [torch.full_like(host_in, float("nan")).pin_memory() for _ in range(7)]
+    for i in range(7):
+        s = ctxs[i % 3]
+        s.set_state(host_in)
+        s.rk3_step(dt, 1)
+        s.get_state(out=outs[i])
+    for s in ctxs:
+        s.sync()
+        s.close()
+    for o in outs:
+        assert np.array_equal(o.numpy(), want)
+
+
 def test_every_tile_config_agrees():
     from paper_1707_08900_gb300 import gbfd
     from paper_1707_08900_gb300 import build  # noqa: F401
