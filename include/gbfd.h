@@ -211,10 +211,11 @@ enum {
  * once the stream reaches that point (gbfd_sync, which also reports a device
  * TIMEOUT, or any wait on the stream). */
 /* GBFD_OPT_FAULT_SKIP_COPY (tests only): value j >= 0 makes the first CTA of
- * the two-points-per-thread tiled kernel skip the TMA copy of its local plane
- * j, so its bounded mbarrier wait gives up after about 2 s, the launch ends
- * early and gbfd_sync reports GBFD_ERR_TIMEOUT with the context still
- * usable; -1 (the default) turns it off. */
+ * the two-points-per-thread tiled kernels skip the TMA copy of local plane j
+ * of its first column (a column has its output planes + 6 local planes), so
+ * its bounded mbarrier wait gives up after about 2 s, the launch ends early
+ * and gbfd_sync reports GBFD_ERR_TIMEOUT with the context still usable; -1
+ * (the default) turns it off. */
 gbfd_status gbfd_set_option(gbfd_ctx *ctx, int key, int64_t value);
 
 /* Tile autotuner (no counterpart in the paper; the paper tuned block shapes
