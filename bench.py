@@ -584,7 +584,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": "256^3", "form": "55-point fused",
-                   "precision": "fp32", "fields": NF, "tile": "default (32x8, two points per thread, packed FP32x2, output lagged 3 planes with pending RHS in TMEM, zc 32)",
+                   "precision": "fp32", "fields": NF, "tile": "default (32x8, two points per thread, packed FP32x2, output lagged 3 planes with pending RHS in TMEM, isotropic weights, z-chunks of 40 planes)",
                    "l2": "inputs larger than L2: 3 x 335 MB padded FP32 state buffers",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,

@@ -14,7 +14,9 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
                                  int form, int cfg, int *dev_error, TmapCache *cache,
                                  cudaStream_t stream, int *launches)
 {
-    const int idx = cfg < 0 ? 0 : cfg;
+    // default: the packed kernel with integer conversions, z-chunk 32 (its
+    // FP64 update binds; 40-plane chunks measured 3% slower here)
+    const int idx = cfg < 0 ? 1 : cfg;
     const TileConfig t = tiled_config(4, idx % kZcChoices);
     cudaError_t e;
     // FP64 u-tilde doubles its ring: a 6-slot state ring keeps two CTAs per SM

@@ -21,7 +21,7 @@ const TileConfig kVariants4[] = {{32, 8, 0, 9, 1},  {32, 4, 0, 9, 1},  {64, 4, 0
                                  {32, 8, 0, 8, 2, 2, 0, 1}, {32, 8, 0, 8, 2, 1, 0, 1},
                                  {32, 8, 0, 8, 2, 2, 1, 1}};
 const TileConfig kVariants8[] = {{32, 4, 0, 8, 1}, {16, 8, 0, 8, 1}};
-const int kZc[kZcChoices] = {32, 16, 64, 128};
+const int kZc[kZcChoices] = {40, 32, 64, 16};
 constexpr int kNz = kZcChoices;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()

@@ -20,8 +20,9 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
                                  cudaStream_t stream, int *launches)
 {
     // default: two points per thread in packed arithmetic, 32 x 8 tile,
-    // lagged output with TMEM, z-chunk 32 (fastest at 256^3 and 512^3 on
-    // GB300 in the tile sweep)
+    // lagged output with TMEM, z-chunk 40 (the best compromise between 256^3
+    // and 512^3 on GB300 in the chunk sweep: 7 chunks of a 256 column fill
+    // 5.9 launch waves of 2 x 152 CTAs, 8 chunks of 32 fill 6.7)
     const int idx = cfg < 0 ? kDefaultF32 : cfg;
     const TileConfig t = tiled_config(4, idx);
     // a forced step (Sect. 6 forcing) runs on the default kernel, whatever
