@@ -251,6 +251,32 @@ bool write_cache(const char *path, const std::map<std::string, std::pair<int, do
     return rename(tmp.c_str(), path) == 0;
 }
 
+// The FP32 default's z-chunk length for this grid (S = resident CTAs of the
+// default kernel: 32 x 8 tiles, two per SM): 40 planes when that still makes
+// at least four launch waves (fewest halo planes, and 7 chunks of a 256
+// column fill 5.9 waves where 8 chunks of 32 fill 6.7); else 32 when that
+// fills at least half a wave; else 16, so that small grids keep their SMs
+// busy.  Measured best at 64^3 (16), 128^3 (32), 256^3 and 512^3 (40).
+int fp32_default_cfg(const gbfd_ctx *c)
+{
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 152;
+    }
+    const long long slots = 2LL * sms;
+    const long long tiles = (long long)((c->p.nx + 31) / 32) * ((c->p.ny + 7) / 8);
+    // positions of 40, 32 and 16 in the tile table's chunk list
+    if (tiles * ((c->p.nz + 39) / 40) >= 4 * slots)
+        return kDefaultF32;
+    if (2 * tiles * ((c->p.nz + 31) / 32) >= slots)
+        return kDefaultF32 + 1;
+    return kDefaultF32 + 3;
+}
+
 gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
 {
     StateBufs b = bufs(c);
@@ -269,9 +295,10 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
                                                                   c->stream, &n);
         break;
     case GBFD_FP32:
-        e = tiled ? launch_substep_tiled<float, float, float>(b, c->c32, st, c->nf, c->p.form,
-                                                              c->tile_cfg, c->dev_error, &c->tmaps,
-                                                              c->stream, &n)
+        e = tiled ? launch_substep_tiled<float, float, float>(
+                        b, c->c32, st, c->nf, c->p.form,
+                        c->tile_cfg < 0 ? fp32_default_cfg(c) : c->tile_cfg, c->dev_error,
+                        &c->tmaps, c->stream, &n)
                   : launch_substep_simple<float, float, float>(b, c->c32, st, c->nf, c->p.form,
                                                                c->stream, &n);
         break;
