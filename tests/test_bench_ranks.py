@@ -50,3 +50,24 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.whole_job_rate(10, 2, 1000.0, 1) == pytest.approx(20.0)
+
+
+def test_committed_profile_matches_the_headline_kernel_sources():
+    """The ncu summary the bench reads its DRAM traffic from was taken on the
+    sources the headline kernel is compiled from now (their fingerprint: the
+    FP32 tiled translation unit, the tile table and every header they
+    include); a kernel change without a new capture fails here, as the
+    bench's traffic would otherwise silently turn null."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    kv = bench.profile_summary("substep55_fp32_lag_tmem_256")
+    assert kv is not None, "no committed profile for the current kernel sources"
+    traffic = bench.profile_traffic("substep55_fp32_lag_tmem_256")
+    gbs = bench.profile_dram_gbs("substep55_fp32_lag_tmem_256")
+    # DRAM bytes per launch at least the algorithmic bytes (10 F w / 3 per
+    # point at 256^3, F = 5, FP32), and an achieved rate below a few TB/s
+    alg = 256 ** 3 * 10 * 5 * 4 / 3.0
+    assert alg <= traffic < 1.5 * alg
+    assert 1000.0 < gbs < 8000.0
