@@ -71,9 +71,9 @@ def measured_peaks():
 
 
 def kernel_source_sha():
-    """Fingerprint of the sources the headline kernel is compiled from: the
-    FP32 tiled translation unit with every header it includes (followed
-    recursively), and the tile table."""
+    """Fingerprint of the code the headline kernel is compiled from (comments
+    and whitespace removed): the FP32 tiled translation unit with every
+    header it includes (followed recursively), and the tile table."""
     d = os.path.join(ROOT, "paper_1707_08900_gb300", "csrc")
     files = []
 
@@ -92,7 +92,11 @@ def kernel_source_sha():
     walk(os.path.join(d, "tiled_common.cu"))
     h = hashlib.sha256()
     for f in sorted(files):
-        h.update(open(f, "rb").read())
+        # the code only: comments and whitespace do not change a kernel
+        text = open(f).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

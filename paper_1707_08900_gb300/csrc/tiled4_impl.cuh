@@ -13,17 +13,19 @@
 // h_k and g_k of u_x, u_y, u_z on a plane are exactly the x and y arm
 // differences that plane's own first-derivative stencils form when it is the
 // centre plane.  So each plane is read from shared memory once: when it is
-// the centre, its arm differences go into running sums of the seven output
-// planes around it (plus to the planes above, minus to those below), and
-// output plane o is complete once plane o + 3 has been the centre.  Its
-// right-hand side without those terms waits three planes in registers, and
-// so does the state of its column (already held for the z stencils).  The
+// the centre, its arm differences go into running sums of the six output
+// planes around it (plus to the planes below it, for which it is z + k;
+// minus to those above, for which it is z - k), and output plane o is
+// complete once plane o + 3 has been the centre.  Its right-hand side without
+// those terms waits three planes, in registers or (TM, the default) in tensor
+// memory; the state of its column is already held for the z stencils.  The
 // three halo planes below and above a z-chunk are never centres: their arm
 // differences come from loads of their own.
 //
 // Per output plane and thread this reads 92 shared pairs (5 column values,
 // 50 x/y arms of the five fields, 32 for the two (x, y) cross terms, 5 of
-// u-tilde) where loading the arms of each arriving plane takes 116.
+// u-tilde; 96 with the halo planes of 40-plane chunks) where loading the
+// arms of each arriving plane takes 116.
 #pragma once
 
 #include "tcgen05.cuh"
