@@ -1,5 +1,5 @@
 // C-ABI entry points of libgbfd (declared in include/gbfd.h): parameter
-// validation, workspace carving, state copies, the RK3 driver loop of
+// validation, workspace carving, state copies, the RK3 step loop of
 // Algorithms 2 and 3, diagnostics.  No device memory is allocated here: all
 // buffers are carved from the caller's workspace.
 #include <cmath>

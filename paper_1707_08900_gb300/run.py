@@ -4,7 +4,7 @@
 
 Draws the k^-2 spectrum initial state (rms Mach 0.1, lnrho 1e-3, seed 1),
 takes dt from CFL 0.4 once, advances `steps` RK3 steps, synchronises and
-prints the diagnostics.  Used as the profiling driver for single kernels.
+prints the diagnostics.  Also the program profiled when a single kernel is captured.
 """
 import argparse
 import json
