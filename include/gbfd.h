@@ -179,15 +179,29 @@ gbfd_status gbfd_sync(gbfd_ctx *ctx);
  * framework whose allocator does not allow it).  It calls no allocating
  * routine: its partial sums live in a fixed file-scope device array of 1216 x
  * 16 doubles (155,648 bytes) that every GPU loading the library holds until
- * the process exits.  The array's device address is looked up on the first
- * call on each device (with that device current); make that first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU race and must be ordered (same stream, or events).
+ * the process exits.  Any grid size within the limits below fits in it (each
+ * block walks the grid rows in a grid-stride loop).  The array's device
+ * address is looked up on the first call on each device (with that device
+ * current), and again after that device's context was replaced (e.g. by
+ * cudaDeviceReset).  Make that first call before any stream capture, and
+ * where allocation is still allowed: with lazy module loading it is also the
+ * call that loads the library's device code, which may allocate device
+ * memory for the module; later calls allocate nothing.  All calls share the
+ * array: calls whose work overlaps on the GPU race and must be ordered (same
+ * stream, or events).
  * Limits: nfields 4 or 5; extents >= 1, nx*ny*nz <= 2^33; box lengths > 0.
  * Errors: INVALID_ARG (with gbfd_last_error(NULL)), CUDA. */
 gbfd_status gbfd_diagnostics_noalloc(const void *state, int state_is_fp64, int nx, int ny, int nz,
                                      int nfields, double lx, double ly, double lz, void *stream,
                                      double *out);
+
+/* Measured FP64 fused multiply-add rate of the current device, in TFLOP/s
+ * (an FMA counts 2): independent FMA chains on every SM, best of four timed
+ * launches on `stream` after two warm-ups (about 0.1 s in all; synchronises
+ * the stream).  It is the roofline denominator of the FP64 path, whose
+ * kernels the FP64 pipe bounds; no counterpart in the paper.  Errors:
+ * INVALID_ARG (NULL output), CUDA. */
+gbfd_status gbfd_fp64_fma_rate(void *stream, double *tflops);
 
 /* Tuning options (no counterpart in the paper; used by the tests and the
  * autotuner).  GBFD_OPT_KERNEL_PATH: 0 = tiled kernels (TMA-staged shared
@@ -348,6 +362,14 @@ gbfd_status gbfd_step_corrected(gbfd_ctx *ctx, gbfd_cnn *c, double dt, int nstep
 gbfd_status gbfd_box_filter(gbfd_ctx *fine, int r, float *out);
 int64_t gbfd_cnn_launch_count(const gbfd_cnn *c);
 const char *gbfd_cnn_last_error(const gbfd_cnn *c);
+/* Launch-shape options (tests; no counterpart in the paper).
+ * GBFD_CNN_OPT_CONV_GRID: CTAs per convolution launch, each walking an equal
+ * share of the 256-point tiles (0 = default, three per SM); a small value
+ * makes every CTA loop over many tiles.  GBFD_CNN_OPT_WGRAD_PARTS: CTAs of
+ * the weight-gradient sums, 1..296 (0 = default 296).  Results agree to
+ * rounding whatever the values; out-of-range values -> INVALID_ARG. */
+enum { GBFD_CNN_OPT_CONV_GRID = 1, GBFD_CNN_OPT_WGRAD_PARTS = 2 };
+gbfd_status gbfd_cnn_set_option(gbfd_cnn *c, int key, int64_t value);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,7 @@ struct gbfd_ctx {
     int64_t launches;
     int kernel_path;  // 0 = tiled when supported, 1 = simple
     int tile_cfg;     // index into the tiled kernel's tile table (-1 = default)
+    int sms;          // SM count of the context's device (read at init)
     int fault_skip;   // test-only fault injection (-1 = off)
     int host_path;    // 0 = pinned host buffers accessed in place, 1 = always staged
     int host_async;   // 1 = gbfd_get_state to host memory does not wait for the stream
@@ -259,15 +260,7 @@ bool write_cache(const char *path, const std::map<std::string, std::pair<int, do
 // busy.  Measured best at 64^3 (16), 128^3 (32), 256^3 and 512^3 (40).
 int fp32_default_cfg(const gbfd_ctx *c)
 {
-    static int sms = 0;
-    if (sms <= 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms <= 0)
-            sms = 152;
-    }
-    const long long slots = 2LL * sms;
+    const long long slots = 2LL * c->sms;
     const long long tiles = (long long)((c->p.nx + 31) / 32) * ((c->p.ny + 7) / 8);
     // positions of 40, 32 and 16 in the tile table's chunk list
     if (tiles * ((c->p.nz + 39) / 40) >= 4 * slots)
@@ -413,6 +406,17 @@ gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_by
     c->launches = 0;
     c->kernel_path = 0;
     c->tile_cfg = -1;
+    {
+        // the device current at init is the context's device
+        int dev = 0;
+        c->sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            c->sms <= 0) {
+            (void)cudaGetLastError();
+            c->sms = 152;
+        }
+    }
     c->fault_skip = -1;
     c->host_path = 0;
     c->host_async = 0;

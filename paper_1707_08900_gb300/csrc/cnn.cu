@@ -593,7 +593,8 @@ struct gbfd_cnn {
     double *lparts, *loss;
     int *derr;
     int adam_t;
-    int grid_conv;
+    int grid_conv;      // CTAs per convolution launch (each walks its share of the tiles)
+    int grid_default;   // three per SM
     int64_t launches;
     char err[512];
 };
@@ -867,7 +868,7 @@ gbfd_status gbfd_cnn_init(int n, int batch, void *workspace, size_t workspace_by
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    c->grid_conv = 3 * (sms > 0 ? sms : 1);
+    c->grid_conv = c->grid_default = 3 * (sms > 0 ? sms : 1);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->ws, 0, pl.total, c->stream);
     // identity normalisation until set
@@ -891,6 +892,28 @@ gbfd_status gbfd_cnn_destroy(gbfd_cnn *c)
 {
     delete c;
     return GBFD_OK;
+}
+
+gbfd_status gbfd_cnn_set_option(gbfd_cnn *c, int key, int64_t value)
+{
+    if (!c)
+        return GBFD_ERR_INVALID_ARG;
+    switch (key) {
+    case GBFD_CNN_OPT_CONV_GRID:
+        if (value < 0 || value > (1 << 20))
+            break;
+        c->grid_conv = value == 0 ? c->grid_default : (int)value;
+        return GBFD_OK;
+    case GBFD_CNN_OPT_WGRAD_PARTS:
+        if (value < 0 || value > kWgradParts)
+            break;
+        c->nparts = value == 0 ? kWgradParts : (int)value;
+        return GBFD_OK;
+    default:
+        break;
+    }
+    cerr(c, "cnn set_option: bad key %d or value %lld", key, (long long)value);
+    return GBFD_ERR_INVALID_ARG;
 }
 
 gbfd_status gbfd_cnn_set_params(gbfd_cnn *c, const float *params)

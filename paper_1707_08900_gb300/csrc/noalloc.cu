@@ -20,8 +20,14 @@
 //    reading them, so nothing has to be cleared, but calls whose work
 //    overlaps on the GPU (different streams without ordering) race on it;
 //  * the device address of the array is looked up once per device, on the
-//    first call made while that device is current; make that first call
-//    before any stream capture begins.
+//    first call made while that device is current (again if that device's
+//    context was replaced, e.g. after cudaDeviceReset, since the array then
+//    lives at a new address); make that first call before any stream
+//    capture begins, and where allocation is allowed: with lazy module
+//    loading it is also the call that loads this file's device code, and
+//    that load may allocate device memory for the module (later calls do
+//    not).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,8 +51,41 @@ static __device__ __align__(256) double g_scratch[kMaxBlocks * kQ];
 
 std::mutex g_mu;
 double *g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];  // context ID the address belongs to
 
-// Device address of g_scratch on the current device (looked up once).
+// Unique ID of the calling thread's current context (0 when it cannot be
+// read); IDs are never reused within a process, unlike context handles.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)p;
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx &&
+        get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+// Device address of g_scratch on the current device: looked up once per
+// device, and again when that device's context has changed.
 cudaError_t scratch_address(double **out)
 {
     int dev = 0;
@@ -56,12 +95,17 @@ cudaError_t scratch_address(double **out)
     if (dev < 0 || dev >= kMaxDevices)
         return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    // the runtime binds the device's primary context on first use; the
+    // symbol lookup below does that, so read the context ID after it when
+    // nothing is cached yet
+    const unsigned long long ctx = g_scratch_addr[dev] ? current_context_id() : 0;
+    if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess)
             return e;
         g_scratch_addr[dev] = static_cast<double *>(p);
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
@@ -182,15 +226,11 @@ extern "C" gbfd_status gbfd_diagnostics_noalloc(const void *state, int state_is_
     if (!(lx > 0) || !(ly > 0) || !(lz > 0) || !std::isfinite(lx) || !std::isfinite(ly) ||
         !std::isfinite(lz))
         return fail("diagnostics_noalloc: box lengths must be finite and > 0");
+    // one block per grid row up to the scratch's kMaxBlocks rows of partial
+    // sums; larger grids need no more scratch, since each block walks the
+    // rows in a grid-stride loop
     const long long rows = (long long)nz * ny;
     const int nblocks = (int)(rows < kMaxBlocks ? rows : kMaxBlocks);
-    if (nblocks > kMaxBlocks) {
-        char buf[160];
-        snprintf(buf, sizeof buf,
-                 "diagnostics_noalloc: %d partial blocks exceed the fixed scratch of %d", nblocks,
-                 kMaxBlocks);
-        return fail(buf);
-    }
     double *scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess) {

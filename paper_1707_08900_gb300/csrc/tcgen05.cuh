@@ -68,8 +68,12 @@ __device__ __forceinline__ void commit(uint64_t *bar)
 }
 
 // TMEM allocation by one whole warp; the address lands in *dst (shared).
+// The .sync.aligned tcgen05 instructions below must be reached by every
+// thread of the warp together; each helper reconverges the warp first (a
+// preceding bounded spin on an mbarrier can leave its lanes apart).
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
 {
+    __syncwarp();
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(dst)),
                  "r"(ncols)
@@ -79,6 +83,7 @@ __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
 
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
                  "r"(ncols)
                  : "memory");
@@ -106,6 +111,7 @@ __device__ __forceinline__ void fence_smem_to_async()
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *r)
 {
     uint32_t v[16];
+    __syncwarp();
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"

@@ -24,12 +24,21 @@ struct TileConfig {
 // i is variant i / kZcChoices with the (i % kZcChoices)-th chunk length.
 constexpr int kZcChoices = 4;
 
-// Default FP32 table entry: variant 19 (32 x 8, two points per thread,
-// packed FP32x2 arithmetic, each plane's x/y arm differences feeding the
-// z-paired mixed terms of the planes around it, output planes finished three
-// planes behind the in-plane work with their pending right-hand sides in
-// TMEM, two steps per loop iteration) with the first z-chunk length.
-constexpr int kDefaultF32 = 19 * kZcChoices;
+// FP32 tile table (55-point form; the 19-point form runs the two-plane
+// packed kernel for variants 1-4):
+//   0  one point per thread, 32 x 8
+//   1  two points per thread, packed FP32x2 arithmetic, two output planes
+//      per loop iteration, in-plane arms of the arriving plane
+//   2  output planes finished three planes behind the in-plane work, each
+//      plane's x/y arm differences feeding the z-paired mixed terms of the
+//      planes around it, pending right-hand sides in registers, two steps
+//      per iteration
+//   3  the same with one step per iteration
+//   4  the same as 2 with the pending right-hand sides in TMEM (default)
+//   5  the same as 4, shared loads free to move across the TMEM accesses
+constexpr int kVarPx1 = 0, kVarPacked = 1, kVarLagReg = 2, kVarLagReg1 = 3, kVarLagTm = 4,
+              kVarLagTmFree = 5;
+constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);

@@ -895,8 +895,10 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     if (bad && threadIdx.x == 0) {
         atomicExch(dev_error, 1);
         // drain the copies still in flight into this CTA's shared memory
+        // (the copy that fault injection skipped never lands: not waited for)
         for (int j = waited; j < issued; ++j)
-            (void)mbar_wait(&bars[(jrun + j) % NS], ((jrun + j) / NS) & 1);
+            if (j != skip_plane)
+                (void)mbar_wait(&bars[(jrun + j) % NS], ((jrun + j) / NS) & 1);
         if constexpr (!WG) {
             for (int o = wwaited; o < wissued; ++o)
                 (void)mbar_wait(&wbars[(wrun + o) % NW], ((wrun + o) / NW) & 1);

@@ -11,15 +11,12 @@ namespace {
 
 // (tx, ty, ns) variants compiled per storage width; each is offered with
 // several z-chunk lengths.
-const TileConfig kVariants4[] = {{32, 8, 0, 9, 1},  {32, 4, 0, 9, 1},  {64, 4, 0, 9, 1},
-                                 {32, 16, 0, 9, 1}, {32, 8, 0, 8, 2},  {32, 16, 0, 9, 2},
-                                 {64, 8, 0, 9, 2}, {32, 8, 0, 8, 2, 1}, {32, 8, 0, 8, 2, 2},
-                                 {32, 8, 0, 7, 2, 3}, {32, 8, 0, 5, 2, 1},
-                                 {32, 8, 0, 4, 2, 1, 1}, {32, 8, 0, 6, 2, 1, 1},
-                                 {32, 8, 0, 6, 2, 1}, {32, 8, 0, 8, 2, 2},
-                                 {32, 16, 0, 8, 2, 2}, {64, 8, 0, 8, 2, 2},
-                                 {32, 8, 0, 8, 2, 2, 0, 1}, {32, 8, 0, 8, 2, 1, 0, 1},
-                                 {32, 8, 0, 8, 2, 2, 1, 1}};
+const TileConfig kVariants4[] = {{32, 8, 0, 9, 1},
+                                 {32, 8, 0, 8, 2, 2},
+                                 {32, 8, 0, 8, 2, 2, 0, 1},
+                                 {32, 8, 0, 8, 2, 1, 0, 1},
+                                 {32, 8, 0, 8, 2, 2, 1, 1},
+                                 {32, 8, 0, 8, 2, 2, 2, 1}};
 const TileConfig kVariants8[] = {{32, 4, 0, 8, 1}, {16, 8, 0, 8, 1}};
 const int kZc[kZcChoices] = {40, 32, 64, 16};
 constexpr int kNz = kZcChoices;

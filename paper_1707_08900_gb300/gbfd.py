@@ -40,7 +40,9 @@ EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state"
            "gbfd_cnn_param_count", "gbfd_cnn_set_params", "gbfd_cnn_get_params",
            "gbfd_cnn_set_norm", "gbfd_cnn_forward", "gbfd_cnn_gradients",
            "gbfd_cnn_train_step", "gbfd_cnn_apply", "gbfd_step_corrected", "gbfd_box_filter",
-           "gbfd_cnn_launch_count", "gbfd_cnn_last_error")
+           "gbfd_cnn_launch_count", "gbfd_cnn_last_error", "gbfd_cnn_set_option",
+           "gbfd_fp64_fma_rate")
+GBFD_CNN_OPT_CONV_GRID, GBFD_CNN_OPT_WGRAD_PARTS = 1, 2
 GBFD_BATCH_OPT_GRAPH, GBFD_BATCH_OPT_ZCHUNK, GBFD_BATCH_OPT_GRID = 1, 2, 3
 
 
@@ -153,6 +155,8 @@ def load(path=None):
     L.gbfd_cnn_launch_count.argtypes = [_VP]
     L.gbfd_cnn_last_error.restype = ctypes.c_char_p
     L.gbfd_cnn_last_error.argtypes = [_VP]
+    L.gbfd_cnn_set_option.argtypes = [_VP, ctypes.c_int, ctypes.c_int64]
+    L.gbfd_fp64_fma_rate.argtypes = [_VP, _DP]
     L.gbfd_status_string.restype = ctypes.c_char_p
     L.gbfd_status_string.argtypes = [ctypes.c_int]
     for name in EXPORTS:
@@ -253,6 +257,17 @@ def gbfd_autotune(ctx, reps=3, cache_path=None):
     path = cache_path.encode() if cache_path else None
     _check(load().gbfd_autotune(ctx, int(reps), path, ctypes.byref(cfg), ctypes.byref(ms)), ctx)
     return cfg.value, ms.value
+
+
+def gbfd_fp64_fma_rate(stream_ptr=None):
+    """Measured FP64 FMA rate of the current device in TFLOP/s (the FP64
+    path's roofline denominator)."""
+    if stream_ptr is None:
+        import torch
+        stream_ptr = torch.cuda.current_stream().cuda_stream
+    r = ctypes.c_double()
+    _check(load().gbfd_fp64_fma_rate(_VP(stream_ptr), ctypes.byref(r)))
+    return r.value
 
 
 def gbfd_last_error(ctx=None):
@@ -521,6 +536,10 @@ class CNN:
             out[k] = np.asarray(v[i:i + m], dtype=np.float64).reshape(sh)
             i += m
         return out
+
+    def set_option(self, key, value):
+        """GBFD_CNN_OPT_CONV_GRID / GBFD_CNN_OPT_WGRAD_PARTS (launch shapes)."""
+        _ccheck(load().gbfd_cnn_set_option(self.c, int(key), ctypes.c_int64(int(value))), self.c)
 
     def set_params(self, p):
         v = np.ascontiguousarray(p if isinstance(p, np.ndarray) else self.flatten(p),

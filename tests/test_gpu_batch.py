@@ -6,14 +6,13 @@ per-step bar and (b) the single-box solver (same arithmetic, same tile)."""
 import numpy as np
 import pytest
 
+from bars import FP32_TOL, INC_TOL, TERM_NU, inc_err, max_abs, term_exposing_state
 from oracle import fd
 from paper_1707_08900_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-
-FP32_TOL = 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -67,6 +66,33 @@ def test_batch_matches_oracle_and_single_box(graph):
         single = s.get_state()
         s.close()
         np.testing.assert_allclose(got, single, rtol=0, atol=1e-6 * np.abs(single).max())
+    b.close()
+
+
+def test_batch_one_step_elementwise_against_oracle():
+    """One batched RK3 step of uneven boxes on the term-exposing state (nu
+    0.02): every box within the FP32 bars, relative L2 and the element-wise
+    increment bar."""
+    from paper_1707_08900_gb300 import gbfd
+    ns = [16, 32, 24, 40]
+    lengths = [2 * np.pi, 3.0, 2 * np.pi, 5.0]
+    sts = [term_exposing_state((n, n, n), 50 + i, inputs) for i, n in enumerate(ns)]
+    b = gbfd.Batch(ns, lengths, [TERM_NU] * len(ns))
+    dts = []
+    for i, (n, L, st) in enumerate(zip(ns, lengths, sts)):
+        b.set_state(i, st.astype(np.float32))
+        g = fd.Grid(n, n, n, L, L, L)
+        dts.append(fd.cfl_dt(st, g, fd.Physics(cs=1.0, nu=TERM_NU), 0.4))
+    b.step(dts, 1)
+    b.sync()
+    for i, (n, L, st, dt) in enumerate(zip(ns, lengths, sts, dts)):
+        got = b.get_state(i)
+        g = fd.Grid(n, n, n, L, L, L)
+        ref = fd.rk3_step(st, dt, g, fd.Physics(cs=1.0, nu=TERM_NU))
+        err, inc = rel_l2(got, ref), inc_err(got, ref, st)
+        print(f"box {i} ({n}^3): relL2 {err} inc {inc} maxabs {max_abs(got, ref)}")
+        assert np.all(err <= FP32_TOL), (i, err)
+        assert np.all(inc <= INC_TOL), (i, inc)
     b.close()
 
 

@@ -47,12 +47,18 @@ def _net(n, batch, p):
     return net
 
 
-@pytest.mark.parametrize("n,batch", [(8, 2), (12, 1)])
-def test_forward_matches_oracle(n, batch):
+@pytest.mark.parametrize("n,batch,grid", [(8, 2, 0), (12, 1, 0), (8, 2, 1), (12, 1, 2),
+                                          (32, 2, 0), (32, 2, 7)])
+def test_forward_matches_oracle(n, batch, grid):
+    """`grid` caps the CTAs of each convolution launch (0: the default three
+    per SM), so that every CTA walks several tiles (8^3 x 2 has 8 tiles of
+    256 points, 32^3 x 2 has 256; 7 CTAs give 36-37 tiles each)."""
+    from paper_1707_08900_gb300 import gbfd
     p = _params(3)
     rng = np.random.default_rng(4)
     xs = rng.standard_normal((batch, 5, n, n, n))
     net = _net(n, batch, p)
+    net.set_option(gbfd.GBFD_CNN_OPT_CONV_GRID, grid)
     ys = net.forward(torch.from_numpy(xs.astype(np.float32)).cuda()).cpu().numpy()
     for b in range(batch):
         y_ref, _ = ocnn.forward(xs[b], p)
@@ -64,21 +70,30 @@ def test_forward_matches_oracle(n, batch):
     net.close()
 
 
-def test_gradients_match_oracle():
+@pytest.mark.parametrize("n,batch,grid,parts", [(8, 2, 0, 0), (8, 2, 1, 3), (32, 2, 0, 0),
+                                                (32, 2, 5, 17)])
+def test_gradients_match_oracle(n, batch, grid, parts):
+    """Loss and parameter gradients against the FP64 oracle; `grid` caps the
+    convolution CTAs as in the forward test, `parts` the CTAs of the weight
+    gradient sums (0: defaults), so CTAs loop over many tiles and points."""
+    from paper_1707_08900_gb300 import gbfd
     p = _params(5)
-    n, batch = 8, 2
     rng = np.random.default_rng(6)
     xs = rng.standard_normal((batch, 5, n, n, n))
     tgt = rng.standard_normal((batch, 5, n, n, n))  # normalised residual targets
     net = _net(n, batch, p)
+    net.set_option(gbfd.GBFD_CNN_OPT_CONV_GRID, grid)
+    net.set_option(gbfd.GBFD_CNN_OPT_WGRAD_PARTS, parts)
     xs_d = torch.from_numpy(xs.astype(np.float32)).cuda()
     ts_d = torch.from_numpy((xs + tgt).astype(np.float32)).cuda()
     g, loss = net.gradients(xs_d, ts_d)
     ref_loss, ref_g = ocnn.loss_and_grads(list(xs), list(tgt), p)
     assert loss == pytest.approx(ref_loss, rel=BF16_FWD_TOL)
     gg = net.unflatten(g)
+    errs = {k: _rel(gg[k], ref_g[k]) for k in ref_g}
+    print({k: f"{v:.2e}" for k, v in errs.items()})
     for k in ref_g:
-        assert _rel(gg[k], ref_g[k]) < BF16_GRAD_TOL, k
+        assert errs[k] < BF16_GRAD_TOL, (k, errs)
     net.close()
 
 

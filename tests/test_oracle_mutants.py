@@ -104,3 +104,37 @@ def test_pins_reject_mutant(name, mutant_dir):
 def test_unmutated_oracle_passes_suite():
     for check in _pin_suite():
         check()
+
+
+def test_increment_bar_catches_every_mutant(mutant_dir):
+    """The GPU parity tests bound the element-wise error of the FP32
+    per-step increment by bars.INC_TOL on the term-exposing state.  That
+    bar must be tight enough to catch a mistake anywhere in the right-hand
+    side: each planted mutant's increment must differ from the oracle's by
+    more than 10 x INC_TOL in some field, in the 55-point or the 19-point
+    form (the 19-point pass-2 mutant only shows in the latter)."""
+    import bars
+    from paper_1707_08900_gb300 import inputs
+    shape = (20, 24, 32)
+    nz, ny, nx = shape
+    g = fd.Grid(nx, ny, nz)
+    ph = fd.Physics(cs=1.0, nu=bars.TERM_NU, entropy_mode=1)
+    base = bars.term_exposing_state(shape, 11, inputs)
+    dt = fd.cfl_dt(base, g, ph, 0.4)
+    refs = [fd.rk3_step(base, dt, g, ph, form) for form in (fd.FORM_55P, fd.FORM_19P)]
+    saved = fd._lib
+    for name, (old, new) in sorted(MUTANTS.items()):
+        so = _build_mutant(mutant_dir, name, old, new)
+        try:
+            fd._lib = None
+            real_build = build_oracle.build
+            build_oracle.build = lambda force=False: so
+            try:
+                fd.lib()
+            finally:
+                build_oracle.build = real_build
+            worst = max(bars.inc_err(fd.rk3_step(base, dt, g, ph, form), ref, base).max()
+                        for form, ref in zip((fd.FORM_55P, fd.FORM_19P), refs))
+        finally:
+            fd._lib = saved
+        assert worst > 10 * bars.INC_TOL, (name, worst)
