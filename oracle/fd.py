@@ -38,6 +38,9 @@ def lib():
         L.or_rk3_coefficients.argtypes = [_P, _P]
         L.or_substep55.argtypes = [_P, _P, _P, _I, _D, _L, _L, _L, _D, _D, _D, _D, _D, _I]
         L.or_substep19.argtypes = [_P, _P, _P, _P, _I, _D, _L, _L, _L, _D, _D, _D, _D, _D, _I]
+        L.or_substep55_wall.argtypes = L.or_substep55.argtypes
+        L.or_substep19_wall.argtypes = L.or_substep19.argtypes
+        L.or_fill_ghosts_z.argtypes = [_P, _L, _L, _L, _I, _P]
         L.or_diagnostics.argtypes = [_P, _L, _L, _L, _D, _D, _D, _I, _P]
         L.or_cfl_dt.restype = _D
         L.or_cfl_dt.argtypes = [_P, _L, _L, _L, _D, _D, _D, _D, _D, _D, _D]
@@ -192,6 +195,77 @@ def rk3_step(state, dt, grid, phys, form=FORM_55P, nsteps=1):
         for s in range(3):
             st, w = substep(st, w, s, dt, grid, phys, form)
     return st
+
+
+# ---------------------------------------------------------------- walls in z
+
+# Parity of each field under the mirror about a wall point (lnrho, u_x,
+# u_y, u_z, s): an impermeable, free-slip wall keeps u_z odd, the rest even.
+WALL_PARITY = (1.0, 1.0, 1.0, -1.0, 1.0)
+GZ_WALL = 3
+
+
+def fill_ghosts_z(ext, parity=WALL_PARITY):
+    """Fill the ghost planes of a ghost-extended state (nf, nz + 6, ny, nx) in
+    place: mirror images about the walls at interior planes 0 and nz - 1."""
+    assert ext.dtype == np.float64 and ext.flags.c_contiguous
+    nf, nzt, ny, nx = ext.shape
+    par = _f64(np.asarray(parity[:nf], dtype=np.float64))
+    lib().or_fill_ghosts_z(_p(ext), nx, ny, nzt - 2 * GZ_WALL, nf, _p(par))
+    return ext
+
+
+def extend_wall(state):
+    """Interior state (nf, nz, ny, nx) -> ghost-extended copy with ghosts filled."""
+    st = _f64(state)
+    nf, nz, ny, nx = st.shape
+    ext = np.zeros((nf, nz + 2 * GZ_WALL, ny, nx))
+    ext[:, GZ_WALL:GZ_WALL + nz] = st
+    return fill_ghosts_z(ext)
+
+
+def interior_wall(ext):
+    return np.ascontiguousarray(ext[:, GZ_WALL:ext.shape[1] - GZ_WALL])
+
+
+def wall_spacing(grid):
+    """Grid spacing with walls through z = 0 and z = lz: lz / (nz - 1) in z."""
+    return (grid.lx / grid.nx, grid.ly / grid.ny, grid.lz / (grid.nz - 1))
+
+
+def substep_wall(ext_in, w, s, dt, grid, phys, form=FORM_55P):
+    """One RK3 substep with walls in z on ghost-extended arrays (ghosts of
+    ext_in filled).  Returns (ext_out with its ghosts filled, w_new)."""
+    st = _f64(ext_in)
+    wn = _f64(w).copy()
+    out = np.zeros_like(st)
+    if form == FORM_55P:
+        lib().or_substep55_wall(_p(st), _p(wn), _p(out), s, dt, *grid.dims(), phys.cs, phys.nu,
+                                phys.entropy_mode)
+    else:
+        divf = np.zeros((1,) + st.shape[1:])
+        lib().or_substep19_wall(_p(st), _p(wn), _p(out), _p(divf), s, dt, *grid.dims(),
+                                phys.cs, phys.nu, phys.entropy_mode)
+    return fill_ghosts_z(out), wn
+
+
+def rk3_step_wall(state, dt, grid, phys, form=FORM_55P, nsteps=1):
+    """`nsteps` RK3 steps with walls in z (Algorithm 1: boundary step, then
+    each substep); interior state in and out."""
+    ext = extend_wall(state)
+    w = np.zeros_like(ext)
+    for _ in range(nsteps):
+        for s in range(3):
+            ext, w = substep_wall(ext, w, s, dt, grid, phys, form)
+    return interior_wall(ext)
+
+
+def cfl_dt_wall(state, grid, phys, cfl=0.4, cnu=0.25):
+    """The dt rule on the wall grid (z spacing lz / (nz - 1))."""
+    st = _f64(state)
+    lz_eff = grid.lz * grid.nz / (grid.nz - 1)  # so that the routine's lz / nz is the spacing
+    return lib().or_cfl_dt(_p(st), grid.nx, grid.ny, grid.nz, grid.lx, grid.ly, lz_eff,
+                           phys.cs, phys.nu, cfl, cnu)
 
 
 def diagnostics(state, grid, phys):

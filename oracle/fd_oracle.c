@@ -34,7 +34,19 @@
  *
  * Grid (Sect. 2.3): N_i equidistant points per axis, spacing L_i / N_i,
  * periodic in every axis (Sect. 4); periodic wrap is plain modular indexing,
- * there are no ghost zones.  Fields are stored [field][z][y][x] with x
+ * there are no ghost zones.  The wall variant (the "_wall" routines) keeps x
+ * and y periodic and bounds z by two walls through the grid points z = 0
+ * and z = Lz (spacing Lz / (N_z - 1)); the paper's ghost zones (Sect. 4,
+ * Algorithm 1's boundary step) then carry the boundary condition: arrays
+ * hold 3 ghost planes below and above the N_z interior planes, and before
+ * each substep (and before the 19-point form's second pass, for the stored
+ * divergence) they are filled as the mirror images of the interior about
+ * the wall points, f(-k) = p f(k) and f(N_z-1+k) = p f(N_z-1-k), with parity
+ * p = +1 for lnrho, u_x, u_y, s and the divergence and p = -1 for u_z: an
+ * impermeable, free-slip wall.  The paper defines no boundary condition
+ * besides periodic; this one is the reading of the ghost-zone mechanism
+ * whose exact solution is known: the periodic solution on 2 (N_z - 1)
+ * planes of the mirror-extended state.  Fields are stored [field][z][y][x] with x
  * fastest; the field order is (lnrho, u_x, u_y, u_z[, s]).  The paper's model
  * is isothermal and carries no energy variable: with entropy_mode = 0 the
  * state has the paper's four fields; with entropy_mode = 1 a fifth field s is
@@ -90,12 +102,16 @@ double or_dmix_point(const double *s, double ha, double hb)
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-    long n[3];   /* points per axis: x, y, z */
-    double h[3]; /* spacing L_i / N_i */
-    long npts;
+    long n[3];   /* points per axis: x, y, z (interior points) */
+    double h[3]; /* spacing L_i / N_i (L_z / (N_z - 1) between walls) */
+    long gz;     /* ghost planes below and above the interior in z: 0
+                    (periodic z) or 3 (walls) */
+    long npts;   /* values stored per field: N_x N_y (N_z + 2 gz) */
 } grid_t;
 
-static grid_t make_grid(long nx, long ny, long nz, double lx, double ly, double lz)
+#define GZ_WALL 3
+
+static grid_t make_grid_bc(long nx, long ny, long nz, double lx, double ly, double lz, long gz)
 {
     grid_t g;
     g.n[0] = nx;
@@ -103,9 +119,15 @@ static grid_t make_grid(long nx, long ny, long nz, double lx, double ly, double 
     g.n[2] = nz;
     g.h[0] = lx / (double)nx;
     g.h[1] = ly / (double)ny;
-    g.h[2] = lz / (double)nz;
-    g.npts = nx * ny * nz;
+    g.h[2] = gz ? lz / (double)(nz - 1) : lz / (double)nz;
+    g.gz = gz;
+    g.npts = nx * ny * (nz + 2 * gz);
     return g;
+}
+
+static grid_t make_grid(long nx, long ny, long nz, double lx, double ly, double lz)
+{
+    return make_grid_bc(nx, ny, nz, lx, ly, lz, 0);
 }
 
 static inline long wrap(long i, long n)
@@ -114,10 +136,13 @@ static inline long wrap(long i, long n)
     return r < 0 ? r + n : r;
 }
 
-/* linear index of point p = (x, y, z), wrapped periodically */
+/* linear index of point p = (x, y, z): x and y wrapped periodically; z
+ * wrapped too, or (walls) taken as is from the ghost-extended array, whose
+ * z = -gz .. N_z - 1 + gz planes are all stored */
 static inline long at(const grid_t *g, const long *p)
 {
-    return (wrap(p[2], g->n[2]) * g->n[1] + wrap(p[1], g->n[1])) * g->n[0] + wrap(p[0], g->n[0]);
+    const long z = g->gz ? p[2] + g->gz : wrap(p[2], g->n[2]);
+    return (z * g->n[1] + wrap(p[1], g->n[1])) * g->n[0] + wrap(p[0], g->n[0]);
 }
 
 /* 7 samples of f along `axis` centred on p */
@@ -422,6 +447,29 @@ int or_rhs_forced(const double *state, double *rhs, long nx, long ny, long nz, d
 }
 
 /* ------------------------------------------------------------------ */
+/* Ghost zones of the wall variant (Sect. 4; Algorithm 1's boundary step) */
+/* ------------------------------------------------------------------ */
+
+/* Fill the 3 ghost planes below and above the N_z interior planes of each
+ * of nf fields of a ghost-extended array (N_z + 6 planes of N_y x N_x per
+ * field, interior plane z at index z + 3): mirror images about the wall
+ * points z = 0 and z = N_z - 1, scaled by the field's parity (+1 or -1):
+ *   f(-k) = parity f(k),  f(N_z - 1 + k) = parity f(N_z - 1 - k),  k = 1..3. */
+void or_fill_ghosts_z(double *st, long nx, long ny, long nz, int nf, const double *parity)
+{
+    const long plane = nx * ny;
+    const long fpitch = plane * (nz + 2 * GZ_WALL);
+    for (int f = 0; f < nf; ++f) {
+        double *a = st + f * fpitch + GZ_WALL * plane; /* interior plane 0 */
+        for (long k = 1; k <= GZ_WALL; ++k)
+            for (long c = 0; c < plane; ++c) {
+                a[-k * plane + c] = parity[f] * a[k * plane + c];
+                a[(nz - 1 + k) * plane + c] = parity[f] * a[(nz - 1 - k) * plane + c];
+            }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* 2N-storage RK3, Eq. 10                                               */
 /* ------------------------------------------------------------------ */
 
@@ -449,9 +497,9 @@ static inline void rk3_update(int s, double dt, double r, double in, double *w, 
  * `in` and `w` (the 2N register, u-tilde), writes `out` and `w`. */
 static void substep55(const double *in, double *w, double *out, int s, double dt, long nx,
                       long ny, long nz, double lx, double ly, double lz, double cs, double nu,
-                      int entropy_mode, const forcing_t *fo)
+                      int entropy_mode, const forcing_t *fo, long gz)
 {
-    grid_t g = make_grid(nx, ny, nz, lx, ly, lz);
+    grid_t g = make_grid_bc(nx, ny, nz, lx, ly, lz, gz);
     phys_t ph = make_phys(cs, nu, entropy_mode);
     const long n = g.npts;
 #pragma omp parallel for schedule(static)
@@ -477,9 +525,9 @@ static void substep55(const double *in, double *w, double *out, int s, double dt
  * with grad taken by Eq. 6 on the stored divergence (Eq. 9). */
 static void substep19(const double *in, double *w, double *out, double *divf, int s, double dt,
                       long nx, long ny, long nz, double lx, double ly, double lz, double cs,
-                      double nu, int entropy_mode, const forcing_t *fo)
+                      double nu, int entropy_mode, const forcing_t *fo, long gz)
 {
-    grid_t g = make_grid(nx, ny, nz, lx, ly, lz);
+    grid_t g = make_grid_bc(nx, ny, nz, lx, ly, lz, gz);
     phys_t ph = make_phys(cs, nu, entropy_mode);
     const long n = g.npts;
     /* pass 1 */
@@ -495,7 +543,15 @@ static void substep19(const double *in, double *w, double *out, double *divf, in
                 for (int f = 0; f < ph.nfields; ++f)
                     rk3_update(s, dt, r[f], in[f * n + c], &w[f * n + c], &out[f * n + c]);
             }
-    /* pass 2 (periodic wrap of the divergence field by modular indexing) */
+    /* the stored divergence is symmetric about a wall: its ghost planes
+     * are the mirror images of the interior (the boundary step between
+     * the passes) */
+    if (gz) {
+        const double even = 1.0;
+        or_fill_ghosts_z(divf, nx, ny, nz, 1, &even);
+    }
+    /* pass 2 (periodic wrap of the divergence field by modular indexing, or
+     * its ghost planes) */
 #pragma omp parallel for schedule(static)
     for (long z = 0; z < nz; ++z)
         for (long y = 0; y < ny; ++y)
@@ -513,14 +569,35 @@ static void substep19(const double *in, double *w, double *out, double *divf, in
 void or_substep55(const double *in, double *w, double *out, int s, double dt, long nx, long ny,
                   long nz, double lx, double ly, double lz, double cs, double nu, int entropy_mode)
 {
-    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL);
+    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, 0);
 }
 
 void or_substep19(const double *in, double *w, double *out, double *divf, int s, double dt,
                   long nx, long ny, long nz, double lx, double ly, double lz, double cs, double nu,
                   int entropy_mode)
 {
-    substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL);
+    substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, 0);
+}
+
+/* Wall variant (z bounded by walls through z = 0 and z = Lz, spacing
+ * Lz / (N_z - 1); x, y periodic): the same substeps on ghost-extended arrays
+ * of N_z + 6 planes per field (interior plane z at index z + 3), whose ghost
+ * planes the caller has filled by or_fill_ghosts_z (Algorithm 1's boundary
+ * step) before the call.  Only interior planes of out, w and divf are
+ * written (divf's ghosts are filled between the passes). */
+void or_substep55_wall(const double *in, double *w, double *out, int s, double dt, long nx,
+                       long ny, long nz, double lx, double ly, double lz, double cs, double nu,
+                       int entropy_mode)
+{
+    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, GZ_WALL);
+}
+
+void or_substep19_wall(const double *in, double *w, double *out, double *divf, int s, double dt,
+                       long nx, long ny, long nz, double lx, double ly, double lz, double cs,
+                       double nu, int entropy_mode)
+{
+    substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL,
+              GZ_WALL);
 }
 
 /* One substep with the forcing of the current time step (k, phi and e are
@@ -536,9 +613,9 @@ int or_substep_forced(const double *in, double *w, double *out, double *divf, in
     if (make_forcing(&fo, kint, phi, e, f0, cs, dt, lx, ly, lz))
         return -1;
     if (form == 1)
-        substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo);
+        substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo, 0);
     else
-        substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo);
+        substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo, 0);
     return 0;
 }
 
