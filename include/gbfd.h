@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define GBFD_ABI_VERSION 1
+#define GBFD_ABI_VERSION 2
 
 typedef enum {
     GBFD_OK = 0,
@@ -71,7 +71,26 @@ typedef struct {
     double lx, ly, lz;    /* box lengths L_i (> 0)                             */
     double cs;            /* isothermal sound speed c_s (>= 0), Eq. 2         */
     double nu;            /* kinematic viscosity nu (>= 0), Eq. 2             */
+    int32_t bc_z;         /* GBFD_BC_PERIODIC (0) or GBFD_BC_WALL (1)          */
+    int32_t reserved;     /* 0                                                */
 } gbfd_params;
+
+/* Boundary condition along z (Sect. 4: ghost zones carry the boundary
+ * conditions; Algorithm 1's "compute boundary conditions" step).
+ * PERIODIC: every axis periodic (the paper's runs); z spacing lz / nz.
+ * WALL: x and y periodic; z bounded by two impermeable, free-slip walls
+ * through the first and last grid planes, which sit at z = 0 and z = lz
+ * (z spacing lz / (nz - 1)).  Three ghost planes below and above the
+ * interior are filled after every substep (and between the two passes of
+ * the 19-point form, for the stored divergence) with the mirror images of
+ * the interior about the wall planes: even (f(-k) = f(k)) for lnrho, u_x,
+ * u_y, s and the divergence, odd (f(-k) = -f(k)) for u_z.  The paper defines
+ * no condition besides periodic; this one is the mirror reading of its
+ * ghost zones, whose solution is the periodic one of the mirror-extended
+ * state.  The initial state should have u_z = 0 on both wall planes.  Not
+ * available with the forcing, the batch or the correction network
+ * (UNSUPPORTED). */
+enum { GBFD_BC_PERIODIC = 0, GBFD_BC_WALL = 1 };
 
 /* FP64 reductions over the current state (grid cell volume dV = prod L_i/N_i):
  * mass = dV sum exp(lnrho); ekin = dV sum exp(lnrho)|u|^2/2;

@@ -39,6 +39,7 @@ struct gbfd_ctx {
     int kernel_path;  // 0 = tiled when supported, 1 = simple
     int tile_cfg;     // index into the tiled kernel's tile table (-1 = default)
     int sms;          // SM count of the context's device (read at init)
+    double h[3];      // grid spacings (z: lz / (nz - 1) between walls)
     int fault_skip;   // test-only fault injection (-1 = off)
     int host_path;    // 0 = pinned host buffers accessed in place, 1 = always staged
     int host_async;   // 1 = gbfd_get_state to host memory does not wait for the stream
@@ -118,6 +119,10 @@ bool validate(const gbfd_params *p, char *why, size_t n)
         snprintf(why, n, "unknown form %d", p->form);
         return false;
     }
+    if (p->bc_z != GBFD_BC_PERIODIC && p->bc_z != GBFD_BC_WALL) {
+        snprintf(why, n, "bc_z must be GBFD_BC_PERIODIC or GBFD_BC_WALL");
+        return false;
+    }
     if (p->entropy_mode != 0 && p->entropy_mode != 1) {
         snprintf(why, n, "entropy_mode must be 0 or 1");
         return false;
@@ -147,9 +152,12 @@ Plan make_plan(const gbfd_params *p)
     const int nf = nfields_of(p);
     const int sb = p->precision == GBFD_FP64 ? 8 : 4;
     const int wb = (p->precision == GBFD_FP64 || p->precision == GBFD_FP32_ACC64_W64) ? 8 : 4;
-    pl.Ls = make_layout(p->nx, p->ny, p->nz, sb, nf);
+    // walls in z: ghost planes on the state and the stored divergence (the
+    // 2N register is only read at interior points)
+    const int gz = p->bc_z == GBFD_BC_WALL ? GZW : 0;
+    pl.Ls = make_layout(p->nx, p->ny, p->nz, sb, nf, gz);
     pl.Lw = make_layout(p->nx, p->ny, p->nz, wb, nf);
-    pl.Ld = make_layout(p->nx, p->ny, p->nz, sb, 1);
+    pl.Ld = make_layout(p->nx, p->ny, p->nz, sb, 1, gz);
     pl.ndiag = diag_blocks(pl.Ls);
     size_t off = 0;
     for (int i = 0; i < 2; ++i) {
@@ -313,6 +321,12 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
     c->launches += n;
     if (e != cudaSuccess)
         return cuda_fail(c, e, "substep launch");
+    // walls in z: the boundary step (Algorithm 1) on the new state
+    n = 0;
+    e = launch_fill_ghosts_z(b.out, c->Ls, c->nf, kWallOddMask, c->stream, &n);
+    c->launches += n;
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "ghost planes");
     c->cur ^= 1;
     return GBFD_OK;
 }
@@ -327,7 +341,8 @@ void set_global_error(const char *msg) { set_err(nullptr, "%s", msg); }
 // correction network and the box filter); false otherwise.
 bool ctx_view(gbfd_ctx *c, float **origin, Layout *L, int *nf, cudaStream_t *s)
 {
-    if (!c || c->broken || c->sbytes != 4 || c->p.nx != c->p.ny || c->p.ny != c->p.nz)
+    if (!c || c->broken || c->sbytes != 4 || c->p.nx != c->p.ny || c->p.ny != c->p.nz ||
+        c->p.bc_z != GBFD_BC_PERIODIC)
         return false;
     *origin = reinterpret_cast<float *>(c->state_region[c->cur] + c->Ls.origin);
     *L = c->Ls;
@@ -422,7 +437,11 @@ gbfd_status gbfd_init(const gbfd_params *p, void *workspace, size_t workspace_by
     c->host_async = 0;
     memset(&c->tmaps, 0, sizeof c->tmaps);
     c->broken = false;
-    const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
+    const double hx = p->lx / p->nx, hy = p->ly / p->ny;
+    const double hz = p->bc_z == GBFD_BC_WALL ? p->lz / (p->nz - 1) : p->lz / p->nz;
+    c->h[0] = hx;
+    c->h[1] = hy;
+    c->h[2] = hz;
     c->c64 = make_coef<double>(hx, hy, hz, p->cs, p->nu);
     c->c32 = make_coef<float>(hx, hy, hz, p->cs, p->nu);
     c->err[0] = 0;
@@ -509,6 +528,12 @@ gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, in
     ctx->launches += nl;
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "set_state scatter");
+    nl = 0;
+    e = launch_fill_ghosts_z(ctx->state_region[ctx->cur] + ctx->Ls.origin, ctx->Ls, ctx->nf,
+                             kWallOddMask, ctx->stream, &nl);
+    ctx->launches += nl;
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "set_state ghost planes");
     return GBFD_OK;
 }
 
@@ -589,6 +614,10 @@ gbfd_status gbfd_rk3_step_forced(gbfd_ctx *ctx, double dt, int nsteps, double f0
     if (nsteps > 0 && (!k || !phi || !e)) {
         set_err(ctx, "rk3_step_forced: k, phi and e must not be NULL");
         return GBFD_ERR_INVALID_ARG;
+    }
+    if (ctx->p.bc_z != GBFD_BC_PERIODIC) {
+        set_err(ctx, "rk3_step_forced: the forcing of Sect. 6 needs a periodic box");
+        return GBFD_ERR_UNSUPPORTED;
     }
     const double two_pi = 6.283185307179586476925286766559;
     const double L[3] = {ctx->p.lx, ctx->p.ly, ctx->p.lz};
@@ -673,7 +702,7 @@ gbfd_status gbfd_diagnostics(gbfd_ctx *ctx, gbfd_diag *out)
         set_err(ctx, "out is NULL");
         return GBFD_ERR_INVALID_ARG;
     }
-    const double dv = (ctx->p.lx / ctx->p.nx) * (ctx->p.ly / ctx->p.ny) * (ctx->p.lz / ctx->p.nz);
+    const double dv = ctx->h[0] * ctx->h[1] * ctx->h[2];
     int nl = 0;
     cudaError_t e = launch_diagnostics(ctx->state_region[ctx->cur] + ctx->Ls.origin, ctx->Ls,
                                        ctx->nf, dv, ctx->diag_part, ctx->ndiag, ctx->diag_out,
@@ -711,7 +740,7 @@ gbfd_status gbfd_cfl_dt(gbfd_ctx *ctx, double cfl, double cnu, double *dt_out)
     gbfd_status st = gbfd_diagnostics(ctx, &d);
     if (st != GBFD_OK)
         return st;
-    const double h[3] = {ctx->p.lx / ctx->p.nx, ctx->p.ly / ctx->p.ny, ctx->p.lz / ctx->p.nz};
+    const double *h = ctx->h;
     double dmin = h[0] < h[1] ? h[0] : h[1];
     dmin = dmin < h[2] ? dmin : h[2];
     double dt = cfl * dmin / (d.umax + ctx->p.cs);

@@ -22,6 +22,13 @@ namespace gbfd {
 // origin is offset so that every interior row starts 128-byte aligned
 // (whole-sector warp accesses).  GX = 4 (not 3) keeps the TMA box origin
 // X = x0 16-byte aligned.
+//
+// With walls in z (the ghost-zone boundary variant) each field also holds
+// gz = 3 ghost planes below and above its nz interior planes: interior plane
+// z sits at plane index z + gz of the field, the origin points at interior
+// plane 0, so element offsets of interior points are unchanged, and ghost
+// planes are z = -3..-1 and nz..nz+2.  A ghost-fill kernel writes them (the
+// parity mirror of the interior about the wall points) after every substep.
 // ---------------------------------------------------------------------------
 constexpr int GX = 4;
 constexpr int GY = 3;
@@ -36,23 +43,39 @@ struct Layout {
     long long fpitch;   // elements between consecutive fields
     long long origin;   // byte offset of element (f=0,z=0,Y=0,X=0) in the region
     long long bytes;    // region bytes for `nf` fields
+    int gz;             // ghost planes below and above in z: 0 (periodic z) or
+                        // GZW (walls in z)
 };
 
-inline Layout make_layout(int nx, int ny, int nz, int w, int nf)
+constexpr int GZW = 3;  // ghost planes per side with walls in z
+
+inline Layout make_layout(int nx, int ny, int nz, int w, int nf, int gz = 0)
 {
     Layout L;
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
     L.w = w;
+    L.gz = gz;
     const long long q = 128 / w;  // elements per 128 bytes
     L.P = ((nx + 2 * GX + q - 1) / q) * q;
     L.rows = ny + 2 * GY;
     L.plane = L.P * L.rows;
-    L.fpitch = L.plane * nz;  // P*w is a multiple of 128, so is this
-    L.origin = 128 - GX * w;
+    L.fpitch = L.plane * (nz + 2 * gz);  // P*w is a multiple of 128, so is this
+    L.origin = 128 - GX * w + (long long)gz * L.plane * w;
     L.bytes = 128 + (long long)nf * L.fpitch * w;
     return L;
+}
+
+// Index of the plane holding local z (which may lie in [-3, nz + 3) for a
+// stencil arm): the wrapped index for periodic z, the plane itself (ghost
+// planes included) with walls.  TMA maps of a walled layout start at ghost
+// plane -gz, so their z coordinate is zplane + gz.
+__host__ __device__ __forceinline__ int zplane(const Layout &L, int z)
+{
+    if (L.gz)
+        return z;
+    return z < 0 ? z + L.nz : (z >= L.nz ? z - L.nz : z);
 }
 
 // Element index of interior point (x, y, z) of field f relative to origin.

@@ -150,6 +150,67 @@ cudaError_t gather_t(const TS *src, TD *dst, const Layout &L, int nf, cudaStream
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ ghost planes in z
+
+// With walls in z (Layout::gz = GZW): the ghost planes of nf fields as the
+// mirror images of the interior about the wall points z = 0 and z = nz - 1,
+// f(-k) = p_f f(k) and f(nz - 1 + k) = p_f f(nz - 1 - k), k = 1..3, where
+// p_f = -1 for the fields flagged in odd_mask (bit f) and +1 otherwise.  Whole
+// padded planes are copied (ghost rows and columns included: the producing
+// kernel has already made them periodic copies).  One thread per 16 bytes of
+// the 2 GZW ghost planes of every field (a padded plane is a whole number of
+// 128-byte rows).
+template <class T>
+__global__ void __launch_bounds__(256) k_fill_ghosts_z(T *__restrict__ origin, Layout L, int nf,
+                                                      int odd_mask)
+{
+    constexpr int V = 16 / sizeof(T);
+    const long long pv = L.plane / V;  // 16-byte vectors per plane
+    const long long total = (long long)nf * 2 * GZW * pv;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long e = i % pv;
+        long long r = i / pv;
+        const int k = 1 + (int)(r % GZW);
+        r /= GZW;
+        const int side = (int)(r % 2);
+        const int f = (int)(r / 2);
+        const int zsrc = side ? L.nz - 1 - k : k;
+        const int zdst = side ? L.nz - 1 + k : -k;
+        const T *src = origin + (long long)f * L.fpitch + (long long)zsrc * L.plane;
+        T *dst = origin + (long long)f * L.fpitch + (long long)zdst * L.plane;
+        // a plane is the P * rows values from its (Y, X) = (0, 0) element,
+        // which is 16-byte aligned (128 - GX w bytes past a 128-byte boundary)
+        uint4 v = reinterpret_cast<const uint4 *>(src)[e];
+        if ((odd_mask >> f) & 1) {
+            T *t = reinterpret_cast<T *>(&v);
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                t[j] = -t[j];
+        }
+        reinterpret_cast<uint4 *>(dst)[e] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fill_ghosts_z(void *origin, const Layout &L, int nf, int odd_mask,
+                                 cudaStream_t stream, int *launches)
+{
+    if (!L.gz)
+        return cudaSuccess;
+    const long long total = (long long)nf * 2 * GZW * (L.plane * L.w / 16);
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    if (L.w == 8)
+        k_fill_ghosts_z<double><<<blocks, 256, 0, stream>>>((double *)origin, L, nf, odd_mask);
+    else
+        k_fill_ghosts_z<float><<<blocks, 256, 0, stream>>>((float *)origin, L, nf, odd_mask);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+namespace {
+
 // ---------------------------------------------------------------- reductions
 
 constexpr int DIAG_THREADS = 256;

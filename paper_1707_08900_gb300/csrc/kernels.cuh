@@ -81,6 +81,14 @@ cudaError_t launch_scatter(const void *src, int src_fp64, void *dst, const Layou
 cudaError_t launch_gather(const void *src, const Layout &L, void *dst, int dst_fp64, int nf,
                           cudaStream_t stream, int *launches);
 
+// With walls in z: fill the ghost planes of nf fields of a walled layout
+// (origin = the layout's origin pointer) as parity mirrors about the wall
+// points; bit f of odd_mask marks an odd field (u_z: bit 3).  No-op for
+// periodic layouts.
+constexpr int kWallOddMask = 1 << 3;
+cudaError_t launch_fill_ghosts_z(void *origin, const Layout &L, int nf, int odd_mask,
+                                 cudaStream_t stream, int *launches);
+
 // FP64 reductions: partials per block, then one fixed-order final pass.
 // out[16]: mass, ekin, umax, urms, rms[5], maxabs[5], nonfinite, (pad).
 int diag_blocks(const Layout &L);

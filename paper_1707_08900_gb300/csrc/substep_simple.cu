@@ -34,9 +34,7 @@ __device__ __forceinline__ GlobalAcc<T> make_acc(const T *base, const Layout &L,
     A.y = y;
 #pragma unroll
     for (int k = -3; k <= 3; ++k) {
-        int zz = z + k;
-        zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
-        A.zk[k + 3] = zz;
+        A.zk[k + 3] = zplane(L, z + k);
     }
     return A;
 }
@@ -148,6 +146,11 @@ template <class TS, class TW, class TA>
 cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKStage &st,
                                 cudaStream_t stream, int *launches)
 {
+    // walls in z: the stored divergence is even about a wall; its ghost
+    // planes are filled between the passes
+    cudaError_t e = launch_fill_ghosts_z(b.div, b.Ls, 1, 0, stream, launches);
+    if (e != cudaSuccess)
+        return e;
     const dim3 block(32, 4, 1);
     const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
     k_pass2_simple<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,

@@ -167,7 +167,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         if (j == skip_plane)
             return;
         int z = z0 - R + j;
-        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        z = zplane(Ls, z) + Ls.gz;  // TMA z coordinate
         const int slot = (jrun + j) % NS;
         tiled::mbar_expect_tx(&bars[slot], RG::SLOT_BYTES);
         tiled::tma_load_4d(smem + slot * RG::SLOT_PITCH, tmap, &bars[slot], x0, y0, z, 0);

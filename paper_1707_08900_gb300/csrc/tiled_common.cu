@@ -69,14 +69,17 @@ bool encode_tmap(TmapCache *cache, const void *origin, const Layout &L, int nf, 
     TmapCache::Entry &e = cache->e[cache->next];
     cache->next = (cache->next + 1) % TmapCache::kEntries;
     memset(&e, 0, sizeof e);
+    // with walls in z the map covers the ghost planes too: it starts at
+    // ghost plane -gz (kernels add gz to the plane index)
     const cuuint64_t dims[4] = {(cuuint64_t)(L.nx + 2 * GX), (cuuint64_t)L.rows,
-                                (cuuint64_t)L.nz, (cuuint64_t)nf};
+                                (cuuint64_t)(L.nz + 2 * L.gz), (cuuint64_t)nf};
+    const char *base = static_cast<const char *>(origin) - (long long)L.gz * L.plane * L.w;
     const cuuint64_t strides[3] = {(cuuint64_t)(L.P * L.w), (cuuint64_t)(L.plane * L.w),
                                    (cuuint64_t)(L.fpitch * L.w)};
     const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)nf};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(&e.map, L.w == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                    4, const_cast<void *>(origin), dims, strides, box, estr,
+                    4, const_cast<char *>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)

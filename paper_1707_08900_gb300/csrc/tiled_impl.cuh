@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(TX *TY) k_substep_tiled(
     int issued = 0;
     auto issue = [&](int j) {
         int z = z0 - R + j;
-        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        z = zplane(Ls, z) + Ls.gz;  // TMA z coordinate
         const int slot = j % NS;
         mbar_expect_tx(&bars[slot], SLOT_BYTES);
         tma_load_4d(smem + slot * SLOT_PITCH, &tmap, &bars[slot], x0, y0, z, 0);

@@ -22,6 +22,8 @@ GBFD_FP64, GBFD_FP32, GBFD_FP32_ACC64, GBFD_FP32_ACC64_W64 = 0, 1, 2, 3
 GBFD_55P, GBFD_19P = 0, 1
 GBFD_OPT_KERNEL_PATH, GBFD_OPT_TILE_CONFIG, GBFD_OPT_FAULT_SKIP_COPY, GBFD_OPT_HOST_PATH = 1, 2, 3, 4
 GBFD_OPT_HOST_ASYNC = 5
+GBFD_BC_PERIODIC, GBFD_BC_WALL = 0, 1
+BCS = {"periodic": GBFD_BC_PERIODIC, "wall": GBFD_BC_WALL}
 
 PRECISIONS = {"fp64": GBFD_FP64, "fp32": GBFD_FP32, "fp32_acc64": GBFD_FP32_ACC64,
               "fp32_acc64_w64": GBFD_FP32_ACC64_W64}
@@ -57,7 +59,7 @@ class gbfd_params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("form", ctypes.c_int32),
                 ("entropy_mode", ctypes.c_int32), ("lx", ctypes.c_double),
                 ("ly", ctypes.c_double), ("lz", ctypes.c_double), ("cs", ctypes.c_double),
-                ("nu", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("bc_z", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gbfd_diag(ctypes.Structure):
@@ -277,9 +279,10 @@ def gbfd_last_error(ctx=None):
 # ------------------------------------------------------------ convenience
 
 def make_params(shape, lengths=(2 * np.pi,) * 3, cs=1.0, nu=5e-3, precision="fp64", form="55p",
-                entropy_mode=1):
+                entropy_mode=1, bc_z="periodic"):
     nz, ny, nx = shape
     p = gbfd_params()
+    p.bc_z = BCS[bc_z] if isinstance(bc_z, str) else int(bc_z)
     p.nx, p.ny, p.nz = nx, ny, nz
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.form = FORMS[form] if isinstance(form, str) else int(form)
@@ -293,16 +296,17 @@ class Solver:
     """A gbfd context plus its workspace (a torch CUDA uint8 tensor).
 
     State arrays are (nfields, nz, ny, nx); nfields = 5 with entropy_mode 1,
-    4 with entropy_mode 0."""
+    4 with entropy_mode 0.  bc_z = "wall" bounds z by two free-slip walls
+    through the first and last planes (z spacing lz / (nz - 1))."""
 
     def __init__(self, shape, lengths=(2 * np.pi,) * 3, cs=1.0, nu=5e-3, precision="fp64",
-                 form="55p", entropy_mode=1, device=None, stream=None):
+                 form="55p", entropy_mode=1, device=None, stream=None, bc_z="periodic"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gbfd needs a CUDA device; there is no CPU path")
         self.torch = torch
         self.device = torch.device(device or "cuda")
-        self.params = make_params(shape, lengths, cs, nu, precision, form, entropy_mode)
+        self.params = make_params(shape, lengths, cs, nu, precision, form, entropy_mode, bc_z)
         self.shape = tuple(shape)
         self.nfields = 5 if entropy_mode else 4
         nbytes = gbfd_workspace_bytes(self.params)

@@ -62,6 +62,13 @@ def test_workspace_size_accounts_for_layout(lib):
     assert gbfd.gbfd_workspace_bytes(p32) >= 3 * 5 * n * 4
     p19 = gbfd.make_params((64, 64, 64), precision="fp32", form="19p")
     assert gbfd.gbfd_workspace_bytes(p19) > gbfd.gbfd_workspace_bytes(p32)
+    # walls in z: 3 ghost planes below and above, on both state buffers
+    pw = gbfd.make_params((64, 64, 64), precision="fp32", bc_z="wall")
+    plane = (64 + 8 + 24) * (64 + 6)  # padded row pitch (a multiple of 32 values) x rows
+    assert gbfd.gbfd_workspace_bytes(pw) >= gbfd.gbfd_workspace_bytes(p32) + 2 * 5 * 6 * plane * 4
+    bad = gbfd.make_params((64, 64, 64), precision="fp32")
+    bad.bc_z = 2
+    assert gbfd.gbfd_workspace_bytes(bad) == 0
 
 
 def test_init_rejects_null_and_misaligned_workspace(lib):
