@@ -383,7 +383,7 @@ int64_t gbfd_cnn_launch_count(const gbfd_cnn *c);
 const char *gbfd_cnn_last_error(const gbfd_cnn *c);
 /* Launch-shape options (tests; no counterpart in the paper).
  * GBFD_CNN_OPT_CONV_GRID: CTAs per convolution launch, each walking an equal
- * share of the 256-point tiles (0 = default, three per SM); a small value
+ * share of the 256-point tiles (0 = default, one per SM); a small value
  * makes every CTA loop over many tiles.  GBFD_CNN_OPT_WGRAD_PARTS: CTAs of
  * the weight-gradient sums, 1..296 (0 = default 296).  Results agree to
  * rounding whatever the values; out-of-range values -> INVALID_ARG. */

@@ -3,20 +3,27 @@
 // coarse solver state after each RK3 step, trained on the GPU.
 //
 // * Convolutions (forward, and the input gradient of the backward pass) are
-//   implicit GEMMs on the tcgen05 tensor cores: M = 128 grid points per tile,
-//   N = output channels, K = 27 taps x input channels; BF16 operands staged
-//   in shared memory as K-major core matrices, FP32 accumulators in TMEM.
-//   A tile of 8 x 16 x 2 points and its periodic halo is staged in shared
-//   memory once; the A operand of each tap is a shifted descriptor into it,
-//   so the 27 taps are issued back to back.  The B operand (weights) is
-//   resident in shared memory.  The input gradient is the same kernel with
-//   the weights transposed in channels and flipped in taps.
+//   implicit GEMMs on the tcgen05 tensor cores: M = 128 grid points per MMA,
+//   N = output channels, K = 27 taps x input channels; BF16 operands in
+//   shared memory as K-major core matrices, FP32 accumulators in TMEM.
+// * A persistent, warp-specialised CTA per SM: one warp loads each tile's
+//   input plus its periodic one-point halo with ONE TMA box into a
+//   double-buffered ring, one thread issues the tile's 27 taps as MMAs from
+//   shifted descriptors into one of two TMEM accumulator buffers, and four
+//   epilogue warps read the other buffer (bias, GELU or GELU', BF16 stores),
+//   so loads, MMAs and epilogues of consecutive tiles overlap.  The weights
+//   (B operand) stay in shared memory.  Activations are kept in a padded,
+//   chunk-major layout whose one-point frame holds the periodic copies, so a
+//   halo never wraps.  The input gradient is the same kernel with the
+//   weights transposed in channels and flipped in taps.
 // * The weight gradient sums over all grid points (K = points) on CUDA cores
 //   in FP32, split over CTAs and reduced in a fixed order (deterministic).
 // * MSE loss, Adam (FP32 master weights, BF16 copies in both GEMM layouts),
 //   input normalisation, the residual update of the solver state, and the
 //   centred box filter that makes training targets from fine-grid runs.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -80,209 +87,355 @@ __device__ __forceinline__ float gelu_grad(float h)
            h * expf(-0.5f * h * h) * 0.39894228040143268f;
 }
 
+// Activations live in a padded, chunk-major layout: act[c8][b][zp][yp][xp][8]
+// (BF16; c8 = channel / 8, padded coordinates xp = x + 1 in 0..n+1, the
+// outermost ones holding the periodic copies of the opposite faces), so that
+// a tile's one-point halo is one rectangular, in-bounds box and the 8
+// channels of one chunk of one point are 16 contiguous bytes.  Whoever writes
+// a point also writes its periodic copies.  Index below in units of 16-byte
+// chunks.
+__host__ __device__ __forceinline__ long long aidx(int c8, int b, int zp, int yp, int xp, int n,
+                                                   int B)
+{
+    const long long m = n + 2;
+    return ((((long long)c8 * B + b) * m + zp) * m + yp) * m + xp;
+}
+
+// Calls f(xp, yp, zp) for the padded position of interior point (x, y, z)
+// and for each of its periodic copies in the one-point frame (up to 8 at a
+// corner; n >= 2).
+template <class F>
+__device__ __forceinline__ void each_copy(int x, int y, int z, int n, F &&f)
+{
+    const int xs[2] = {x + 1, x == 0 ? n + 1 : 0}, nxs = (x == 0 || x == n - 1) ? 2 : 1;
+    const int ys[2] = {y + 1, y == 0 ? n + 1 : 0}, nys = (y == 0 || y == n - 1) ? 2 : 1;
+    const int zs[2] = {z + 1, z == 0 ? n + 1 : 0}, nzs = (z == 0 || z == n - 1) ? 2 : 1;
+    for (int iz = 0; iz < nzs; ++iz)
+        for (int iy = 0; iy < nys; ++iy)
+            for (int ix = 0; ix < nxs; ++ix)
+                f(xs[ix], ys[iy], zs[iz]);
+}
+
 struct ConvArgs {
-    const bf16 *x;       // [npts][CIN] channels-last input
     const bf16 *wB;      // [N][27*CIN] in core-matrix order
     const float *bias;   // [N]                      (EPI_GELU, EPI_LINEAR)
-    float *hsave;        // [npts][N] pre-activation (EPI_GELU)
-    bf16 *yb;            // [npts][N]                (EPI_GELU: GELU(h), EPI_DGELU: dh)
+    float *hsave;        // [npts][N] pre-activation (EPI_GELU; NULL: not kept)
+    bf16 *yb;            // padded chunk-major output (EPI_GELU: GELU(h), EPI_DGELU: dh)
     float *yf;           // [npts][8]                (EPI_LINEAR)
     const float *hprev;  // [npts][N]                (EPI_DGELU)
     int n;               // grid side
     int npts;            // batch * n^3
+    int B;               // samples allocated in the padded arrays
     int *dev_error;
 };
 
 // A conv tile is TXT x TYT points in each of ZB consecutive z planes: one
 // M = 128 MMA row block per plane, row r = point (x0 + r % TXT, y0 + r / TXT).
-// The tile's input plus its one-point periodic halo is staged in shared
-// memory once, as 16-byte chunks of 8 channels: chunk c of halo point
-// (hx, hy, hz) at c * CS + ((hz * HY + hy) * HX + hx) * 16.  For tap
-// (dx, dy, dz) the A operand of plane zb is then the same buffer at a shifted
-// start: core matrices of 8 x-consecutive rows (16-byte row stride), row
-// groups one halo row apart (SBO = HX * 16), K chunks CS apart (LBO), so all
-// 27 taps are issued back to back without any further data movement.
+// Its input plus the one-point halo, HX x HY x HZ points of CIN channels, is
+// ONE TMA box of the padded chunk-major input, (8 channels, HX, HY, HZ,
+// CIN / 8 chunks): in shared memory chunk c of halo point (hx, hy, hz) sits at
+// c * CS + ((hz * HY + hy) * HX + hx) * 16.  For tap (dx, dy, dz) the A
+// operand of plane zb is then the same buffer at a shifted start: core
+// matrices of 8 x-consecutive rows (16-byte row stride), row groups one halo
+// row apart (SBO = HX * 16), K chunks CS apart (LBO), so the 27 taps are
+// issued back to back without any further data movement.
 constexpr int TXT = 8, TYT = 16, ZB = 2;
 constexpr int HX = TXT + 2, HY = TYT + 2, HZ = ZB + 2, HPTS = HX * HY * HZ;
 static_assert(TXT * TYT == MT, "one MMA row block per tile plane");
+
+// Warp roles of the convolution CTA (one per SM, persistent over tiles):
+// warp 0 issues the TMA halo loads, warp 1 the MMAs (and owns the TMEM
+// allocation), warps 2-5 are the epilogue (warp w reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31).
+constexpr int CONV_THREADS = 192;
+constexpr int NSTAGE = 2;  // halo buffers
+constexpr int NACC = 2;    // TMEM accumulator buffers
 
 template <int CIN, int N, int EPI>
 struct ConvSmem {
     static constexpr int K = TAPS * CIN;
     static constexpr int CH8 = CIN / 8;
     static constexpr int B_BYTES = N * K * 2;
-    // chunk stride: 32 bytes past a 128-byte multiple, so the 16-byte
-    // stores of one point's chunks fall in different banks
-    static constexpr int CS = (HPTS * 16 + 127) / 128 * 128 + 32;
-    static constexpr int A_OFF = (B_BYTES + 1023) / 1024 * 1024;
+    static constexpr int CS = HPTS * 16;  // chunk stride of the TMA box
     static constexpr int A_BYTES = CH8 * CS;
-    static constexpr int BAR_OFF = (A_OFF + A_BYTES + 15) / 16 * 16;
-    static constexpr int BYTES = BAR_OFF + 32;
-    static constexpr int TCOLS = ZB * N <= 32 ? 32 : 64;  // TMEM accumulator columns
+    static constexpr int A_OFF = (B_BYTES + 1023) / 1024 * 1024;
+    static constexpr int A_PITCH = (A_BYTES + 1023) / 1024 * 1024;
+    static constexpr int BAR_OFF = A_OFF + NSTAGE * A_PITCH;
+    // full[2], empty[2], acc_full[2], acc_empty[2], TMEM address, abort flag,
+    // issue / consume counts for the drain
+    static constexpr int BYTES = BAR_OFF + 8 * 8 + 32;
+    static constexpr int ACC_COLS = ZB * N;  // one accumulator buffer
+    static constexpr int TCOLS = NACC * ACC_COLS <= 32 ? 32 : (NACC * ACC_COLS <= 64 ? 64 : 128);
+    static_assert(CS % 16 == 0 && (CS >> 4) < (1 << 14), "descriptor offsets");
 };
 
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2, int c3, int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(tiled::smem_u32(dst)),
+        "l"((uint64_t)map), "r"(tiled::smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tiled::smem_u32(bar))
+                 : "memory");
+}
+
+// Bounded wait that also gives up when another role has raised the CTA's
+// abort flag; a wait that runs out (about 2 s) raises it.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    if (tiled::mbar_try_wait(bar, parity))
+        return true;
+    const uint64_t t0 = tiled::global_ns();
+    while (true) {
+        if (tiled::mbar_try_wait(bar, parity))
+            return true;
+        if (*abort)
+            return false;
+        if (tiled::global_ns() - t0 > 2000000000ull) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tile_origin(int tile, int n, int &x0, int &y0, int &z0, int &b)
+{
+    const int tx_n = (n + TXT - 1) / TXT, ty_n = (n + TYT - 1) / TYT, tz_n = (n + ZB - 1) / ZB;
+    int r = tile;
+    x0 = (r % tx_n) * TXT;
+    r /= tx_n;
+    y0 = (r % ty_n) * TYT;
+    r /= ty_n;
+    z0 = (r % tz_n) * ZB;
+    b = r / tz_n;
+}
+
 template <int CIN, int N, int EPI>
-__global__ void __launch_bounds__(NTHR) k_conv_tc(const ConvArgs a)
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap xmap, const ConvArgs a)
 {
     using SM = ConvSmem<CIN, N, EPI>;
-    constexpr int K = SM::K;
     constexpr int KSTEPS = CIN / 16;  // MMAs per tap and plane
-    constexpr int CH8 = SM::CH8;
-    constexpr int SBO_B = K * 16;
+    constexpr int SBO_B = SM::K * 16;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sB = smem;
     unsigned char *sA = smem + SM::A_OFF;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM::BAR_OFF);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + SM::BAR_OFF + 16);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + SM::BAR_OFF);
+    uint64_t *empty = full + NSTAGE;
+    uint64_t *accf = empty + NSTAGE;
+    uint64_t *acce = accf + NACC;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + NACC);
+    volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
+    int *cnt = reinterpret_cast<int *>(tslot + 2);  // issued, consumed, committed, drained
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
-    for (int i = threadIdx.x; i < SM::B_BYTES / 16; i += NTHR)
+    // the weights (B operand) stay in shared memory for the whole launch
+    for (int i = threadIdx.x; i < SM::B_BYTES / 16; i += CONV_THREADS)
         reinterpret_cast<uint4 *>(sB)[i] = reinterpret_cast<const uint4 *>(a.wB)[i];
     if (threadIdx.x == 0) {
-        tiled::mbar_init(&bars[0], 1);
+        for (int s = 0; s < NSTAGE; ++s) {
+            tiled::mbar_init(&full[s], 1);
+            tiled::mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < NACC; ++s) {
+            tiled::mbar_init(&accf[s], 1);
+            tiled::mbar_init(&acce[s], 4);  // one arrival per epilogue warp
+        }
+        *abort = 0;
+        cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
         tiled::fence_mbar_init();
     }
-    if (threadIdx.x < 32)
+    if (warp == 1)
         tc::tmem_alloc(tslot, SM::TCOLS);
+    tc::fence_smem_to_async();  // the weights, written by the generic proxy, feed the MMAs
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tslot;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(MT, N);
-    const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
-    uint32_t ph = 0;
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot);
     const int n = a.n;
     const long long n3 = (long long)n * n * n;
     const int nb = (int)(a.npts / n3);
-    const int tx_n = (n + TXT - 1) / TXT, ty_n = (n + TYT - 1) / TYT, tz_n = (n + ZB - 1) / ZB;
-    const int ntiles = nb * tz_n * ty_n * tx_n;
-    bool timeout = false;
+    const int ntiles = nb * ((n + ZB - 1) / ZB) * ((n + TYT - 1) / TYT) * ((n + TXT - 1) / TXT);
 
-#pragma unroll 1
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int r = tile;
-        const int x0 = (r % tx_n) * TXT;
-        r /= tx_n;
-        const int y0 = (r % ty_n) * TYT;
-        r /= ty_n;
-        const int z0 = (r % tz_n) * ZB;
-        const int b = r / tz_n;
-        // the halo box, periodic (tiles may reach past n on small grids)
-        const bf16 *xb = a.x + (long long)b * n3 * CIN;
-        // fully unrolled so that all of a thread's loads are in flight at once
-        constexpr int NLD = (HPTS * CH8 + NTHR - 1) / NTHR;
-#pragma unroll
-        for (int it = 0; it < NLD; ++it) {
-            const int i = threadIdx.x + it * NTHR;
-            if (i >= HPTS * CH8)
-                break;
-            const int c = i % CH8, hp = i / CH8;
-            const int hx = hp % HX, hy = (hp / HX) % HY, hz = hp / (HX * HY);
-            const int gx = (x0 - 1 + hx + n) % n, gy = (y0 - 1 + hy + n) % n;
-            const int gz = (z0 - 1 + hz + n) % n;
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(
-                                      xb + (((long long)gz * n + gy) * n + gx) * CIN) +
-                                  c);
-            *reinterpret_cast<uint4 *>(sA + c * SM::CS + hp * 16) = v;
+    if (warp == 0) {
+        // producer: one halo box per tile into the stage the MMAs freed
+        if (lane == 0) {
+            int i = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                const int s = i % NSTAGE;
+                if (!wait_or_abort(&empty[s], ((i / NSTAGE) & 1) ^ 1, abort))
+                    break;
+                int x0, y0, z0, b;
+                tile_origin(tile, n, x0, y0, z0, b);
+                tiled::mbar_expect_tx(&full[s], SM::A_BYTES);
+                // padded coordinates of the halo's first point: (x0 - 1) + 1
+                tma_load_5d(sA + s * SM::A_PITCH, &xmap, &full[s], 0, x0, y0, b * (n + 2) + z0,
+                            0);
+                cnt[0] = i + 1;
+            }
         }
-        // the halo writes (generic proxy) become visible to the tensor core;
-        // every thread is done reading the previous tile's accumulators
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc::fence_after_sync();
+    } else if (warp == 1) {
+        // MMA issuer: 27 taps x ZB planes x KSTEPS per tile into one of two
+        // accumulator buffers; the commits free the halo stage and hand the
+        // accumulators to the epilogue
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(MT, N);
+            const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
+            int i = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                const int s = i % NSTAGE, acc = i % NACC;
+                if (!wait_or_abort(&full[s], (i / NSTAGE) & 1, abort))
+                    break;
+                cnt[1] = i + 1;
+                if (!wait_or_abort(&acce[acc], ((i / NACC) & 1) ^ 1, abort))
+                    break;
+                tc::fence_after_sync();
+                const uint32_t abase = sA_u32 + s * SM::A_PITCH;
 #pragma unroll 1
-            for (int zb = 0; zb < ZB; ++zb)
+                for (int zb = 0; zb < ZB; ++zb)
 #pragma unroll 1
-                for (int tap = 0; tap < TAPS; ++tap) {
-                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // 0..2: offset + 1
-                    const uint32_t a0 =
-                        sA_u32 + (uint32_t)((((zb + dz) * HY + dy) * HX + dx) * 16);
+                    for (int tap = 0; tap < TAPS; ++tap) {
+                        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // offset + 1
+                        const uint32_t a0 =
+                            abase + (uint32_t)((((zb + dz) * HY + dy) * HX + dx) * 16);
 #pragma unroll
-                    for (int s = 0; s < KSTEPS; ++s) {
-                        const uint64_t ad = tc::smem_desc(a0 + 2 * s * SM::CS, SM::CS, HX * 16);
-                        const uint64_t bd =
-                            tc::smem_desc(sB_u32 + (tap * KSTEPS + s) * 256, 128, SBO_B);
-                        tc::mma_bf16(tmem + zb * N, ad, bd, idesc, (tap > 0 || s > 0) ? 1u : 0u);
+                        for (int k = 0; k < KSTEPS; ++k) {
+                            const uint64_t ad = tc::smem_desc(a0 + 2 * k * SM::CS, SM::CS, HX * 16);
+                            const uint64_t bd =
+                                tc::smem_desc(sB_u32 + (tap * KSTEPS + k) * 256, 128, SBO_B);
+                            tc::mma_bf16(tmem + acc * SM::ACC_COLS + zb * N, ad, bd, idesc,
+                                         (tap > 0 || k > 0) ? 1u : 0u);
+                        }
                     }
-                }
-            tc::commit(&bars[0]);
+                tc::commit(&empty[s]);
+                tc::commit(&accf[acc]);
+                cnt[2] = i + 1;
+            }
         }
-        if (!tiled::mbar_wait(&bars[0], ph))
-            timeout = true;
-        ph ^= 1;
-        tc::fence_after_sync();
-        const int lx = threadIdx.x % TXT, ly = threadIdx.x / TXT;
-        const int x = x0 + lx, y = y0 + ly;
-        const uint32_t taddr = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
-#pragma unroll 1
-        for (int zb = 0; zb < ZB; ++zb) {
-            float acc[32];
-            tc::tmem_ld16(taddr + zb * N, acc);
-            if (N > 16)
-                tc::tmem_ld16(taddr + zb * N + 16, acc + 16);
-            const int z = z0 + zb;
-            const bool valid = x < n && y < n && z < n;
-            const long long p = (long long)b * n3 + ((long long)z * n + y) * n + x;
-            if (valid && !timeout) {
-                if (EPI == EPI_GELU) {
-                    float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * N);
-                    uint4 *yo = reinterpret_cast<uint4 *>(a.yb + p * N);
+    } else {
+        // epilogue: TMEM -> registers, release the accumulators, then bias /
+        // GELU / GELU' and the stores (with the periodic copies)
+        const int q = warp % 4;
+        const int r = q * 32 + lane;  // row of the M block = TMEM lane
+        const int lx = r % TXT, ly = r / TXT;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        int i = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int acc = i % NACC;
+            // one lane waits, the warp follows it (the TMEM loads below are
+            // warp-collective)
+            int ok = 0;
+            if (lane == 0)
+                ok = wait_or_abort(&accf[acc], (i / NACC) & 1, abort);
+            if (!__shfl_sync(0xffffffffu, ok, 0))
+                break;
+            // the other lanes observe the completed phase too (it cannot
+            // move on before this warp releases the buffer)
+            if (lane != 0)
+                (void)tiled::mbar_try_wait(&accf[acc], (i / NACC) & 1);
+            tc::fence_after_sync();
+            float v[ZB][N];
+#pragma unroll
+            for (int zb = 0; zb < ZB; ++zb) {
+                tc::tmem_ld16(tl + acc * SM::ACC_COLS + zb * N, v[zb]);
+                if constexpr (N > 16)
+                    tc::tmem_ld16(tl + acc * SM::ACC_COLS + zb * N + 16, v[zb] + 16);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&acce[acc]);
+            if (warp == 2 && lane == 0)
+                cnt[3] = i + 1;
+            int x0, y0, z0, b;
+            tile_origin(tile, n, x0, y0, z0, b);
+            const int x = x0 + lx, y = y0 + ly;
+#pragma unroll
+            for (int zb = 0; zb < ZB; ++zb) {
+                const int z = z0 + zb;
+                if (x >= n || y >= n || z >= n)
+                    continue;
+                const long long p = (long long)b * n3 + ((long long)z * n + y) * n + x;
+                if constexpr (EPI == EPI_LINEAR) {
+                    float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
+                    yo[0] = make_float4(v[zb][0] + __ldg(a.bias + 0), v[zb][1] + __ldg(a.bias + 1),
+                                        v[zb][2] + __ldg(a.bias + 2), v[zb][3] + __ldg(a.bias + 3));
+                    yo[1] = make_float4(v[zb][4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
+                } else {
+                    uint4 out[N / 8];
 #pragma unroll
                     for (int c = 0; c < N; c += 8) {
                         float h[8];
+                        if constexpr (EPI == EPI_GELU) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            h[i] = acc[c + i] + __ldg(a.bias + c + i);
-                        hs[c / 4] = make_float4(h[0], h[1], h[2], h[3]);
-                        hs[c / 4 + 1] = make_float4(h[4], h[5], h[6], h[7]);
+                            for (int j = 0; j < 8; ++j)
+                                h[j] = v[zb][c + j] + __ldg(a.bias + c + j);
+                            if (a.hsave) {
+                                float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * N + c);
+                                hs[0] = make_float4(h[0], h[1], h[2], h[3]);
+                                hs[1] = make_float4(h[4], h[5], h[6], h[7]);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                h[j] = gelu(h[j]);
+                        } else {
+                            const float4 *hp = reinterpret_cast<const float4 *>(a.hprev + p * N + c);
+                            const float4 h0 = __ldg(hp), h1 = __ldg(hp + 1);
+                            const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                h[j] = v[zb][c + j] * gelu_grad(hv[j]);
+                        }
                         __nv_bfloat162 o[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            o[i] = __floats2bfloat162_rn(gelu(h[2 * i]), gelu(h[2 * i + 1]));
-                        yo[c / 8] = *reinterpret_cast<uint4 *>(o);
+                        for (int j = 0; j < 4; ++j)
+                            o[j] = __floats2bfloat162_rn(h[2 * j], h[2 * j + 1]);
+                        out[c / 8] = *reinterpret_cast<uint4 *>(o);
                     }
-                } else if (EPI == EPI_LINEAR) {
-                    float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
-                    yo[0] = make_float4(acc[0] + __ldg(a.bias + 0), acc[1] + __ldg(a.bias + 1),
-                                        acc[2] + __ldg(a.bias + 2), acc[3] + __ldg(a.bias + 3));
-                    yo[1] = make_float4(acc[4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
-                } else {
-                    const float4 *hp = reinterpret_cast<const float4 *>(a.hprev + p * N);
-                    uint4 *yo = reinterpret_cast<uint4 *>(a.yb + p * N);
+                    uint4 *yb = reinterpret_cast<uint4 *>(a.yb);
+                    each_copy(x, y, z, n, [&](int xp, int yp, int zp) {
 #pragma unroll
-                    for (int c = 0; c < N; c += 8) {
-                        const float4 h0 = __ldg(hp + c / 4), h1 = __ldg(hp + c / 4 + 1);
-                        const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                        __nv_bfloat162 o[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            o[i] = __floats2bfloat162_rn(acc[c + 2 * i] * gelu_grad(h[2 * i]),
-                                                         acc[c + 2 * i + 1] * gelu_grad(h[2 * i + 1]));
-                        yo[c / 8] = *reinterpret_cast<uint4 *>(o);
-                    }
+                        for (int c8 = 0; c8 < N / 8; ++c8)
+                            yb[aidx(c8, b, zp, yp, xp, n, a.B)] = out[c8];
+                    });
                 }
             }
         }
-        tc::fence_before_sync();
-        if (__syncthreads_or(timeout)) {
-            if (threadIdx.x == 0)
-                atomicExch(a.dev_error, 2);
-            break;
-        }
     }
     __syncthreads();
+    if (*abort) {
+        // a wait gave up: let the copies and MMAs still in flight land
+        // before the shared memory and TMEM go away (bounded, abort ignored)
+        if (threadIdx.x == 0) {
+            atomicExch(a.dev_error, 2);
+            volatile int never = 0;
+            for (int j = cnt[1]; j < cnt[0]; ++j)
+                (void)wait_or_abort(&full[j % NSTAGE], (j / NSTAGE) & 1, &never);
+            for (int j = cnt[3]; j < cnt[2]; ++j)
+                (void)wait_or_abort(&accf[j % NACC], (j / NACC) & 1, &never);
+        }
+        __syncthreads();
+    }
     tc::fence_after_sync();
-    if (threadIdx.x < 32)
+    if (warp == 1)
         tc::tmem_dealloc(tmem, SM::TCOLS);
 }
 
 // Weight (and bias) gradient of one layer, summed over this CTA's share of
 // the points: dW[co][tap][ci] += dY[p][co] X[p + tap][ci]; db[co] += dY[p][co].
+// dY and X are padded chunk-major activations (B samples allocated), so the
+// neighbour p + tap is read without any wrap arithmetic.
 template <int CO, int CI>
 __global__ void __launch_bounds__(TAPS *(CI / 4)) k_wgrad(const bf16 *__restrict__ dY,
                                                           const bf16 *__restrict__ X, int n,
-                                                          int npts, float *__restrict__ part)
+                                                          int npts, int B, float *__restrict__ part)
 {
     constexpr int NT = TAPS * (CI / 4);
     __shared__ __align__(16) bf16 sdy[MT * CO];
@@ -302,11 +455,20 @@ __global__ void __launch_bounds__(TAPS *(CI / 4)) k_wgrad(const bf16 *__restrict
     const long long chunk = ((long long)npts + gridDim.x - 1) / gridDim.x;
     const long long p0 = chunk * blockIdx.x;
     const long long p1 = min((long long)npts, p0 + chunk);
+    const uint4 *dY4 = reinterpret_cast<const uint4 *>(dY);
     for (long long base = p0; base < p1; base += MT) {
         const int cnt = (int)min((long long)MT, p1 - base);
         __syncthreads();
-        for (int i = t; i < cnt * CO / 8; i += NT)
-            reinterpret_cast<uint4 *>(sdy)[i] = __ldg(reinterpret_cast<const uint4 *>(dY + base * CO) + i);
+        for (int i = t; i < cnt * (CO / 8); i += NT) {
+            const int j = i / (CO / 8), c8 = i % (CO / 8);
+            const long long p = base + j;
+            const int b = (int)(p / n3);
+            int r = (int)(p - (long long)b * n3);
+            const int z = r / n2;
+            r -= z * n2;
+            reinterpret_cast<uint4 *>(sdy)[i] =
+                __ldg(dY4 + aidx(c8, b, z + 1, r / n + 1, r % n + 1, n, B));
+        }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
             const long long p = base + j;
@@ -316,15 +478,9 @@ __global__ void __launch_bounds__(TAPS *(CI / 4)) k_wgrad(const bf16 *__restrict
             r -= z * n2;
             const int y = r / n;
             const int x = r - y * n;
-            int zz = z + dz, yy = y + dyo, xx = x + dx;
-            zz += zz < 0 ? n : 0;
-            zz -= zz >= n ? n : 0;
-            yy += yy < 0 ? n : 0;
-            yy -= yy >= n ? n : 0;
-            xx += xx < 0 ? n : 0;
-            xx -= xx >= n ? n : 0;
-            const long long q = (long long)b * n3 + ((long long)zz * n + yy) * n + xx;
-            const uint2 xr = __ldg(reinterpret_cast<const uint2 *>(X + q * CI + 4 * cq));
+            const long long q =
+                aidx(cq / 2, b, z + 1 + dz, y + 1 + dyo, x + 1 + dx, n, B) * 8 + (cq % 2) * 4;
+            const uint2 xr = __ldg(reinterpret_cast<const uint2 *>(X + q));
             const float2 x01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&xr.x));
             const float2 x23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&xr.y));
             const float xv[4] = {x01.x, x01.y, x23.x, x23.y};
@@ -367,31 +523,43 @@ __global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int c
     g[i] = s;
 }
 
-// Normalised, channels-last, zero-padded BF16 input of layer 1 from compact
-// FP32 states [batch][5][n^3] (nf physical fields present).
-__global__ void k_input_compact(const float *__restrict__ xs, int nf, int n3, int npts,
+// Normalised BF16 input of layer 1 (C0 = 16 channels, zero beyond the nf
+// physical fields) at point (b, x, y, z) into the padded chunk-major x0,
+// with its periodic copies.
+__device__ __forceinline__ void put_input(bf16 *x0, const float *v, int b, int x, int y, int z,
+                                          int n, int B)
+{
+    __nv_bfloat162 o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        o[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const uint4 c0 = reinterpret_cast<uint4 *>(o)[0], c1 = reinterpret_cast<uint4 *>(o)[1];
+    uint4 *dst = reinterpret_cast<uint4 *>(x0);
+    each_copy(x, y, z, n, [&](int xp, int yp, int zp) {
+        dst[aidx(0, b, zp, yp, xp, n, B)] = c0;
+        dst[aidx(1, b, zp, yp, xp, n, B)] = c1;
+    });
+}
+
+// Layer-1 input from compact FP32 states [batch][5][n^3] (nf fields present).
+__global__ void k_input_compact(const float *__restrict__ xs, int nf, int n, int npts, int B,
                                 const float *__restrict__ mean, const float *__restrict__ stdv,
                                 bf16 *__restrict__ x0)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts)
         return;
+    const int n3 = n * n * n;
     const int b = p / n3, r = p - b * n3;
-    __nv_bfloat162 o[8];
     float v[C0];
 #pragma unroll
     for (int c = 0; c < C0; ++c)
         v[c] = (c < nf) ? (xs[((long long)b * NC + c) * n3 + r] - mean[c]) / stdv[c] : 0.f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        o[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    uint4 *dst = reinterpret_cast<uint4 *>(x0 + (long long)p * C0);
-    dst[0] = reinterpret_cast<uint4 *>(o)[0];
-    dst[1] = reinterpret_cast<uint4 *>(o)[1];
+    put_input(x0, v, b, r % n, (r / n) % n, r / (n * n), n, B);
 }
 
 // Same from a solver context's padded FP32 state (one box, batch 1).
-__global__ void k_input_state(const float *__restrict__ st, Layout L, int nf,
+__global__ void k_input_state(const float *__restrict__ st, Layout L, int nf, int B,
                               const float *__restrict__ mean, const float *__restrict__ stdv,
                               bf16 *__restrict__ x0)
 {
@@ -400,17 +568,11 @@ __global__ void k_input_state(const float *__restrict__ st, Layout L, int nf,
     if (p >= n * n * n)
         return;
     const int z = p / (n * n), y = (p / n) % n, x = p % n;
-    __nv_bfloat162 o[8];
     float v[C0];
 #pragma unroll
     for (int c = 0; c < C0; ++c)
         v[c] = (c < nf) ? (st[lidx(L, c, z, y, x)] - mean[c]) / stdv[c] : 0.f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        o[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    uint4 *dst = reinterpret_cast<uint4 *>(x0 + (long long)p * C0);
-    dst[0] = reinterpret_cast<uint4 *>(o)[0];
-    dst[1] = reinterpret_cast<uint4 *>(o)[1];
+    put_input(x0, v, 0, x, y, z, n, B);
 }
 
 // state += std_out * y (the de-normalised predicted residual), ghosts kept.
@@ -444,9 +606,10 @@ __global__ void k_output_compact(const float *__restrict__ y, int n3, int npts,
 // sums per block (FP64) and dY3 = 2 (y - t) / count in BF16, channels-last.
 __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ xs,
                        const float *__restrict__ ts, const float *__restrict__ sout, int nf,
-                       int n3, int npts, float inv_count, bf16 *__restrict__ dy3,
+                       int n, int npts, int B, float inv_count, bf16 *__restrict__ dy3,
                        double *__restrict__ part)
 {
+    const int n3 = n * n * n;
     __shared__ double sh[256];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
@@ -464,13 +627,8 @@ __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ xs
             l += (double)e * (double)e;
             d[c] = 2.f * e * inv_count;
         }
-        __nv_bfloat162 o[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            o[i] = __floats2bfloat162_rn(d[2 * i], d[2 * i + 1]);
-        uint4 *dst = reinterpret_cast<uint4 *>(dy3 + (long long)p * C3);
-        dst[0] = reinterpret_cast<uint4 *>(o)[0];
-        dst[1] = reinterpret_cast<uint4 *>(o)[1];
+        // dY3 into the padded chunk-major layout, with its periodic copies
+        put_input(dy3, d, b, r % n, (r / n) % n, r / (n * n), n, B);
     }
     sh[threadIdx.x] = l;
     __syncthreads();
@@ -594,7 +752,9 @@ struct gbfd_cnn {
     int *derr;
     int adam_t;
     int grid_conv;      // CTAs per convolution launch (each walks its share of the tiles)
-    int grid_default;   // three per SM
+    int grid_default;   // one per SM
+    // TMA maps of the convolution inputs (padded chunk-major activations)
+    CUtensorMap map_x0, map_a1, map_a2, map_dy3, map_dh2;
     int64_t launches;
     char err[512];
 };
@@ -632,12 +792,14 @@ CnnPlan plan_for(int n, int batch)
 {
     CnnPlan pl;
     const size_t np = (size_t)batch * n * n * n;
+    const size_t npad = (size_t)batch * (n + 2) * (n + 2) * (n + 2);  // padded activations
     const size_t sizes[] = {
         kParams * 4, kParams * 4, kParams * 4, kParams * 4,  // w m v g
         (size_t)CH * TAPS * C0 * 2, (size_t)CH * TAPS * CH * 2, (size_t)C3 * TAPS * CH * 2,  // fwd
         (size_t)C0 * TAPS * CH * 2, (size_t)CH * TAPS * CH * 2, (size_t)CH * TAPS * C3 * 2,  // bwd
         CH * 4, CH * 4, C3 * 4, 64 * 4,                                   // biases, norm
-        np * C0 * 2, np * CH * 2, np * CH * 2, np * C3 * 2, np * CH * 2, np * CH * 2,  // bf16 acts
+        npad * C0 * 2, npad * CH * 2, npad * CH * 2, npad * C3 * 2, npad * CH * 2,
+        npad * CH * 2,                                                    // bf16 acts
         np * CH * 4, np * CH * 4, np * 8 * 4,                             // h1 h2 y3
         (size_t)kWgradParts * (CH * TAPS * CH + CH) * 4,                 // parts
         ((np + 255) / 256 + 8) * 8, 64, 256};
@@ -653,7 +815,7 @@ CnnPlan plan_for(int n, int batch)
 }
 
 template <int CIN, int N, int EPI>
-cudaError_t conv(gbfd_cnn *c, const ConvArgs &a)
+cudaError_t conv(gbfd_cnn *c, const CUtensorMap &xmap, const ConvArgs &a)
 {
     using SM = ConvSmem<CIN, N, EPI>;
     auto k = k_conv_tc<CIN, N, EPI>;
@@ -663,11 +825,43 @@ cudaError_t conv(gbfd_cnn *c, const ConvArgs &a)
     const int n = a.n;
     const long long ntiles = (long long)(a.npts / ((long long)n * n * n)) * ((n + ZB - 1) / ZB) *
                              ((n + TYT - 1) / TYT) * ((n + TXT - 1) / TXT);
-    // three CTAs per SM walking the tiles (measured faster than sizing the
-    // grid to the resident CTAs)
-    k<<<(int)std::min<long long>(ntiles, c->grid_conv), NTHR, SM::BYTES, c->stream>>>(a);
+    // persistent: one CTA per SM walking the tiles (fewer on request)
+    k<<<(int)std::min<long long>(ntiles, c->grid_conv), CONV_THREADS, SM::BYTES, c->stream>>>(xmap,
+                                                                                             a);
     c->launches++;
     return cudaGetLastError();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// TMA map of a padded chunk-major activation of cin channels (B samples on
+// an n^3 grid): dims (8 channels, n + 2, n + 2, (n + 2) B, cin / 8), box =
+// one conv tile's halo, (8, HX, HY, HZ, cin / 8).
+bool encode_act_map(CUtensorMap *m, const bf16 *base, int n, int B, int cin)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn)
+        return false;
+    const cuuint64_t np2 = (cuuint64_t)(n + 2);
+    const cuuint64_t dims[5] = {8, np2, np2, np2 * (cuuint64_t)B, (cuuint64_t)(cin / 8)};
+    const cuuint64_t strides[4] = {16, np2 * 16, np2 * np2 * 16, np2 * np2 * np2 * B * 16};
+    const cuuint32_t box[5] = {8, HX, HY, HZ, (cuuint32_t)(cin / 8)};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 cudaError_t pack(gbfd_cnn *c, const float *g, float lr)
@@ -693,43 +887,43 @@ cudaError_t pack(gbfd_cnn *c, const float *g, float lr)
     return cudaGetLastError();
 }
 
-// forward of `npts` points whose layer-1 input is already in x0
-cudaError_t forward(gbfd_cnn *c, int npts)
+// forward of `npts` points whose layer-1 input is already in x0; `keep`
+// saves the pre-activations for the backward pass (training only)
+cudaError_t forward(gbfd_cnn *c, int npts, bool keep)
 {
     ConvArgs a;
     memset(&a, 0, sizeof a);
     a.n = c->n;
     a.npts = npts;
+    a.B = c->batch;
     a.dev_error = c->derr;
-    a.x = c->x0;
     a.wB = c->fwd[0];
     a.bias = c->bias[0];
-    a.hsave = c->h1;
+    a.hsave = keep ? c->h1 : nullptr;
     a.yb = c->a1;
-    cudaError_t e = conv<C0, CH, EPI_GELU>(c, a);
+    cudaError_t e = conv<C0, CH, EPI_GELU>(c, c->map_x0, a);
     if (e != cudaSuccess)
         return e;
-    a.x = c->a1;
     a.wB = c->fwd[1];
     a.bias = c->bias[1];
-    a.hsave = c->h2;
+    a.hsave = keep ? c->h2 : nullptr;
     a.yb = c->a2;
-    e = conv<CH, CH, EPI_GELU>(c, a);
+    e = conv<CH, CH, EPI_GELU>(c, c->map_a1, a);
     if (e != cudaSuccess)
         return e;
-    a.x = c->a2;
     a.wB = c->fwd[2];
     a.bias = c->bias[2];
     a.hsave = nullptr;
     a.yb = nullptr;
     a.yf = c->y3;
-    return conv<CH, C3, EPI_LINEAR>(c, a);
+    return conv<CH, C3, EPI_LINEAR>(c, c->map_a2, a);
 }
 
 template <int CO, int CI>
 cudaError_t wgrad(gbfd_cnn *c, const bf16 *dY, const bf16 *X, int npts, float *g)
 {
-    k_wgrad<CO, CI><<<c->nparts, TAPS * (CI / 4), 0, c->stream>>>(dY, X, c->n, npts, c->parts);
+    k_wgrad<CO, CI><<<c->nparts, TAPS * (CI / 4), 0, c->stream>>>(dY, X, c->n, npts, c->batch,
+                                                                    c->parts);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -745,7 +939,7 @@ cudaError_t backward(gbfd_cnn *c, const float *xs, const float *ts, int nf, int 
     const int n3 = c->n * c->n * c->n, npts = batch * n3;
     const int blocks = (npts + 255) / 256;
     const float *sout = c->norm + 10;
-    k_loss<<<blocks, 256, 0, c->stream>>>(c->y3, xs, ts, sout, nf, n3, npts,
+    k_loss<<<blocks, 256, 0, c->stream>>>(c->y3, xs, ts, sout, nf, c->n, npts, c->batch,
                                           1.0f / ((float)NC * npts), c->dy3, c->lparts);
     k_sum_double<<<1, 256, 0, c->stream>>>(c->lparts, blocks, c->loss);
     c->launches += 2;
@@ -761,22 +955,21 @@ cudaError_t backward(gbfd_cnn *c, const float *xs, const float *ts, int nf, int 
     a.n = c->n;
     a.npts = npts;
     a.dev_error = c->derr;
-    a.x = c->dy3;
+    a.B = c->batch;
     a.wB = c->bwd[2];
     a.hprev = c->h2;
     a.yb = c->dh2;
-    e = conv<C3, CH, EPI_DGELU>(c, a);
+    e = conv<C3, CH, EPI_DGELU>(c, c->map_dy3, a);
     if (e != cudaSuccess)
         return e;
     // layer 2
     e = wgrad<CH, CH>(c, c->dh2, c->a1, npts, c->g + poff(1));
     if (e != cudaSuccess)
         return e;
-    a.x = c->dh2;
     a.wB = c->bwd[1];
     a.hprev = c->h1;
     a.yb = c->dh1;
-    e = conv<CH, CH, EPI_DGELU>(c, a);
+    e = conv<CH, CH, EPI_DGELU>(c, c->map_dh2, a);
     if (e != cudaSuccess)
         return e;
     // layer 1: weight gradient only
@@ -868,7 +1061,17 @@ gbfd_status gbfd_cnn_init(int n, int batch, void *workspace, size_t workspace_by
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    c->grid_conv = c->grid_default = 3 * (sms > 0 ? sms : 1);
+    c->grid_conv = c->grid_default = sms > 0 ? sms : 1;
+    if (e == cudaSuccess &&
+        !(encode_act_map(&c->map_x0, c->x0, n, batch, C0) &&
+          encode_act_map(&c->map_a1, c->a1, n, batch, CH) &&
+          encode_act_map(&c->map_a2, c->a2, n, batch, CH) &&
+          encode_act_map(&c->map_dy3, c->dy3, n, batch, C3) &&
+          encode_act_map(&c->map_dh2, c->dh2, n, batch, CH))) {
+        cerr(nullptr, "cnn init: TMA descriptor encoding failed");
+        delete c;
+        return GBFD_ERR_CUDA;
+    }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->ws, 0, pl.total, c->stream);
     // identity normalisation until set
@@ -1018,11 +1221,11 @@ gbfd_status gbfd_cnn_forward(gbfd_cnn *c, const float *xs, int nf, int batch, fl
         return GBFD_ERR_INVALID_ARG;
     }
     const int n3 = c->n * c->n * c->n, npts = batch * n3;
-    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, n3, npts, c->norm,
-                                                                c->norm + 5, c->x0);
+    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, c->n, npts, c->batch,
+                                                                c->norm, c->norm + 5, c->x0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = forward(c, npts);
+        e = forward(c, npts, false);
     if (e == cudaSuccess) {
         k_output_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(c->y3, n3, npts, ys);
         e = cudaGetLastError();
@@ -1042,12 +1245,12 @@ gbfd_status gbfd_cnn_gradients(gbfd_cnn *c, const float *xs, const float *ts, in
         return GBFD_ERR_INVALID_ARG;
     }
     const int n3 = c->n * c->n * c->n, npts = batch * n3;
-    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, n3, npts, c->norm,
-                                                                c->norm + 5, c->x0);
+    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, c->n, npts, c->batch,
+                                                                c->norm, c->norm + 5, c->x0);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = forward(c, npts);
+        e = forward(c, npts, true);
     if (e == cudaSuccess)
         e = backward(c, xs, ts, nf, batch);
     double l = 0;
@@ -1073,12 +1276,12 @@ gbfd_status gbfd_cnn_train_step(gbfd_cnn *c, const float *xs, const float *ts, i
         return GBFD_ERR_INVALID_ARG;
     }
     const int n3 = c->n * c->n * c->n, npts = batch * n3;
-    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, n3, npts, c->norm,
-                                                                c->norm + 5, c->x0);
+    k_input_compact<<<(npts + 255) / 256, 256, 0, c->stream>>>(xs, nf, c->n, npts, c->batch,
+                                                                c->norm, c->norm + 5, c->x0);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = forward(c, npts);
+        e = forward(c, npts, true);
     if (e == cudaSuccess)
         e = backward(c, xs, ts, nf, batch);
     c->adam_t++;
@@ -1114,10 +1317,11 @@ gbfd_status gbfd_cnn_apply(gbfd_cnn *c, gbfd_ctx *ctx)
     // run on the solver's stream so the correction is ordered with its steps
     const cudaStream_t saved = c->stream;
     c->stream = s;
-    k_input_state<<<(n3 + 255) / 256, 256, 0, s>>>(st, L, nf, c->norm, c->norm + 5, c->x0);
+    k_input_state<<<(n3 + 255) / 256, 256, 0, s>>>(st, L, nf, c->batch, c->norm, c->norm + 5,
+                                                   c->x0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = forward(c, n3);
+        e = forward(c, n3, false);
     if (e == cudaSuccess) {
         k_apply<<<(n3 + 255) / 256, 256, 0, s>>>(st, L, nf, c->y3, c->norm + 10);
         e = cudaGetLastError();

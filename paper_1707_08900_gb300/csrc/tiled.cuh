@@ -40,6 +40,9 @@ constexpr int kVarPx1 = 0, kVarPacked = 1, kVarLagReg = 2, kVarLagReg1 = 3, kVar
               kVarLagTmFree = 5;
 constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 
+// Default FP64 table entry (see tiled_f64.cu).
+constexpr int kDefaultF64 = 0;
+
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);
 TileConfig tiled_config(int sbytes, int i);

@@ -390,10 +390,13 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
             };
 
             if constexpr (PK) {
-                // FP32 storage and stencil arithmetic; the Eq. 10 update (u-tilde
-                // and the new state) in TA, u-tilde stored as TW
-                static_assert(std::is_same<TS, float>::value, "the packed path is FP32");
-                constexpr bool UP32 = std::is_same<TA, float>::value && std::is_same<TW, float>::value;
+                // stencil arithmetic in TS on point pairs (packed FP32x2 for
+                // FP32, pairs of scalar operations for FP64); the Eq. 10
+                // update in TA, u-tilde stored as TW: in TS when all three
+                // agree, else the precision form (FP32 storage, FP64 update)
+                constexpr bool UP32 = std::is_same<TA, TS>::value && std::is_same<TW, TS>::value;
+                static_assert(UP32 || std::is_same<TS, float>::value,
+                              "FP64 update only with FP32 storage");
                 using P = PairOps<TS>;
                 if (valid0) {
                     const int zo = z0 + oo;

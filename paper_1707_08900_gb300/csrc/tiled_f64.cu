@@ -1,5 +1,10 @@
-// Tiled substep instantiations with FP64 storage and arithmetic.
-#include "tiled_impl.cuh"
+// Tiled substep instantiations with FP64 storage and arithmetic (FP64 tile
+// table): 0, 1 the one-point-per-thread kernel on 32 x 4 and 16 x 8 tiles;
+// 2-4 the two-point kernel on point pairs (scalar FP64 operations in pairs)
+// with the z-paired Eq. 8 terms accumulated forward from each arriving plane,
+// on 32 x 4 tiles with one or two output planes per iteration and on 32 x 8.
+// Forced steps (Sect. 6 forcing) run the one-point kernel.
+#include "tiled2_impl.cuh"
 
 namespace gbfd {
 
@@ -8,16 +13,32 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
                                  int form, int cfg, int *dev_error, TmapCache *cache,
                                  cudaStream_t stream, int *launches)
 {
-    const int idx = cfg < 0 ? 0 : cfg;
+    const int idx = cfg < 0 ? kDefaultF64 : cfg;
     const TileConfig t = tiled_config(8, idx);
-    const int v = idx / kZcChoices;
+    const int v = st.fo.on ? 0 : idx / kZcChoices;
     cudaError_t e;
-    if (v == 0)
+    switch (v) {
+    case 0:
         e = launch_tiled_cfg<TS, TW, TA, 32, 4, 8>(b, c, st, nf, form, t.zc, v, dev_error, cache,
                                                    stream, launches);
-    else
+        break;
+    case 1:
         e = launch_tiled_cfg<TS, TW, TA, 16, 8, 8>(b, c, st, nf, form, t.zc, v, dev_error, cache,
                                                    stream, launches);
+        break;
+    case 2:
+        e = launch_px2_cfg<TS, TW, TA, 32, 4, 6, true, 1, 1, false, false, false, 3>(
+            b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
+        break;
+    case 3:
+        e = launch_px2_cfg<TS, TW, TA, 32, 4, 5, true, 2, 1, false, false, false, 3>(
+            b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
+        break;
+    default:
+        e = launch_px2_cfg<TS, TW, TA, 32, 8, 5, true, 1, 1, false, false, false, 3>(
+            b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
+        break;
+    }
     if (e != cudaSuccess || form == 0)
         return e;
     return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);

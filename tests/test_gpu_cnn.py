@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 BF16_FWD_TOL = 2e-2
-BF16_GRAD_TOL = 4e-2
+BF16_GRAD_TOL = 2e-2
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -43,8 +43,10 @@ def _check_fp32(got, ref, base, what=""):
     the max-abs errors beside them."""
     err, inc, mab = rel_l2(got, ref), inc_err(got, ref, base), max_abs(got, ref)
     bar = inc_bar(ref, base)
-    print(f"{what} relL2 {np.array2string(err, precision=2)} inc {np.array2string(inc, precision=2)}"
-          f" bar {np.array2string(bar, precision=2)} maxabs {np.array2string(mab, precision=2)}")
+
+    def fmt(a):
+        return "[" + " ".join(f"{v:.2e}" for v in a) + "]"
+    print(f"{what} relL2 {fmt(err)} inc {fmt(inc)} bar {fmt(bar)} maxabs {fmt(mab)}")
     assert np.all(err <= FP32_TOL), (what, err)
     assert np.all(inc <= bar), (what, inc, bar)
     return err, inc
