@@ -364,7 +364,7 @@ def run_ours(args):
     s.close()
     nerr = 2 + k64
     errs = {}
-    for prec in ("fp32", "fp32_acc64"):
+    for prec in ("fp32", "fp32_acc64", "fp32_accff"):
         s2 = make(prec, "55p")
         s2.rk3_step(dt, nerr)
         x = s2.get_state()
@@ -455,6 +455,15 @@ def run_ours(args):
     msa, _ = timed_steps(s, dt, kacc, stream, torch)
     extra["fp32_acc64_55p"] = {"value": world * npts * kacc / (max_over_ranks_(msa) * 1e-3),
                                "steps": kacc, "ms_per_step": msa / kacc}
+    s.close()
+    # ---- the same update in float-float FP32 pairs (Dekker / Knuth
+    # error-free products and sums) on the FP32 default kernel
+    s = make("fp32_accff", "55p")
+    s.rk3_step(dt, 2)
+    torch.cuda.synchronize()
+    msf, _ = timed_steps(s, dt, kacc, stream, torch)
+    extra["fp32_accff_55p"] = {"value": world * npts * kacc / (max_over_ranks_(msf) * 1e-3),
+                               "steps": kacc, "ms_per_step": msf / kacc}
     s.close()
 
     # ---- batched form: 96 boxes (32 each of 32^3, 64^3, 128^3), rms Mach

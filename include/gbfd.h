@@ -54,8 +54,18 @@ typedef enum {
  *   w <- alpha w + dt rhs and u <- u + beta w of Eq. 10 is done in FP64 in
  *   registers and rounded to FP32 storage.
  * FP32_ACC64_W64: as FP32_ACC64, but the 2N register w (u-tilde) is also
- *   stored in FP64. */
-enum { GBFD_FP64 = 0, GBFD_FP32 = 1, GBFD_FP32_ACC64 = 2, GBFD_FP32_ACC64_W64 = 3 };
+ *   stored in FP64.
+ * FP32_ACCFF: as FP32_ACC64, with the update carried in float-float
+ *   arithmetic (each value an unevaluated sum of two FP32 numbers, products
+ *   and sums made error-free, Dekker 1971 / Knuth) on the FP32 units instead
+ *   of the FP64 pipe; w stored in FP32.  55-point form only. */
+enum {
+    GBFD_FP64 = 0,
+    GBFD_FP32 = 1,
+    GBFD_FP32_ACC64 = 2,
+    GBFD_FP32_ACC64_W64 = 3,
+    GBFD_FP32_ACCFF = 4
+};
 
 /* Stencil form (Sect. 4.1 and 4.2).
  * 55P: single pass; grad(div u) from Eq. 7 and the bidiagonal Eq. 8.

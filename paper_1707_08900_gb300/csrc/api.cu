@@ -111,8 +111,12 @@ bool validate(const gbfd_params *p, char *why, size_t n)
         snprintf(why, n, "grid too large");
         return false;
     }
-    if (p->precision < GBFD_FP64 || p->precision > GBFD_FP32_ACC64_W64) {
+    if (p->precision < GBFD_FP64 || p->precision > GBFD_FP32_ACCFF) {
         snprintf(why, n, "unknown precision %d", p->precision);
+        return false;
+    }
+    if (p->precision == GBFD_FP32_ACCFF && p->form != GBFD_55P) {
+        snprintf(why, n, "the float-float precision form is built for the 55-point form only");
         return false;
     }
     if (p->form != GBFD_55P && p->form != GBFD_19P) {
@@ -312,6 +316,15 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
                                                                c->tile_cfg, c->dev_error, &c->tmaps,
                                                                c->stream, &n)
                   : launch_substep_simple<float, float, double>(b, c->c32, st, c->nf, c->p.form,
+                                                                c->stream, &n);
+        break;
+    case GBFD_FP32_ACCFF:
+        e = tiled ? launch_substep_tiled<float, float, ffloat>(b, c->c32, st, c->nf, c->p.form,
+                                                               c->tile_cfg < 0 ? fp32_default_cfg(c)
+                                                                               : c->tile_cfg,
+                                                               c->dev_error, &c->tmaps, c->stream,
+                                                               &n)
+                  : launch_substep_simple<float, float, ffloat>(b, c->c32, st, c->nf, c->p.form,
                                                                 c->stream, &n);
         break;
     default:
@@ -782,7 +795,9 @@ gbfd_status gbfd_autotune(gbfd_ctx *ctx, int reps, const char *cache_path, int *
     // the precision forms compile three kernels (packed two-point with integer
     // or hardware conversions, one-point): tune those and their chunk lengths
     const bool acc = ctx->p.precision == GBFD_FP32_ACC64 || ctx->p.precision == GBFD_FP32_ACC64_W64;
-    const int count = acc ? 3 * kZcChoices : tiled_config_count(ctx->sbytes);
+    // the float-float form runs one kernel: tune its chunk length only
+    const bool ff = ctx->p.precision == GBFD_FP32_ACCFF;
+    const int count = acc ? 3 * kZcChoices : (ff ? kZcChoices : tiled_config_count(ctx->sbytes));
     std::map<std::string, std::pair<int, double>> cache;
     if (cache_path) {
         cache = read_cache(cache_path);

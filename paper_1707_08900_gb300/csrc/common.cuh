@@ -249,6 +249,77 @@ __device__ __forceinline__ void rk3_update(bool first, TA alpha, TA beta, TA dt,
     out = (TS)((TA)u + beta * wn);
 }
 
+// A value carried as an unevaluated sum of two FP32 numbers, hi + lo with
+// |lo| <= ulp(hi) / 2 ("float-float", Dekker 1971): the precision form's
+// Eq. 10 update in compensated FP32 arithmetic.  Built from an FP64 value
+// (the RK3 coefficients and dt) or from an FP32 one (lo = 0).
+struct ffloat {
+    float hi, lo;
+    __host__ __device__ ffloat() : hi(0.f), lo(0.f) {}
+    __host__ __device__ ffloat(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+
+// Error-free transformations (round-to-nearest FP32; explicit _rn operations
+// so that nothing is contracted into a fused multiply-add):
+// a * b = p + e exactly (fused multiply-add form of Dekker's product) ...
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// ... a + b = s + e exactly (Knuth's TwoSum, no ordering of a and b needed) ...
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// ... and a + b = s + e exactly when |a| >= |b| (Dekker's FastTwoSum).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Eq. 10 for one FP32 value in float-float arithmetic: w_new = alpha w + dt r
+// kept as hi + lo (the products and their sum error-free, the low-order
+// terms summed in FP32), w stored as its FP32 rounding hi, and
+// u_out = u + beta (hi + lo) rounded once to FP32 from an error-free sum.
+// About 48 significant bits, so the result matches the FP64 update of the
+// same inputs except where the two roundings of a near-tie differ.
+__device__ __forceinline__ void rk3_update_ff(bool first, ffloat alpha, ffloat beta, ffloat dt,
+                                              float r, float u, float &w, float &out)
+{
+    float p2, e2, hi, lo;
+    two_prod(dt.hi, r, p2, e2);
+    e2 = __fmaf_rn(dt.lo, r, e2);
+    if (first) {
+        fast_two_sum(p2, e2, hi, lo);
+    } else {
+        float p1, e1, s, t;
+        two_prod(alpha.hi, w, p1, e1);
+        e1 = __fmaf_rn(alpha.lo, w, e1);
+        two_sum(p1, p2, s, t);
+        // s can be small after cancellation: renormalise with the full TwoSum
+        two_sum(s, __fadd_rn(t, __fadd_rn(e1, e2)), hi, lo);
+    }
+    w = hi;
+    float q, f, s2, t2;
+    two_prod(beta.hi, hi, q, f);
+    f = __fmaf_rn(beta.hi, lo, f);
+    f = __fmaf_rn(beta.lo, hi, f);
+    two_sum(u, q, s2, t2);
+    out = __fadd_rn(s2, __fadd_rn(t2, f));
+}
+
+template <>
+__device__ __forceinline__ void rk3_update<ffloat, float, float>(bool first, ffloat alpha,
+                                                                 ffloat beta, ffloat dt, ffloat r,
+                                                                 float u, float &w, float &out)
+{
+    rk3_update_ff(first, alpha, beta, dt, r.hi, u, w, out);
+}
+
 // Exact IEEE-754 conversions between binary32 and binary64 done with integer
 // instructions, so that GB300's narrow FP64 pipe is left to the arithmetic.
 // binary32 (sign, 8-bit exponent e, 23-bit fraction m) -> binary64: exponent

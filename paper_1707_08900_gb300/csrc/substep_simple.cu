@@ -3,6 +3,8 @@
 // valid grid and the cross-check for the tiled kernels; the fused
 // 55-point substep is Algorithm 2, the two kernels of the 19-point form are
 // the two passes of Algorithm 3 (Eqs. 14-16).
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "stencil.cuh"
 
@@ -129,17 +131,21 @@ cudaError_t launch_substep_simple(const StateBufs &b, const Coef<TS> &c, const R
         *launches += 1;
         return cudaGetLastError();
     }
-    if (nf == 5)
-        k_substep_simple<TS, TW, TA, 5, false><<<grid, block, 0, stream>>>(in, out, w, divf, b.Ls,
-                                                                          b.Lw, c, st);
-    else
-        k_substep_simple<TS, TW, TA, 4, false><<<grid, block, 0, stream>>>(in, out, w, divf, b.Ls,
-                                                                          b.Lw, c, st);
-    cudaError_t e = cudaGetLastError();
-    *launches += 1;
-    if (e != cudaSuccess)
-        return e;
-    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
+    if constexpr (std::is_same<TA, ffloat>::value) {
+        return cudaErrorNotSupported;  // the float-float form is 55-point only
+    } else {
+        if (nf == 5)
+            k_substep_simple<TS, TW, TA, 5, false><<<grid, block, 0, stream>>>(in, out, w, divf,
+                                                                              b.Ls, b.Lw, c, st);
+        else
+            k_substep_simple<TS, TW, TA, 4, false><<<grid, block, 0, stream>>>(in, out, w, divf,
+                                                                              b.Ls, b.Lw, c, st);
+        cudaError_t e = cudaGetLastError();
+        *launches += 1;
+        if (e != cudaSuccess)
+            return e;
+        return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
+    }
 }
 
 template <class TS, class TW, class TA>
@@ -168,6 +174,10 @@ template cudaError_t launch_substep_simple<float, float, float>(const StateBufs 
                                                                const RKStage &, int, int,
                                                                cudaStream_t, int *);
 template cudaError_t launch_substep_simple<float, float, double>(const StateBufs &,
+                                                                const Coef<float> &,
+                                                                const RKStage &, int, int,
+                                                                cudaStream_t, int *);
+template cudaError_t launch_substep_simple<float, float, ffloat>(const StateBufs &,
                                                                 const Coef<float> &,
                                                                 const RKStage &, int, int,
                                                                 cudaStream_t, int *);

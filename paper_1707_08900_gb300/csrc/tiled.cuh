@@ -40,8 +40,10 @@ constexpr int kVarPx1 = 0, kVarPacked = 1, kVarLagReg = 2, kVarLagReg1 = 3, kVar
               kVarLagTmFree = 5;
 constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 
-// Default FP64 table entry (see tiled_f64.cu).
-constexpr int kDefaultF64 = 0;
+// Default FP64 table entry (see tiled_f64.cu): the one-point kernel on
+// 16 x 8 tiles, z-chunks of 40 (2% faster than 32 x 4 at 256^3; the FP64
+// pipe is the bound, about 80% busy).
+constexpr int kDefaultF64 = 4;
 
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);

@@ -507,6 +507,16 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
                     o2 = P::fma(BETA, wn, u0);
                     if (!last)
                         *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = wn;
+                } else if constexpr (std::is_same<TA, ffloat>::value) {
+                    // the precision form in float-float arithmetic
+                    static_assert(std::is_same<TW, float>::value, "u-tilde stored in FP32");
+                    float wo[2] = {first ? 0.f : wv[f].x, first ? 0.f : wv[f].y};
+                    float on[2];
+                    rk3_update_ff(first, alpha, beta, dt, r[f].x, u0.x, wo[0], on[0]);
+                    rk3_update_ff(first, alpha, beta, dt, r[f].y, u0.y, wo[1], on[1]);
+                    o2 = make_float2(on[0], on[1]);
+                    if (!last)
+                        *reinterpret_cast<V *>(w + f * Lw.fpitch + go_w) = make_float2(wo[0], wo[1]);
                 } else {
                     static_assert(std::is_same<TA, double>::value, "FP64 update");
                     TW wo[2] = {first ? (TW)0 : wv[f].x, first ? (TW)0 : wv[f].y};

@@ -3,10 +3,8 @@
 // kernel, the two-plane packed two-point kernel, and the kernel that
 // finishes output planes three planes behind the in-plane work (pending
 // right-hand sides in registers, two or one steps per iteration, or in TMEM:
-// the default).  The 19-point form's second pass is the tiled one
-// (pass2_tiled.cuh).  The z-chunk length comes from the table entry; the API picks
+// the default).  The z-chunk length comes from the table entry; the API picks
 // the default entry's chunk per grid (fp32_default_cfg in api.cu).
-#include "pass2_tiled.cuh"
 #include "tiled4_impl.cuh"
 
 namespace gbfd {
@@ -46,8 +44,11 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     }
     if (e != cudaSuccess || form == 0)
         return e;
-    // the 19-point form's second pass: tiled (the first pass's z-chunk)
-    return launch_pass2_tiled(b, c, st, t.zc, dev_error, cache, stream, launches);
+    // the 19-point form's second pass: one thread per point (a z-streaming
+    // TMA-tiled version measured slower at 256^3: 10.2 against 11.6 G
+    // updates/s for the form, its per-plane work being too small to hide the
+    // ring's latency; the one-point kernel is within 15% of its own bytes)
+    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
 }
 
 template cudaError_t launch_substep_tiled<float, float, float>(const StateBufs &,

@@ -18,7 +18,7 @@ GBFD_OK = 0
 STATUS = {0: "GBFD_OK", 1: "GBFD_ERR_INVALID_ARG", 2: "GBFD_ERR_WORKSPACE", 3: "GBFD_ERR_CUDA",
           4: "GBFD_ERR_TIMEOUT", 5: "GBFD_ERR_UNSUPPORTED", 6: "GBFD_ERR_STATE"}
 
-GBFD_FP64, GBFD_FP32, GBFD_FP32_ACC64, GBFD_FP32_ACC64_W64 = 0, 1, 2, 3
+GBFD_FP64, GBFD_FP32, GBFD_FP32_ACC64, GBFD_FP32_ACC64_W64, GBFD_FP32_ACCFF = 0, 1, 2, 3, 4
 GBFD_55P, GBFD_19P = 0, 1
 GBFD_OPT_KERNEL_PATH, GBFD_OPT_TILE_CONFIG, GBFD_OPT_FAULT_SKIP_COPY, GBFD_OPT_HOST_PATH = 1, 2, 3, 4
 GBFD_OPT_HOST_ASYNC = 5
@@ -26,7 +26,7 @@ GBFD_BC_PERIODIC, GBFD_BC_WALL = 0, 1
 BCS = {"periodic": GBFD_BC_PERIODIC, "wall": GBFD_BC_WALL}
 
 PRECISIONS = {"fp64": GBFD_FP64, "fp32": GBFD_FP32, "fp32_acc64": GBFD_FP32_ACC64,
-              "fp32_acc64_w64": GBFD_FP32_ACC64_W64}
+              "fp32_acc64_w64": GBFD_FP32_ACC64_W64, "fp32_accff": GBFD_FP32_ACCFF}
 FORMS = {"55p": GBFD_55P, "19p": GBFD_19P}
 
 # exported symbols of include/gbfd.h (checked by the ABI test)

@@ -1,6 +1,6 @@
-"""Precision study: FP32 storage and stencils with the RK3 update in FP32, or
-in FP64 registers (u-tilde stored in FP32 or FP64), against an FP64 run of
-the same solver on the same state.  (The one-step check of this workload
+"""Precision study: FP32 storage and stencils with the RK3 update in FP32, in
+FP64 registers (u-tilde stored in FP32 or FP64), or in float-float FP32
+pairs, against an FP64 run of the same solver on the same state.  (The one-step check of this workload
 against the FP64 oracle on 64^3 windows is a GPU test:
 tests/test_gpu_parity.py::test_config3_window_against_oracle.)
 
@@ -21,7 +21,7 @@ import numpy as np
 
 from . import gbfd, inputs
 
-FORMS = ("fp32", "fp32_acc64", "fp32_acc64_w64")
+FORMS = ("fp32", "fp32_acc64", "fp32_acc64_w64", "fp32_accff")
 
 
 def _errors(x, ref):
