@@ -99,8 +99,16 @@ typedef struct {
  * ghost zones, whose solution is the periodic one of the mirror-extended
  * state.  The initial state should have u_z = 0 on both wall planes.  Not
  * available with the forcing, the batch or the correction network
- * (UNSUPPORTED). */
-enum { GBFD_BC_PERIODIC = 0, GBFD_BC_WALL = 1 };
+ * (UNSUPPORTED).
+ * EXCHANGE: the box is one z-slab of a larger periodic domain split along z
+ * (the domain decomposition the paper names as the route to several GPUs,
+ * Sect. 7): x and y periodic, z spacing lz / nz, and the three ghost planes
+ * below and above the slab are the neighbouring slabs' boundary planes,
+ * which the caller moves between substeps with gbfd_halo_pack /
+ * gbfd_halo_unpack (one exchange of the five fields per substep; the
+ * 19-point form would need a second one for the divergence between its
+ * passes and is not provided: INVALID_ARG).  55-point form only. */
+enum { GBFD_BC_PERIODIC = 0, GBFD_BC_WALL = 1, GBFD_BC_EXCHANGE = 2 };
 
 /* FP64 reductions over the current state (grid cell volume dV = prod L_i/N_i):
  * mass = dV sum exp(lnrho); ekin = dV sum exp(lnrho)|u|^2/2;
@@ -190,6 +198,21 @@ gbfd_status gbfd_cfl_dt(gbfd_ctx *ctx, double cfl, double cnu, double *dt_out);
  * arrays, k = 0, k parallel to e, phi not finite), CUDA. */
 gbfd_status gbfd_rk3_step_forced(gbfd_ctx *ctx, double dt, int nsteps, double f0, const int *k,
                                  const double *phi, const double *e);
+
+/* Halo exchange of a bc_z = GBFD_BC_EXCHANGE context (Sect. 7's domain
+ * decomposition along z; no counterpart kernel in the paper).  A message is
+ * the three interior planes next to one side, every field, whole padded
+ * planes: gbfd_halo_bytes(ctx) bytes (0 for other contexts).  pack(side)
+ * copies this slab's planes 0..2 (side 0) or nz-3..nz-1 (side 1) into the
+ * device buffer dst; unpack(side) writes the device buffer src into the
+ * ghost planes -3..-1 (side 0) or nz..nz+2 (side 1).  So the lower
+ * neighbour's side-1 message is unpacked into side 0 and the upper
+ * neighbour's side-0 message into side 1, before every substep (after
+ * gbfd_set_state too).  Both are stream-ordered device copies on the
+ * context's stream.  Errors: UNSUPPORTED (other contexts), INVALID_ARG. */
+size_t gbfd_halo_bytes(const gbfd_ctx *ctx);
+gbfd_status gbfd_halo_pack(gbfd_ctx *ctx, int side, void *dst);
+gbfd_status gbfd_halo_unpack(gbfd_ctx *ctx, int side, const void *src);
 
 /* Wait for the context's stream and report any device-side error
  * (bounded waits that gave up -> TIMEOUT; CUDA errors -> CUDA). */

@@ -40,6 +40,7 @@ def lib():
         L.or_substep19.argtypes = [_P, _P, _P, _P, _I, _D, _L, _L, _L, _D, _D, _D, _D, _D, _I]
         L.or_substep55_wall.argtypes = L.or_substep55.argtypes
         L.or_substep19_wall.argtypes = L.or_substep19.argtypes
+        L.or_substep55_slab.argtypes = L.or_substep55.argtypes
         L.or_fill_ghosts_z.argtypes = [_P, _L, _L, _L, _I, _P]
         L.or_diagnostics.argtypes = [_P, _L, _L, _L, _D, _D, _D, _I, _P]
         L.or_cfl_dt.restype = _D
@@ -258,6 +259,19 @@ def rk3_step_wall(state, dt, grid, phys, form=FORM_55P, nsteps=1):
         for s in range(3):
             ext, w = substep_wall(ext, w, s, dt, grid, phys, form)
     return interior_wall(ext)
+
+
+def substep_slab(ext_in, w, s, dt, grid, phys):
+    """One 55-point substep on a z-slab (ghost-extended arrays, nz + 6
+    planes, ghosts filled by the caller from the neighbouring slabs); `grid`
+    is the slab's (nz interior planes, lz = nz x the z spacing).  Returns
+    (ext_out with its interior written and its ghost planes zero, w_new)."""
+    st = _f64(ext_in)
+    wn = _f64(w).copy()
+    out = np.zeros_like(st)
+    lib().or_substep55_slab(_p(st), _p(wn), _p(out), s, dt, *grid.dims(), phys.cs, phys.nu,
+                            phys.entropy_mode)
+    return out, wn
 
 
 def cfl_dt_wall(state, grid, phys, cfl=0.4, cnu=0.25):

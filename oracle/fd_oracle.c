@@ -111,7 +111,11 @@ typedef struct {
 
 #define GZ_WALL 3
 
-static grid_t make_grid_bc(long nx, long ny, long nz, double lx, double ly, double lz, long gz)
+/* gz = 0: periodic z; gz = 3 with walls (spacing lz / (nz - 1)), or a
+ * z-slab of a periodic domain whose ghost planes hold the neighbouring
+ * slabs' planes (walls = 0: spacing lz / nz) */
+static grid_t make_grid_gw(long nx, long ny, long nz, double lx, double ly, double lz, long gz,
+                           int walls)
 {
     grid_t g;
     g.n[0] = nx;
@@ -119,10 +123,15 @@ static grid_t make_grid_bc(long nx, long ny, long nz, double lx, double ly, doub
     g.n[2] = nz;
     g.h[0] = lx / (double)nx;
     g.h[1] = ly / (double)ny;
-    g.h[2] = gz ? lz / (double)(nz - 1) : lz / (double)nz;
+    g.h[2] = walls ? lz / (double)(nz - 1) : lz / (double)nz;
     g.gz = gz;
     g.npts = nx * ny * (nz + 2 * gz);
     return g;
+}
+
+static grid_t make_grid_bc(long nx, long ny, long nz, double lx, double ly, double lz, long gz)
+{
+    return make_grid_gw(nx, ny, nz, lx, ly, lz, gz, gz != 0);
 }
 
 static grid_t make_grid(long nx, long ny, long nz, double lx, double ly, double lz)
@@ -497,9 +506,9 @@ static inline void rk3_update(int s, double dt, double r, double in, double *w, 
  * `in` and `w` (the 2N register, u-tilde), writes `out` and `w`. */
 static void substep55(const double *in, double *w, double *out, int s, double dt, long nx,
                       long ny, long nz, double lx, double ly, double lz, double cs, double nu,
-                      int entropy_mode, const forcing_t *fo, long gz)
+                      int entropy_mode, const forcing_t *fo, long gz, int walls)
 {
-    grid_t g = make_grid_bc(nx, ny, nz, lx, ly, lz, gz);
+    grid_t g = make_grid_gw(nx, ny, nz, lx, ly, lz, gz, walls);
     phys_t ph = make_phys(cs, nu, entropy_mode);
     const long n = g.npts;
 #pragma omp parallel for schedule(static)
@@ -569,7 +578,7 @@ static void substep19(const double *in, double *w, double *out, double *divf, in
 void or_substep55(const double *in, double *w, double *out, int s, double dt, long nx, long ny,
                   long nz, double lx, double ly, double lz, double cs, double nu, int entropy_mode)
 {
-    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, 0);
+    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, 0, 0);
 }
 
 void or_substep19(const double *in, double *w, double *out, double *divf, int s, double dt,
@@ -589,7 +598,18 @@ void or_substep55_wall(const double *in, double *w, double *out, int s, double d
                        long ny, long nz, double lx, double ly, double lz, double cs, double nu,
                        int entropy_mode)
 {
-    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, GZ_WALL);
+    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, GZ_WALL, 1);
+}
+
+/* One substep of Algorithm 2 on a z-slab of a periodic domain split along z
+ * (the domain decomposition of Sect. 7): ghost-extended arrays as for the
+ * wall variant, whose ghost planes the caller has filled with the
+ * neighbouring slabs' boundary planes; z spacing lz / nz. */
+void or_substep55_slab(const double *in, double *w, double *out, int s, double dt, long nx,
+                       long ny, long nz, double lx, double ly, double lz, double cs, double nu,
+                       int entropy_mode)
+{
+    substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, NULL, GZ_WALL, 0);
 }
 
 void or_substep19_wall(const double *in, double *w, double *out, double *divf, int s, double dt,
@@ -615,7 +635,7 @@ int or_substep_forced(const double *in, double *w, double *out, double *divf, in
     if (form == 1)
         substep19(in, w, out, divf, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo, 0);
     else
-        substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo, 0);
+        substep55(in, w, out, s, dt, nx, ny, nz, lx, ly, lz, cs, nu, entropy_mode, &fo, 0, 0);
     return 0;
 }
 

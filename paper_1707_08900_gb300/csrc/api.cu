@@ -123,8 +123,12 @@ bool validate(const gbfd_params *p, char *why, size_t n)
         snprintf(why, n, "unknown form %d", p->form);
         return false;
     }
-    if (p->bc_z != GBFD_BC_PERIODIC && p->bc_z != GBFD_BC_WALL) {
-        snprintf(why, n, "bc_z must be GBFD_BC_PERIODIC or GBFD_BC_WALL");
+    if (p->bc_z != GBFD_BC_PERIODIC && p->bc_z != GBFD_BC_WALL && p->bc_z != GBFD_BC_EXCHANGE) {
+        snprintf(why, n, "bc_z must be GBFD_BC_PERIODIC, GBFD_BC_WALL or GBFD_BC_EXCHANGE");
+        return false;
+    }
+    if (p->bc_z == GBFD_BC_EXCHANGE && p->form != GBFD_55P) {
+        snprintf(why, n, "exchanged z halos are built for the 55-point form only");
         return false;
     }
     if (p->entropy_mode != 0 && p->entropy_mode != 1) {
@@ -158,7 +162,7 @@ Plan make_plan(const gbfd_params *p)
     const int wb = (p->precision == GBFD_FP64 || p->precision == GBFD_FP32_ACC64_W64) ? 8 : 4;
     // walls in z: ghost planes on the state and the stored divergence (the
     // 2N register is only read at interior points)
-    const int gz = p->bc_z == GBFD_BC_WALL ? GZW : 0;
+    const int gz = p->bc_z != GBFD_BC_PERIODIC ? GZW : 0;
     pl.Ls = make_layout(p->nx, p->ny, p->nz, sb, nf, gz);
     pl.Lw = make_layout(p->nx, p->ny, p->nz, wb, nf);
     pl.Ld = make_layout(p->nx, p->ny, p->nz, sb, 1, gz);
@@ -338,12 +342,15 @@ gbfd_status do_substep(gbfd_ctx *c, int s, double dt)
     c->launches += n;
     if (e != cudaSuccess)
         return cuda_fail(c, e, "substep launch");
-    // walls in z: the boundary step (Algorithm 1) on the new state
-    n = 0;
-    e = launch_fill_ghosts_z(b.out, c->Ls, c->nf, kWallOddMask, c->stream, &n);
-    c->launches += n;
-    if (e != cudaSuccess)
-        return cuda_fail(c, e, "ghost planes");
+    // walls in z: the boundary step (Algorithm 1) on the new state (with
+    // exchanged halos the caller fills the ghost planes instead)
+    if (c->p.bc_z == GBFD_BC_WALL) {
+        n = 0;
+        e = launch_fill_ghosts_z(b.out, c->Ls, c->nf, kWallOddMask, c->stream, &n);
+        c->launches += n;
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "ghost planes");
+    }
     c->cur ^= 1;
     return GBFD_OK;
 }
@@ -545,12 +552,14 @@ gbfd_status gbfd_set_state(gbfd_ctx *ctx, const void *src, int src_on_device, in
     ctx->launches += nl;
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "set_state scatter");
-    nl = 0;
-    e = launch_fill_ghosts_z(ctx->state_region[ctx->cur] + ctx->Ls.origin, ctx->Ls, ctx->nf,
-                             kWallOddMask, ctx->stream, &nl);
-    ctx->launches += nl;
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e, "set_state ghost planes");
+    if (ctx->p.bc_z == GBFD_BC_WALL) {
+        nl = 0;
+        e = launch_fill_ghosts_z(ctx->state_region[ctx->cur] + ctx->Ls.origin, ctx->Ls, ctx->nf,
+                                 kWallOddMask, ctx->stream, &nl);
+        ctx->launches += nl;
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "set_state ghost planes");
+    }
     return GBFD_OK;
 }
 
@@ -688,6 +697,54 @@ gbfd_status gbfd_rk3_step_forced(gbfd_ctx *ctx, double dt, int nsteps, double f0
             return st;
     }
     return GBFD_OK;
+}
+
+size_t gbfd_halo_bytes(const gbfd_ctx *ctx)
+{
+    if (!ctx || ctx->p.bc_z != GBFD_BC_EXCHANGE)
+        return 0;
+    return (size_t)ctx->nf * GZW * ctx->Ls.plane * ctx->Ls.w;
+}
+
+// One side's halo message: the GZW interior planes next to that side, whole
+// padded planes of every field, [field][plane][Y][X].
+static gbfd_status halo_copy(gbfd_ctx *ctx, int side, void *buf, bool pack)
+{
+    gbfd_status st = check_ctx(ctx);
+    if (st != GBFD_OK)
+        return st;
+    if (ctx->p.bc_z != GBFD_BC_EXCHANGE) {
+        set_err(ctx, "halo exchange needs a context created with bc_z = GBFD_BC_EXCHANGE");
+        return GBFD_ERR_UNSUPPORTED;
+    }
+    if ((side != 0 && side != 1) || !buf) {
+        set_err(ctx, "halo: side must be 0 (low z) or 1 (high z) and the buffer non-NULL");
+        return GBFD_ERR_INVALID_ARG;
+    }
+    const Layout &L = ctx->Ls;
+    char *origin = ctx->state_region[ctx->cur] + L.origin;
+    // pack: interior planes 0..2 (side 0) or nz-3..nz-1 (side 1); unpack:
+    // ghost planes -3..-1 (side 0) or nz..nz+2 (side 1), in increasing z
+    const long long z0 = pack ? (side ? L.nz - GZW : 0) : (side ? L.nz : -GZW);
+    char *field0 = origin + z0 * L.plane * L.w;
+    const size_t width = (size_t)GZW * L.plane * L.w, fp = (size_t)L.fpitch * L.w;
+    cudaError_t e = pack ? cudaMemcpy2DAsync(buf, width, field0, fp, width, ctx->nf,
+                                             cudaMemcpyDeviceToDevice, ctx->stream)
+                         : cudaMemcpy2DAsync(field0, fp, buf, width, width, ctx->nf,
+                                             cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, pack ? "halo pack" : "halo unpack");
+    return GBFD_OK;
+}
+
+gbfd_status gbfd_halo_pack(gbfd_ctx *ctx, int side, void *dst)
+{
+    return halo_copy(ctx, side, dst, true);
+}
+
+gbfd_status gbfd_halo_unpack(gbfd_ctx *ctx, int side, const void *src)
+{
+    return halo_copy(ctx, side, const_cast<void *>(src), false);
 }
 
 gbfd_status gbfd_sync(gbfd_ctx *ctx)

@@ -145,9 +145,11 @@ static_assert(TXT * TYT == MT, "one MMA row block per tile plane");
 
 // Warp roles of the convolution CTA (one per SM, persistent over tiles):
 // warp 0 issues the TMA halo loads, warp 1 the MMAs (and owns the TMEM
-// allocation), warps 2-5 are the epilogue (warp w reads TMEM lanes
-// 32 (w % 4) .. 32 (w % 4) + 31).
-constexpr int CONV_THREADS = 192;
+// allocation), warps 2-9 are the epilogue (warp w reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31; warps 2-5 the first half of the output
+// channels, 6-9 the second).
+constexpr int CONV_THREADS = 320;
+constexpr int EPI_WARPS = 8;
 constexpr int NSTAGE = 2;  // halo buffers
 constexpr int NACC = 2;    // TMEM accumulator buffers
 
@@ -169,16 +171,7 @@ struct ConvSmem {
     static_assert(CS % 16 == 0 && (CS >> 4) < (1 << 14), "descriptor offsets");
 };
 
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                            int c0, int c1, int c2, int c3, int c4)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(tiled::smem_u32(dst)),
-        "l"((uint64_t)map), "r"(tiled::smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
-        "r"(c4)
-        : "memory");
-}
+
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -246,7 +239,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         }
         for (int s = 0; s < NACC; ++s) {
             tiled::mbar_init(&accf[s], 1);
-            tiled::mbar_init(&acce[s], 4);  // one arrival per epilogue warp
+            tiled::mbar_init(&acce[s], EPI_WARPS);  // one arrival per epilogue warp
         }
         *abort = 0;
         cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
@@ -275,9 +268,10 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 int x0, y0, z0, b;
                 tile_origin(tile, n, x0, y0, z0, b);
                 tiled::mbar_expect_tx(&full[s], SM::A_BYTES);
-                // padded coordinates of the halo's first point: (x0 - 1) + 1
-                tma_load_5d(sA + s * SM::A_PITCH, &xmap, &full[s], 0, x0, y0, b * (n + 2) + z0,
-                            0);
+                // padded coordinates of the halo's first point: (x0 - 1) + 1;
+                // x and the 8 channels of a chunk form one 160-byte row
+                tiled::tma_load_4d(sA + s * SM::A_PITCH, &xmap, &full[s], 8 * x0, y0,
+                                   b * (n + 2) + z0, 0);
                 cnt[0] = i + 1;
             }
         }
@@ -321,11 +315,14 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         }
     } else {
         // epilogue: TMEM -> registers, release the accumulators, then bias /
-        // GELU / GELU' and the stores (with the periodic copies)
-        const int q = warp % 4;
+        // GELU / GELU' and the stores (with the periodic copies).  Two warps
+        // per TMEM lane quarter, each taking half of the output channels.
+        constexpr int NH = N / 2;  // channels per epilogue warp
+        const int e = warp - 2;
+        const int q = warp % 4, c0 = (e / 4) * NH;
         const int r = q * 32 + lane;  // row of the M block = TMEM lane
         const int lx = r % TXT, ly = r / TXT;
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + c0;
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int acc = i % NACC;
@@ -341,18 +338,19 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             if (lane != 0)
                 (void)tiled::mbar_try_wait(&accf[acc], (i / NACC) & 1);
             tc::fence_after_sync();
-            float v[ZB][N];
+            float v[ZB][NH];
 #pragma unroll
             for (int zb = 0; zb < ZB; ++zb) {
-                tc::tmem_ld16(tl + acc * SM::ACC_COLS + zb * N, v[zb]);
-                if constexpr (N > 16)
-                    tc::tmem_ld16(tl + acc * SM::ACC_COLS + zb * N + 16, v[zb] + 16);
+                if constexpr (NH == 16)
+                    tc::tmem_ld16(tl + acc * SM::ACC_COLS + zb * N, v[zb]);
+                else
+                    tc::tmem_ld8(tl + acc * SM::ACC_COLS + zb * N, v[zb]);
             }
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&acce[acc]);
-            if (warp == 2 && lane == 0)
+            if (e == 0 && lane == 0)
                 cnt[3] = i + 1;
             int x0, y0, z0, b;
             tile_origin(tile, n, x0, y0, z0, b);
@@ -364,21 +362,24 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     continue;
                 const long long p = (long long)b * n3 + ((long long)z * n + y) * n + x;
                 if constexpr (EPI == EPI_LINEAR) {
-                    float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
-                    yo[0] = make_float4(v[zb][0] + __ldg(a.bias + 0), v[zb][1] + __ldg(a.bias + 1),
-                                        v[zb][2] + __ldg(a.bias + 2), v[zb][3] + __ldg(a.bias + 3));
-                    yo[1] = make_float4(v[zb][4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
+                    // five real output channels, all in the first half
+                    if (c0 == 0) {
+                        float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
+                        yo[0] = make_float4(v[zb][0] + __ldg(a.bias + 0), v[zb][1] + __ldg(a.bias + 1),
+                                            v[zb][2] + __ldg(a.bias + 2), v[zb][3] + __ldg(a.bias + 3));
+                        yo[1] = make_float4(v[zb][4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
+                    }
                 } else {
-                    uint4 out[N / 8];
+                    uint4 out[NH / 8];
 #pragma unroll
-                    for (int c = 0; c < N; c += 8) {
+                    for (int c = 0; c < NH; c += 8) {
                         float h[8];
                         if constexpr (EPI == EPI_GELU) {
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
-                                h[j] = v[zb][c + j] + __ldg(a.bias + c + j);
+                                h[j] = v[zb][c + j] + __ldg(a.bias + c0 + c + j);
                             if (a.hsave) {
-                                float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * N + c);
+                                float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * N + c0 + c);
                                 hs[0] = make_float4(h[0], h[1], h[2], h[3]);
                                 hs[1] = make_float4(h[4], h[5], h[6], h[7]);
                             }
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                             for (int j = 0; j < 8; ++j)
                                 h[j] = gelu(h[j]);
                         } else {
-                            const float4 *hp = reinterpret_cast<const float4 *>(a.hprev + p * N + c);
+                            const float4 *hp =
+                                reinterpret_cast<const float4 *>(a.hprev + p * N + c0 + c);
                             const float4 h0 = __ldg(hp), h1 = __ldg(hp + 1);
                             const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
@@ -402,8 +404,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     uint4 *yb = reinterpret_cast<uint4 *>(a.yb);
                     each_copy(x, y, z, n, [&](int xp, int yp, int zp) {
 #pragma unroll
-                        for (int c8 = 0; c8 < N / 8; ++c8)
-                            yb[aidx(c8, b, zp, yp, xp, n, a.B)] = out[c8];
+                        for (int k8 = 0; k8 < NH / 8; ++k8)
+                            yb[aidx(c0 / 8 + k8, b, zp, yp, xp, n, a.B)] = out[k8];
                     });
                 }
             }
@@ -847,19 +849,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 // TMA map of a padded chunk-major activation of cin channels (B samples on
-// an n^3 grid): dims (8 channels, n + 2, n + 2, (n + 2) B, cin / 8), box =
-// one conv tile's halo, (8, HX, HY, HZ, cin / 8).
+// an n^3 grid): dims (8 (n + 2) values = x and the 8 channels of a chunk,
+// n + 2, (n + 2) B, cin / 8), box = one conv tile's halo, (8 HX, HY, HZ,
+// cin / 8): 160-byte rows.
 bool encode_act_map(CUtensorMap *m, const bf16 *base, int n, int B, int cin)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn)
         return false;
     const cuuint64_t np2 = (cuuint64_t)(n + 2);
-    const cuuint64_t dims[5] = {8, np2, np2, np2 * (cuuint64_t)B, (cuuint64_t)(cin / 8)};
-    const cuuint64_t strides[4] = {16, np2 * 16, np2 * np2 * 16, np2 * np2 * np2 * B * 16};
-    const cuuint32_t box[5] = {8, HX, HY, HZ, (cuuint32_t)(cin / 8)};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims, strides, box,
+    const cuuint64_t dims[4] = {8 * np2, np2, np2 * (cuuint64_t)B, (cuuint64_t)(cin / 8)};
+    const cuuint64_t strides[3] = {np2 * 16, np2 * np2 * 16, np2 * np2 * np2 * B * 16};
+    const cuuint32_t box[4] = {8 * HX, HY, HZ, (cuuint32_t)(cin / 8)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }

@@ -126,5 +126,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *r)
         r[i] = __uint_as_float(v[i]);
 }
 
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes into r[0..7].
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *r)
+{
+    uint32_t v[8];
+    __syncwarp();
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        r[i] = __uint_as_float(v[i]);
+}
+
 }  // namespace tc
 }  // namespace gbfd

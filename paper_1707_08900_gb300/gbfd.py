@@ -22,8 +22,8 @@ GBFD_FP64, GBFD_FP32, GBFD_FP32_ACC64, GBFD_FP32_ACC64_W64, GBFD_FP32_ACCFF = 0,
 GBFD_55P, GBFD_19P = 0, 1
 GBFD_OPT_KERNEL_PATH, GBFD_OPT_TILE_CONFIG, GBFD_OPT_FAULT_SKIP_COPY, GBFD_OPT_HOST_PATH = 1, 2, 3, 4
 GBFD_OPT_HOST_ASYNC = 5
-GBFD_BC_PERIODIC, GBFD_BC_WALL = 0, 1
-BCS = {"periodic": GBFD_BC_PERIODIC, "wall": GBFD_BC_WALL}
+GBFD_BC_PERIODIC, GBFD_BC_WALL, GBFD_BC_EXCHANGE = 0, 1, 2
+BCS = {"periodic": GBFD_BC_PERIODIC, "wall": GBFD_BC_WALL, "exchange": GBFD_BC_EXCHANGE}
 
 PRECISIONS = {"fp64": GBFD_FP64, "fp32": GBFD_FP32, "fp32_acc64": GBFD_FP32_ACC64,
               "fp32_acc64_w64": GBFD_FP32_ACC64_W64, "fp32_accff": GBFD_FP32_ACCFF}
@@ -43,7 +43,7 @@ EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state"
            "gbfd_cnn_set_norm", "gbfd_cnn_forward", "gbfd_cnn_gradients",
            "gbfd_cnn_train_step", "gbfd_cnn_apply", "gbfd_step_corrected", "gbfd_box_filter",
            "gbfd_cnn_launch_count", "gbfd_cnn_last_error", "gbfd_cnn_set_option",
-           "gbfd_fp64_fma_rate")
+           "gbfd_fp64_fma_rate", "gbfd_halo_bytes", "gbfd_halo_pack", "gbfd_halo_unpack")
 GBFD_CNN_OPT_CONV_GRID, GBFD_CNN_OPT_WGRAD_PARTS = 1, 2
 GBFD_BATCH_OPT_GRAPH, GBFD_BATCH_OPT_ZCHUNK, GBFD_BATCH_OPT_GRID = 1, 2, 3
 
@@ -159,6 +159,10 @@ def load(path=None):
     L.gbfd_cnn_last_error.argtypes = [_VP]
     L.gbfd_cnn_set_option.argtypes = [_VP, ctypes.c_int, ctypes.c_int64]
     L.gbfd_fp64_fma_rate.argtypes = [_VP, _DP]
+    L.gbfd_halo_bytes.restype = ctypes.c_size_t
+    L.gbfd_halo_bytes.argtypes = [_VP]
+    L.gbfd_halo_pack.argtypes = [_VP, ctypes.c_int, _VP]
+    L.gbfd_halo_unpack.argtypes = [_VP, ctypes.c_int, _VP]
     L.gbfd_status_string.restype = ctypes.c_char_p
     L.gbfd_status_string.argtypes = [ctypes.c_int]
     for name in EXPORTS:

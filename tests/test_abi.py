@@ -67,8 +67,14 @@ def test_workspace_size_accounts_for_layout(lib):
     plane = (64 + 8 + 24) * (64 + 6)  # padded row pitch (a multiple of 32 values) x rows
     assert gbfd.gbfd_workspace_bytes(pw) >= gbfd.gbfd_workspace_bytes(p32) + 2 * 5 * 6 * plane * 4
     bad = gbfd.make_params((64, 64, 64), precision="fp32")
-    bad.bc_z = 2
+    bad.bc_z = 3
     assert gbfd.gbfd_workspace_bytes(bad) == 0
+    # exchanged halos (z-slabs of a decomposed box): 55-point form only
+    assert gbfd.gbfd_workspace_bytes(gbfd.make_params((64, 64, 64), bc_z="exchange")) > 0
+    assert gbfd.gbfd_workspace_bytes(gbfd.make_params((64, 64, 64), form="19p",
+                                                      bc_z="exchange")) == 0
+    assert gbfd.gbfd_workspace_bytes(gbfd.make_params((64, 64, 64), form="19p",
+                                                      precision="fp32_accff")) == 0
 
 
 def test_init_rejects_null_and_misaligned_workspace(lib):

@@ -109,7 +109,7 @@ WALL_MUTANTS = {
                        "a[-k * plane + c] = a[k * plane + c];"),
     "mirror_off_by_one": ("a[(nz - 1 + k) * plane + c] = parity[f] * a[(nz - 1 - k) * plane + c];",
                           "a[(nz - 1 + k) * plane + c] = parity[f] * a[(nz - k) * plane + c];"),
-    "spacing_periodic": ("g.h[2] = gz ? lz / (double)(nz - 1) : lz / (double)nz;",
+    "spacing_periodic": ("g.h[2] = walls ? lz / (double)(nz - 1) : lz / (double)nz;",
                          "g.h[2] = lz / (double)nz;"),
     "divergence_ghosts_stale": ("        or_fill_ghosts_z(divf, nx, ny, nz, 1, &even);",
                                 "        (void)even;"),
