@@ -344,17 +344,43 @@ gbfd_status gbfd_batch_step(gbfd_batch *b, const double *dt, int nsteps);
 /* FP64 diagnostics of one box (synchronises). */
 gbfd_status gbfd_batch_diagnostics(gbfd_batch *b, int box, gbfd_diag *out);
 
-/* Wait for the stream; TIMEOUT when a bounded device wait gave up. */
+/* Wait for the stream; TIMEOUT when a bounded device wait gave up (an
+ * mbarrier wait in a column, or a dataflow item's wait for its box's
+ * previous substep), after which the batch stays usable. */
 gbfd_status gbfd_batch_sync(gbfd_batch *b);
 
-/* Options: GBFD_BATCH_OPT_GRAPH (1 = replay CUDA graphs, the default; 0 =
- * direct launches), GBFD_BATCH_OPT_ZCHUNK (planes per work item: 8, 16, 32,
- * 64), GBFD_BATCH_OPT_GRID (persistent CTAs; default SMs x resident CTAs). */
-enum { GBFD_BATCH_OPT_GRAPH = 1, GBFD_BATCH_OPT_ZCHUNK = 2, GBFD_BATCH_OPT_GRID = 3 };
+/* Options (no counterpart in the paper):
+ * GBFD_BATCH_OPT_GRAPH: 1 = replay CUDA graphs (default), 0 = direct launches;
+ * GBFD_BATCH_OPT_ZCHUNK: planes per work item: 8, 16, 32 (default), 64;
+ * GBFD_BATCH_OPT_GRID: persistent CTAs per launch (0 = SMs x resident CTAs);
+ * GBFD_BATCH_OPT_KERNEL: column routine: 0 = two-plane packed on 32 x 8
+ *   tiles (default), 1 = lagged output with TMEM on 32 x 8 (weights read from
+ *   shared memory), 2 = two-plane packed on 64 x 8;
+ * GBFD_BATCH_OPT_DATAFLOW: 1 = all substeps of a gbfd_batch_step in ONE
+ *   persistent launch, work items ordered by substep and each waiting
+ *   (bounded, about 2 s) for its box's previous substep through a per-box
+ *   completion counter (default); 0 = one launch per substep;
+ * GBFD_BATCH_OPT_FAULT_STALL (tests): the dataflow work item with this index
+ *   is never counted as done, so its box's next substep runs into the
+ *   bounded wait (TIMEOUT at gbfd_batch_sync); -1 = off (default).
+ * Out-of-range values -> INVALID_ARG.  gbfd_batch_get_option reads them back
+ * (GRID: the grid in use). */
+enum {
+    GBFD_BATCH_OPT_GRAPH = 1,
+    GBFD_BATCH_OPT_ZCHUNK = 2,
+    GBFD_BATCH_OPT_GRID = 3,
+    GBFD_BATCH_OPT_KERNEL = 4,
+    GBFD_BATCH_OPT_DATAFLOW = 5,
+    GBFD_BATCH_OPT_FAULT_STALL = 6
+};
 gbfd_status gbfd_batch_set_option(gbfd_batch *b, int key, int64_t value);
+gbfd_status gbfd_batch_get_option(const gbfd_batch *b, int key, int64_t *value);
 
-/* Autotuner of the batch: times `steps` RK3 steps for each z-chunk length
- * without advancing the state, keeps the fastest (outputs may be NULL). */
+/* Autotuner of the batch: times `steps` RK3 steps (dt = 0, which leaves the
+ * state's values unchanged) for every column routine x z-chunk length x
+ * launch mode (dataflow or per substep), keeps the fastest; its z-chunk and
+ * time per step are returned (outputs may be NULL; the rest is readable with
+ * gbfd_batch_get_option). */
 gbfd_status gbfd_batch_autotune(gbfd_batch *b, int steps, int *best_zc, double *best_ms);
 
 int64_t gbfd_batch_launch_count(const gbfd_batch *b);

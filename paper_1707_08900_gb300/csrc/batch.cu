@@ -1,17 +1,30 @@
 // Batched form: many independent periodic cubic boxes of uneven sizes, each
-// with its own viscosity and time step, advanced together.  Every substep is
-// ONE persistent launch whose CTAs walk a work list of equal-cost columns
-// (box, 32x8 tile, z-chunk) drawn from all boxes, through the same
-// TMA-staged two-points-per-thread pipeline as the single-box kernel
-// (tiled2::run_column, packed FP32x2 form); a run of RK3 steps is captured
-// once as a CUDA graph and replayed.  FP32 storage and arithmetic.
+// with its own viscosity and time step, advanced together.  The work is a
+// list of equal-cost columns (box, tile, z-chunk) drawn from all boxes, each
+// streamed through the same TMA-staged two-points-per-thread pipeline as the
+// single-box kernels (the two-plane packed column routine on 32 x 8 or 64 x 8
+// tiles, or the lagged-output routine with its pending right-hand sides in
+// TMEM on 32 x 8 tiles), FP32 storage and arithmetic.  Two ways to run it:
 //
-// Per-box data lives in device memory: the TMA descriptors of the box's two
-// state buffers and its u-tilde, the buffer pointers and layout, and the
-// stencil weights with the box's spacing folded in (cubic cells: one set of
-// weights for all axes, so it fits in registers).  Time steps are read from
-// a device array the host refreshes before each replay, so one graph serves
-// any dt.
+// * dataflow (the default): ALL substeps of a run of RK3 steps in ONE
+//   persistent launch.  CTAs take work items (substep k, column i) in order
+//   from an atomic counter; an item of box b at substep k waits (bounded)
+//   until the box's completion counter shows every column of its substeps
+//   before k done, then streams its column and adds one to the counter
+//   (release after the stores, acquire before the TMA loads).  Items are
+//   taken in order and only wait for items taken earlier, so the launch
+//   cannot deadlock whatever the residency; boxes at different substeps
+//   overlap, so no device-wide barrier is ever needed;
+// * one persistent launch per substep walking the list (CTAs stride it).
+//
+// A run of RK3 steps is captured once as a CUDA graph and replayed.  Per-box
+// data lives in device memory: the TMA descriptors of the box's two state
+// buffers and its u-tilde (for both tile widths), the buffer pointers and
+// layout, and the stencil weights with the box's spacing folded in (cubic
+// cells: one set of weights for all axes; the lagged routine reads them from
+// shared memory, where they do not cost registers).  Time steps are read
+// from a device array the host refreshes before each replay, so one graph
+// serves any dt.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -26,52 +39,227 @@
 #include <vector>
 
 #include "../../include/gbfd.h"
-#include "tiled2_impl.cuh"
+#include "tiled4_impl.cuh"
 
 namespace gbfd {
 namespace batch {
 
-constexpr int TX = 32, TY = 8, NS = 8, U = 2;  // U: output planes per loop iteration
+constexpr int NS = 8, U = 2;  // ring slots, output planes per loop iteration
+
+// Column routines (kernel kinds) and their tiles.
+enum { KIND_PACKED = 0, KIND_LAG = 1, KIND_PACKED64 = 2, NKIND = 3 };
+__host__ __device__ constexpr int kind_tx(int kind) { return kind == KIND_PACKED64 ? 64 : 32; }
+constexpr int TY = 8;
 
 struct BoxDesc {
-    CUtensorMap tm_state[2];  // halo boxes of state buffers 0 and 1
-    CUtensorMap tm_w;         // tile boxes of u-tilde
-    float *state[2];          // origins of the padded state buffers
-    float *w;                 // origin of the padded u-tilde buffer
-    Layout L;                 // layout of all three (FP32)
+    CUtensorMap tm_state[2][2];  // [tile width 32 / 64][buffer]: halo boxes of the state
+    CUtensorMap tm_w[2];         // [tile width]: tile boxes of u-tilde
+    float *state[2];             // origins of the padded state buffers
+    float *w;                    // origin of the padded u-tilde buffer
+    Layout L;                    // layout of all three (FP32)
     CubicCoef<float> coef;
+    int nitems;                  // columns of this box in the work list
 };
 
-template <int NF>
-__global__ void __launch_bounds__((TX / 2) * TY) k_batch_substep(
+// Device-side state of the dataflow launch, zeroed before each launch.
+struct Flow {
+    int next;   // next work item to hand out
+    int abort;  // a wait gave up: stop taking work
+    int done[1];  // [nbox] columns completed, over all substeps so far
+};
+
+template <int KIND, int NF>
+constexpr int smem_bytes()
+{
+    if constexpr (KIND == KIND_LAG)
+        return tiled4::RingL<float, NF, 32, TY, NS, U>::BYTES;
+    else
+        return tiled2::Ring<float, float, NF, kind_tx(KIND), TY, NS, U + 2>::BYTES;
+}
+
+// One column of one box at substep s (parity: which state buffer is the
+// input).  Returns false when a bounded wait gave up.
+template <int KIND, int NF>
+__device__ __forceinline__ bool run_item(const BoxDesc *__restrict__ B, const int4 item,
+                                         const int s, const int parity, const float dt,
+                                         const int zc, const CubicCoef<float> &scoef, int &jrun,
+                                         int &wrun, unsigned char *smem, int *dev_error,
+                                         const uint32_t tmem)
+{
+    constexpr int TX = kind_tx(KIND);
+    constexpr int wi = TX == 64 ? 1 : 0;
+    const Layout L = B->L;
+    const int nout = min(zc, L.nz - item.w);
+    // Williamson's coefficients (common.cuh: RK3_ALPHA, RK3_BETA), in FP32
+    const float alpha = s == 0 ? 0.0f : (s == 1 ? (float)(-5.0 / 9.0) : (float)(-153.0 / 128.0));
+    const float beta = s == 0 ? (float)(1.0 / 3.0) : (s == 1 ? (float)(15.0 / 16.0)
+                                                            : (float)(8.0 / 15.0));
+    if constexpr (KIND == KIND_LAG) {
+        return tiled4::run_column<float, float, NF, TX, TY, NS, U, false, false, 1>(
+            &B->tm_state[wi][parity], &B->tm_w[wi], B->state[parity ^ 1], B->w, L, L, scoef,
+            alpha, beta, dt, s == 0, s == 2, item.y, item.z, item.w, nout, jrun, wrun, smem,
+            dev_error, -1, nullptr, tmem);
+    } else {
+        const CubicCoef<float> c = B->coef;
+        return tiled2::run_column<float, float, float, NF, true, TX, TY, NS, true, U, false>(
+            &B->tm_state[wi][parity], &B->tm_w[wi], B->state[parity ^ 1], B->w, nullptr, L, L, c,
+            alpha, beta, dt, s == 0, s == 2, item.y, item.z, item.w, nout, jrun, wrun, smem,
+            dev_error);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ uint32_t tmem_open(unsigned char *smem, int bytes)
+{
+    if constexpr (KIND != KIND_LAG)
+        return 0;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + bytes - 16);
+    if (threadIdx.x < 32)
+        tc::tmem_alloc(slot, tiled4::kTmCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    return *reinterpret_cast<volatile uint32_t *>(slot);
+}
+
+template <int KIND>
+__device__ __forceinline__ void tmem_close(uint32_t tmem)
+{
+    if constexpr (KIND == KIND_LAG) {
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (threadIdx.x < 32)
+            tc::tmem_dealloc(tmem, tiled4::kTmCols);
+    }
+}
+
+// One persistent launch per substep: the CTAs stride the work list.
+template <int KIND, int NF>
+__global__ void __launch_bounds__((kind_tx(KIND) / 2) * TY) k_batch_substep(
     const BoxDesc *__restrict__ boxes, const int4 *__restrict__ items, const int nitems,
-    const float *__restrict__ dts, const int zc, const RKStage st, const int parity,
+    const float *__restrict__ dts, const int zc, const int s, const int parity,
     int *__restrict__ dev_error)
 {
-    using RG = tiled2::Ring<float, float, NF, TX, TY, NS, U + 2>;
+    constexpr int SMB = smem_bytes<KIND, NF>();
     extern __shared__ __align__(128) unsigned char smem[];
-    tiled2::init_barriers(reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF), NS + RG::NW);
+    __shared__ CubicCoef<float> scoef;
+    if constexpr (KIND == KIND_LAG)
+        tiled2::init_barriers(reinterpret_cast<uint64_t *>(
+                                  smem + tiled4::RingL<float, NF, 32, TY, NS, U>::BAR_OFF),
+                              NS + U + 2);
+    else
+        tiled2::init_barriers(reinterpret_cast<uint64_t *>(
+                                  smem + tiled2::Ring<float, float, NF, kind_tx(KIND), TY, NS,
+                                                      U + 2>::BAR_OFF),
+                              NS + U + 2);
+    const uint32_t tmem = tmem_open<KIND>(smem, SMB);
     int jrun = 0, wrun = 0;
 #pragma unroll 1
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 item = items[it];  // box, x0, y0, z0
         const BoxDesc *B = boxes + item.x;
-        const CubicCoef<float> c = B->coef;
-        const Layout L = B->L;
-        const float dt = dts[item.x];
-        const int nout = min(zc, L.nz - item.w);
-        if (!tiled2::run_column<float, float, float, NF, true, TX, TY, NS, true, U, false>(
-                &B->tm_state[parity], &B->tm_w, B->state[parity ^ 1], B->w, nullptr, L, L, c,
-                (float)st.alpha, (float)st.beta, dt, st.first != 0, st.last != 0, item.y, item.z,
-                item.w, nout, jrun, wrun, smem, dev_error))
+        __syncthreads();  // every thread is done with the previous box's weights
+        if (threadIdx.x == 0)
+            scoef = B->coef;
+        __syncthreads();
+        if (!run_item<KIND, NF>(B, item, s, parity, dts[item.x], zc, scoef, jrun, wrun, smem,
+                                dev_error, tmem))
             break;
     }
+    tmem_close<KIND>(tmem);
 }
 
-template <int NF>
-constexpr int smem_bytes()
+__device__ __forceinline__ int ld_acquire(const int *p)
 {
-    return tiled2::Ring<float, float, NF, TX, TY, NS, U + 2>::BYTES;
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All substeps of nsub = 3 nsteps in one persistent launch (dataflow over
+// per-box completion counters; see the top of the file).  stall_item (tests
+// only, -1 = off): the CTA that finishes this work item does not count it,
+// so the items that depend on it wait until their bounded wait gives up.
+template <int KIND, int NF>
+__global__ void __launch_bounds__((kind_tx(KIND) / 2) * TY) k_batch_flow(
+    const BoxDesc *__restrict__ boxes, const int4 *__restrict__ items, const int nitems,
+    const int nsub, const float *__restrict__ dts, const int zc, const int cur,
+    Flow *__restrict__ flow, int *__restrict__ dev_error, const int stall_item)
+{
+    constexpr int SMB = smem_bytes<KIND, NF>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ CubicCoef<float> scoef;
+    __shared__ int sq;
+    if constexpr (KIND == KIND_LAG)
+        tiled2::init_barriers(reinterpret_cast<uint64_t *>(
+                                  smem + tiled4::RingL<float, NF, 32, TY, NS, U>::BAR_OFF),
+                              NS + U + 2);
+    else
+        tiled2::init_barriers(reinterpret_cast<uint64_t *>(
+                                  smem + tiled2::Ring<float, float, NF, kind_tx(KIND), TY, NS,
+                                                      U + 2>::BAR_OFF),
+                              NS + U + 2);
+    const uint32_t tmem = tmem_open<KIND>(smem, SMB);
+    const long long nq = (long long)nsub * nitems;
+    int jrun = 0, wrun = 0;
+#pragma unroll 1
+    while (true) {
+        if (threadIdx.x == 0) {
+            int q = -1;
+            if (!ld_acquire(&flow->abort)) {
+                q = atomicAdd(&flow->next, 1);
+                if (q < nq) {
+                    const int k = q / nitems;
+                    const int box = items[q % nitems].x;
+                    // every column of this box's substeps before k is done
+                    const int need = k * boxes[box].nitems;
+                    if (ld_acquire(&flow->done[box]) < need) {
+                        const uint64_t t0 = tiled::global_ns();
+                        while (ld_acquire(&flow->done[box]) < need) {
+                            if (ld_acquire(&flow->abort) ||
+                                tiled::global_ns() - t0 > 2000000000ull) {
+                                atomicExch(&flow->abort, 1);
+                                atomicExch(dev_error, 3);
+                                q = -1;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                    }
+                    // the other CTAs' generic-proxy stores are visible: order
+                    // them before this thread's TMA (async-proxy) loads
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                } else {
+                    q = -1;
+                }
+            }
+            sq = q;
+            if (q >= 0)
+                scoef = boxes[items[q % nitems].x].coef;
+        }
+        __syncthreads();
+        const int q = sq;
+        if (q < 0)
+            break;
+        const int k = q / nitems;
+        const int4 item = items[q % nitems];
+        const BoxDesc *B = boxes + item.x;
+        const bool ok = run_item<KIND, NF>(B, item, k % 3, (cur + k) & 1, dts[item.x], zc, scoef,
+                                           jrun, wrun, smem, dev_error, tmem);
+        __syncthreads();  // the column's stores are issued by every thread
+        if (threadIdx.x == 0) {
+            if (!ok)
+                atomicExch(&flow->abort, 1);
+            else if (q != stall_item) {
+                __threadfence();  // release: the stores before the count
+                atomicAdd(&flow->done[item.x], 1);
+            }
+        }
+        if (!ok)
+            break;
+    }
+    tmem_close<KIND>(tmem);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -110,19 +298,21 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 struct Plan {
     std::vector<Layout> lay;
     std::vector<size_t> off_state0, off_state1, off_w;
-    size_t off_desc, off_items, off_dt, off_staging, off_part, off_out, off_err, total;
+    size_t off_desc, off_items, off_dt, off_staging, off_part, off_out, off_err, off_flow, total;
     int nitems;
     int ndiag;
 };
 
+size_t flow_bytes(int nbox) { return sizeof(int) * (2 + (size_t)nbox); }
+
 int zc_for(int n, int zc) { return std::min(zc, n); }
 
-int count_items(const int32_t *n, int nbox, int zc)
+int count_items(const int32_t *n, int nbox, int zc, int tx)
 {
     int c = 0;
     for (int b = 0; b < nbox; ++b) {
         const int z = zc_for(n[b], zc);
-        c += ((n[b] + TX - 1) / TX) * ((n[b] + TY - 1) / TY) * ((n[b] + z - 1) / z);
+        c += ((n[b] + tx - 1) / tx) * ((n[b] + TY - 1) / TY) * ((n[b] + z - 1) / z);
     }
     return c;
 }
@@ -157,8 +347,8 @@ bool make_plan(int nbox, const int32_t *n, int entropy_mode, Plan &pl, char *why
     }
     pl.off_desc = off;
     off = align256(off + sizeof(BoxDesc) * nbox);
-    // the work list is sized for the smallest z-chunk offered (8)
-    pl.nitems = count_items(n, nbox, 8);
+    // the work list is sized for the smallest z-chunk (8) and tile (32 wide)
+    pl.nitems = count_items(n, nbox, 8, 32);
     pl.off_items = off;
     off = align256(off + sizeof(int4) * pl.nitems);
     pl.off_dt = off;
@@ -172,6 +362,8 @@ bool make_plan(int nbox, const int32_t *n, int entropy_mode, Plan &pl, char *why
     off = align256(off + 16 * sizeof(double));
     pl.off_err = off;
     off = align256(off + 256);
+    pl.off_flow = off;
+    off = align256(off + flow_bytes(nbox));
     pl.total = off;
     return true;
 }
@@ -197,9 +389,14 @@ struct gbfd_batch {
     char *staging;
     double *dpart, *dout;
     int *derr;
+    Flow *dflow;
     int cur;
     int zc;
-    int grid;
+    int kind;        // column routine (KIND_*)
+    int flow;        // 1: all substeps in one dataflow launch; 0: one launch per substep
+    int stall_item;  // tests: a work item whose completion is never counted (-1 off)
+    int grid;        // CTAs of a launch (0: resident CTAs of the kind on every SM)
+    int grid_kind[NKIND];
     int use_graph;
     int nitems;
     int64_t launches;
@@ -233,18 +430,23 @@ void drop_graphs(gbfd_batch *b)
     b->graphs.clear();
 }
 
-// Build the work list for chunk length zc: box-major so that neighbouring
-// CTAs stream neighbouring tiles of the same box (halo reuse in L2).
-gbfd_status build_items(gbfd_batch *b, int zc)
+// Build the work list for chunk length zc and the kind's tile: box-major so
+// that neighbouring CTAs stream neighbouring tiles of the same box (halo
+// reuse in L2); each box's column count goes to its descriptor (the dataflow
+// launch's completion target).
+gbfd_status build_items(gbfd_batch *b, int zc, int kind)
 {
     std::vector<int4> items;
+    const int tx = kind_tx(kind);
     for (int bx = 0; bx < b->nbox; ++bx) {
         const int n = b->n[bx];
         const int z = zc_for(n, zc);
+        const size_t before = items.size();
         for (int z0 = 0; z0 < n; z0 += z)
             for (int y0 = 0; y0 < n; y0 += TY)
-                for (int x0 = 0; x0 < n; x0 += TX)
+                for (int x0 = 0; x0 < n; x0 += tx)
                     items.push_back(make_int4(bx, x0, y0, z0));
+        b->hdesc[bx].nitems = (int)(items.size() - before);
     }
     if ((int)items.size() > b->plan.nitems) {
         berr(b, "work list overflow");
@@ -252,45 +454,81 @@ gbfd_status build_items(gbfd_batch *b, int zc)
     }
     cudaError_t e = cudaMemcpyAsync(b->ditems, items.data(), sizeof(int4) * items.size(),
                                     cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess)
-        return bcuda(b, e, "work list upload");
-    e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ddesc, b->hdesc.data(), sizeof(BoxDesc) * b->nbox,
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess)
         return bcuda(b, e, "work list upload");
     b->nitems = (int)items.size();
     b->zc = zc;
+    b->kind = kind;
     drop_graphs(b);
     return GBFD_OK;
 }
 
-cudaError_t launch_one(gbfd_batch *b, int s, int parity, cudaStream_t stream)
+int grid_of(const gbfd_batch *b) { return b->grid > 0 ? b->grid : b->grid_kind[b->kind]; }
+
+template <int KIND, int NF>
+cudaError_t launch_substep_k(gbfd_batch *b, int s, int parity, cudaStream_t stream)
 {
-    RKStage st = make_stage(s, 0.0, 0.0);
-    if (b->nf == 5) {
-        k_batch_substep<5><<<b->grid, (TX / 2) * TY, smem_bytes<5>(), stream>>>(
-            b->ddesc, b->ditems, b->nitems, b->ddt, b->zc, st, parity, b->derr);
-    } else {
-        k_batch_substep<4><<<b->grid, (TX / 2) * TY, smem_bytes<4>(), stream>>>(
-            b->ddesc, b->ditems, b->nitems, b->ddt, b->zc, st, parity, b->derr);
-    }
+    k_batch_substep<KIND, NF><<<grid_of(b), (kind_tx(KIND) / 2) * TY, smem_bytes<KIND, NF>(),
+                                stream>>>(b->ddesc, b->ditems, b->nitems, b->ddt, b->zc, s, parity,
+                                          b->derr);
     return cudaGetLastError();
 }
 
-gbfd_status enqueue_steps(gbfd_batch *b, int nsteps, cudaStream_t stream)
+template <int KIND, int NF>
+cudaError_t launch_flow_k(gbfd_batch *b, int nsub, int cur, cudaStream_t stream)
 {
+    cudaError_t e = cudaMemsetAsync(b->dflow, 0, flow_bytes(b->nbox), stream);
+    if (e != cudaSuccess)
+        return e;
+    k_batch_flow<KIND, NF><<<grid_of(b), (kind_tx(KIND) / 2) * TY, smem_bytes<KIND, NF>(),
+                             stream>>>(b->ddesc, b->ditems, b->nitems, nsub, b->ddt, b->zc, cur,
+                                       b->dflow, b->derr, b->stall_item);
+    return cudaGetLastError();
+}
+
+#define GBFD_BATCH_DISPATCH(FN, ...)                                                              \
+    (b->nf == 5 ? (b->kind == KIND_LAG      ? FN<KIND_LAG, 5>(__VA_ARGS__)                        \
+                   : b->kind == KIND_PACKED64 ? FN<KIND_PACKED64, 5>(__VA_ARGS__)                 \
+                                              : FN<KIND_PACKED, 5>(__VA_ARGS__))                  \
+                : (b->kind == KIND_LAG      ? FN<KIND_LAG, 4>(__VA_ARGS__)                        \
+                   : b->kind == KIND_PACKED64 ? FN<KIND_PACKED64, 4>(__VA_ARGS__)                 \
+                                              : FN<KIND_PACKED, 4>(__VA_ARGS__)))
+
+cudaError_t launch_one(gbfd_batch *b, int s, int parity, cudaStream_t stream)
+{
+    return GBFD_BATCH_DISPATCH(launch_substep_k, b, s, parity, stream);
+}
+
+// nsteps RK3 steps from state buffer `cur`: one dataflow launch, or 3 nsteps
+// substep launches; returns the number of kernel launches in `nl`.
+gbfd_status enqueue_steps(gbfd_batch *b, int nsteps, int cur, cudaStream_t stream, int *nl)
+{
+    if (b->flow) {
+        cudaError_t e = GBFD_BATCH_DISPATCH(launch_flow_k, b, 3 * nsteps, cur, stream);
+        if (e != cudaSuccess)
+            return bcuda(b, e, "batch dataflow launch");
+        *nl = 1;
+        return GBFD_OK;
+    }
     for (int k = 0; k < 3 * nsteps; ++k) {
-        cudaError_t e = launch_one(b, k % 3, (b->cur + k) & 1, stream);
+        cudaError_t e = launch_one(b, k % 3, (cur + k) & 1, stream);
         if (e != cudaSuccess)
             return bcuda(b, e, "batch substep launch");
     }
-    b->launches += 3 * nsteps;
+    *nl = 3 * nsteps;
     return GBFD_OK;
 }
 
-gbfd_status graph_for(gbfd_batch *b, int nsteps, cudaGraphExec_t *out)
+gbfd_status graph_for(gbfd_batch *b, int nsteps, cudaGraphExec_t *out, int *nl)
 {
     auto key = std::make_pair(nsteps, b->cur);
     auto it = b->graphs.find(key);
+    *nl = b->flow ? 1 : 3 * nsteps;
     if (it != b->graphs.end()) {
         *out = it->second;
         return GBFD_OK;
@@ -298,9 +536,8 @@ gbfd_status graph_for(gbfd_batch *b, int nsteps, cudaGraphExec_t *out)
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess)
         return bcuda(b, e, "graph capture begin");
-    const int64_t before = b->launches;
-    gbfd_status st = enqueue_steps(b, nsteps, b->cap);
-    b->launches = before;  // counted when the graph is replayed
+    int n = 0;
+    gbfd_status st = enqueue_steps(b, nsteps, b->cur, b->cap, &n);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->cap, &g);
     if (st != GBFD_OK) {
@@ -430,9 +667,14 @@ gbfd_status gbfd_batch_init(int nbox, const int32_t *n, const double *lengths, c
         d.state[1] = (float *)(b->ws + pl.off_state1[i] + d.L.origin);
         d.w = (float *)(b->ws + pl.off_w[i] + d.L.origin);
         d.coef = make_cubic_coef<float>(lengths[i] / n[i], cs, nu[i]);
-        if (!encode(&d.tm_state[0], d.state[0], d.L, b->nf, TX + 2 * GX, TY + 2 * GY) ||
-            !encode(&d.tm_state[1], d.state[1], d.L, b->nf, TX + 2 * GX, TY + 2 * GY) ||
-            !encode(&d.tm_w, d.w, d.L, b->nf, TX, TY)) {
+        bool ok = true;
+        for (int wi = 0; wi < 2; ++wi) {
+            const int tx = wi ? 64 : 32;
+            ok = ok && encode(&d.tm_state[wi][0], d.state[0], d.L, b->nf, tx + 2 * GX, TY + 2 * GY) &&
+                 encode(&d.tm_state[wi][1], d.state[1], d.L, b->nf, tx + 2 * GX, TY + 2 * GY) &&
+                 encode(&d.tm_w[wi], d.w, d.L, b->nf, tx, TY);
+        }
+        if (!ok) {
             berr(nullptr, "TMA descriptor encoding failed for box %d", i);
             cudaStreamDestroy(b->cap);
             delete b;
@@ -442,24 +684,43 @@ gbfd_status gbfd_batch_init(int nbox, const int32_t *n, const double *lengths, c
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->ddesc, b->hdesc.data(), sizeof(BoxDesc) * nbox,
                             cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) {
-        auto k5 = k_batch_substep<5>;
-        auto k4 = k_batch_substep<4>;
-        e = cudaFuncSetAttribute(k5, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<5>());
+    b->dflow = (Flow *)(b->ws + pl.off_flow);
+    b->zc = 32;
+    b->kind = KIND_PACKED;
+    b->flow = 1;
+    b->stall_item = -1;
+    b->grid = 0;
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess)
+        e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // resident CTAs per SM of each kind (the persistent grids), and the
+    // shared-memory limits of every kernel
+    auto setup = [&](auto sub, auto flowk, int threads, int smb, int kind) {
+        int per = 0;
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     smem_bytes<4>());
-        int dev = 0, sms = 0, per = 0;
+            e = cudaFuncSetAttribute(sub, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
         if (e == cudaSuccess)
-            e = cudaGetDevice(&dev);
+            e = cudaFuncSetAttribute(flowk, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
         if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = b->nf == 5 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                 &per, k5, (TX / 2) * TY, smem_bytes<5>())
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                 &per, k4, (TX / 2) * TY, smem_bytes<4>());
-        b->grid = sms * std::max(per, 1);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, flowk, threads, smb);
+        b->grid_kind[kind] = sms * std::max(per, 1);
+    };
+    if (b->nf == 5) {
+        setup(k_batch_substep<KIND_PACKED, 5>, k_batch_flow<KIND_PACKED, 5>, 128,
+              smem_bytes<KIND_PACKED, 5>(), KIND_PACKED);
+        setup(k_batch_substep<KIND_LAG, 5>, k_batch_flow<KIND_LAG, 5>, 128,
+              smem_bytes<KIND_LAG, 5>(), KIND_LAG);
+        setup(k_batch_substep<KIND_PACKED64, 5>, k_batch_flow<KIND_PACKED64, 5>, 256,
+              smem_bytes<KIND_PACKED64, 5>(), KIND_PACKED64);
+    } else {
+        setup(k_batch_substep<KIND_PACKED, 4>, k_batch_flow<KIND_PACKED, 4>, 128,
+              smem_bytes<KIND_PACKED, 4>(), KIND_PACKED);
+        setup(k_batch_substep<KIND_LAG, 4>, k_batch_flow<KIND_LAG, 4>, 128,
+              smem_bytes<KIND_LAG, 4>(), KIND_LAG);
+        setup(k_batch_substep<KIND_PACKED64, 4>, k_batch_flow<KIND_PACKED64, 4>, 256,
+              smem_bytes<KIND_PACKED64, 4>(), KIND_PACKED64);
     }
     if (e != cudaSuccess) {
         bcuda(nullptr, e, "batch init");
@@ -467,7 +728,7 @@ gbfd_status gbfd_batch_init(int nbox, const int32_t *n, const double *lengths, c
         delete b;
         return GBFD_ERR_CUDA;
     }
-    gbfd_status st = build_items(b, 32);
+    gbfd_status st = build_items(b, 32, KIND_PACKED);
     if (st != GBFD_OK) {
         berr(nullptr, "%s", b->err);
         cudaStreamDestroy(b->cap);
@@ -566,20 +827,21 @@ gbfd_status gbfd_batch_step(gbfd_batch *b, const double *dt, int nsteps)
     if (e != cudaSuccess)
         return bcuda(b, e, "batch dt upload");
     gbfd_status st;
+    int nl = 0;
     if (b->use_graph) {
         cudaGraphExec_t ex;
-        st = graph_for(b, nsteps, &ex);
+        st = graph_for(b, nsteps, &ex, &nl);
         if (st != GBFD_OK)
             return st;
         e = cudaGraphLaunch(ex, b->stream);
         if (e != cudaSuccess)
             return bcuda(b, e, "graph launch");
-        b->launches += 3 * nsteps;
     } else {
-        st = enqueue_steps(b, nsteps, b->stream);
+        st = enqueue_steps(b, nsteps, b->cur, b->stream, &nl);
         if (st != GBFD_OK)
             return st;
     }
+    b->launches += nl;
     b->cur ^= (nsteps & 1);  // 3 nsteps buffer swaps
     return GBFD_OK;
 }
@@ -650,11 +912,27 @@ gbfd_status gbfd_batch_set_option(gbfd_batch *b, int key, int64_t value)
     case GBFD_BATCH_OPT_ZCHUNK:
         if (value != 8 && value != 16 && value != 32 && value != 64)
             break;
-        return build_items(b, (int)value);
+        return build_items(b, (int)value, b->kind);
     case GBFD_BATCH_OPT_GRID:
-        if (value < 1 || value > 65535)
+        if (value < 0 || value > 65535)
             break;
         b->grid = (int)value;
+        drop_graphs(b);
+        return GBFD_OK;
+    case GBFD_BATCH_OPT_KERNEL:
+        if (value < 0 || value >= NKIND)
+            break;
+        return build_items(b, b->zc, (int)value);
+    case GBFD_BATCH_OPT_DATAFLOW:
+        if (value != 0 && value != 1)
+            break;
+        b->flow = (int)value;
+        drop_graphs(b);
+        return GBFD_OK;
+    case GBFD_BATCH_OPT_FAULT_STALL:
+        if (value < -1 || value > (1LL << 30))
+            break;
+        b->stall_item = (int)value;
         drop_graphs(b);
         return GBFD_OK;
     default:
@@ -668,56 +946,93 @@ int64_t gbfd_batch_launch_count(const gbfd_batch *b) { return b ? b->launches : 
 
 const char *gbfd_batch_last_error(const gbfd_batch *b) { return b ? b->err : g_batch_err; }
 
+gbfd_status gbfd_batch_get_option(const gbfd_batch *b, int key, int64_t *value)
+{
+    if (!b || !value)
+        return GBFD_ERR_INVALID_ARG;
+    switch (key) {
+    case GBFD_BATCH_OPT_GRAPH:
+        *value = b->use_graph;
+        return GBFD_OK;
+    case GBFD_BATCH_OPT_ZCHUNK:
+        *value = b->zc;
+        return GBFD_OK;
+    case GBFD_BATCH_OPT_GRID:
+        *value = grid_of(b);
+        return GBFD_OK;
+    case GBFD_BATCH_OPT_KERNEL:
+        *value = b->kind;
+        return GBFD_OK;
+    case GBFD_BATCH_OPT_DATAFLOW:
+        *value = b->flow;
+        return GBFD_OK;
+    case GBFD_BATCH_OPT_FAULT_STALL:
+        *value = b->stall_item;
+        return GBFD_OK;
+    default:
+        return GBFD_ERR_INVALID_ARG;
+    }
+}
+
 gbfd_status gbfd_batch_autotune(gbfd_batch *b, int steps, int *best_zc, double *best_ms)
 {
     if (!b || steps < 1)
         return GBFD_ERR_INVALID_ARG;
-    // time substep launches on the current state without advancing it: the
-    // outputs land in the other buffer, which holds no state between steps
+    // Times every (column routine, z-chunk, dataflow or per-substep) on real
+    // RK3 steps with dt = 0, which leave the state's values unchanged
+    // (u + beta * 0 = u), and keeps the fastest.
     const int zcs[] = {8, 16, 32, 64};
     double best = 1e30;
-    int bz = b->zc;
+    int bz = b->zc, bk = b->kind, bf = b->flow;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bcuda(b, cudaGetLastError(), "autotune events");
-    std::vector<float> one(b->nbox, 1e-6f);
-    cudaError_t e = cudaMemcpyAsync(b->ddt, one.data(), sizeof(float) * b->nbox,
+    std::vector<float> zero(b->nbox, 0.0f);
+    cudaError_t e = cudaMemcpyAsync(b->ddt, zero.data(), sizeof(float) * b->nbox,
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(b->stream);
-    for (int zc : zcs) {
-        if (e != cudaSuccess)
-            break;
-        gbfd_status st = build_items(b, zc);
-        if (st != GBFD_OK) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return st;
+    gbfd_status st = GBFD_OK;
+    for (int kind = 0; kind < NKIND && e == cudaSuccess && st == GBFD_OK; ++kind)
+        for (int zc : zcs) {
+            if (e != cudaSuccess || st != GBFD_OK)
+                break;
+            st = build_items(b, zc, kind);
+            for (int flow = 0; flow < 2 && st == GBFD_OK && e == cudaSuccess; ++flow) {
+                b->flow = flow;
+                int nl = 0;
+                st = enqueue_steps(b, 1, b->cur, b->stream, &nl);  // warm-up
+                b->launches += nl;
+                b->cur ^= 1;
+                if (st == GBFD_OK)
+                    e = cudaEventRecord(e0, b->stream);
+                if (st == GBFD_OK && e == cudaSuccess)
+                    st = enqueue_steps(b, steps, b->cur, b->stream, &nl);
+                b->launches += nl;
+                b->cur ^= (steps & 1);
+                if (st == GBFD_OK && e == cudaSuccess)
+                    e = cudaEventRecord(e1, b->stream);
+                if (st == GBFD_OK && e == cudaSuccess)
+                    e = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (st == GBFD_OK && e == cudaSuccess)
+                    e = cudaEventElapsedTime(&ms, e0, e1);
+                if (st == GBFD_OK && e == cudaSuccess && ms / steps < best) {
+                    best = ms / steps;
+                    bz = zc;
+                    bk = kind;
+                    bf = flow;
+                }
+            }
         }
-        for (int r = 0; r < steps + 1 && e == cudaSuccess; ++r) {
-            if (r == 1)
-                e = cudaEventRecord(e0, b->stream);
-            for (int s = 0; s < 3 && e == cudaSuccess; ++s)
-                e = launch_one(b, s, b->cur, b->stream);
-            b->launches += 3;
-        }
-        if (e == cudaSuccess)
-            e = cudaEventRecord(e1, b->stream);
-        if (e == cudaSuccess)
-            e = cudaEventSynchronize(e1);
-        float ms = 0;
-        if (e == cudaSuccess)
-            e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && ms / steps < best) {
-            best = ms / steps;
-            bz = zc;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (st != GBFD_OK)
+        return st;
     if (e != cudaSuccess)
         return bcuda(b, e, "autotune");
-    gbfd_status st = build_items(b, bz);
+    b->flow = bf;
+    st = build_items(b, bz, bk);
     if (st != GBFD_OK)
         return st;
     if (best_zc)

@@ -150,7 +150,7 @@ static_assert(TXT * TYT == MT, "one MMA row block per tile plane");
 // channels, 6-9 the second).
 constexpr int CONV_THREADS = 320;
 constexpr int EPI_WARPS = 8;
-constexpr int NSTAGE = 2;  // halo buffers
+constexpr int NSTAGE = 3;  // halo buffers
 constexpr int NACC = 2;    // TMEM accumulator buffers
 
 template <int CIN, int N, int EPI>
@@ -281,7 +281,13 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         // accumulators to the epilogue
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(MT, N);
-            const uint32_t sA_u32 = tc::smem_u32(sA), sB_u32 = tc::smem_u32(sB);
+            // descriptors of the stage and weight bases; every tap's operand
+            // is a compile-time byte offset from them (the start address is
+            // the descriptor's low field, in 16-byte units, and shared
+            // memory addresses stay below 2^18 bytes, so adding the offset
+            // cannot carry into the next field)
+            const uint64_t bd0 = tc::smem_desc(tc::smem_u32(sB), 128, SBO_B);
+            const uint64_t ad0 = tc::smem_desc(tc::smem_u32(sA), SM::CS, HX * 16);
             int i = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
                 const int s = i % NSTAGE, acc = i % NACC;
@@ -291,20 +297,19 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 if (!wait_or_abort(&acce[acc], ((i / NACC) & 1) ^ 1, abort))
                     break;
                 tc::fence_after_sync();
-                const uint32_t abase = sA_u32 + s * SM::A_PITCH;
-#pragma unroll 1
+                const uint64_t adst = ad0 + (uint64_t)((s * SM::A_PITCH) >> 4);
+                const uint32_t dt0 = tmem + acc * SM::ACC_COLS;
+#pragma unroll
                 for (int zb = 0; zb < ZB; ++zb)
-#pragma unroll 1
+#pragma unroll
                     for (int tap = 0; tap < TAPS; ++tap) {
                         const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // offset + 1
-                        const uint32_t a0 =
-                            abase + (uint32_t)((((zb + dz) * HY + dy) * HX + dx) * 16);
 #pragma unroll
                         for (int k = 0; k < KSTEPS; ++k) {
-                            const uint64_t ad = tc::smem_desc(a0 + 2 * k * SM::CS, SM::CS, HX * 16);
-                            const uint64_t bd =
-                                tc::smem_desc(sB_u32 + (tap * KSTEPS + k) * 256, 128, SBO_B);
-                            tc::mma_bf16(tmem + acc * SM::ACC_COLS + zb * N, ad, bd, idesc,
+                            const int aoff =
+                                ((((zb + dz) * HY + dy) * HX + dx) * 16 + 2 * k * SM::CS) >> 4;
+                            tc::mma_bf16(dt0 + zb * N, adst + (uint64_t)aoff,
+                                         bd0 + (uint64_t)((tap * KSTEPS + k) * 16), idesc,
                                          (tap > 0 || k > 0) ? 1u : 0u);
                         }
                     }

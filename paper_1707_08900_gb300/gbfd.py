@@ -43,9 +43,11 @@ EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state"
            "gbfd_cnn_set_norm", "gbfd_cnn_forward", "gbfd_cnn_gradients",
            "gbfd_cnn_train_step", "gbfd_cnn_apply", "gbfd_step_corrected", "gbfd_box_filter",
            "gbfd_cnn_launch_count", "gbfd_cnn_last_error", "gbfd_cnn_set_option",
-           "gbfd_fp64_fma_rate", "gbfd_halo_bytes", "gbfd_halo_pack", "gbfd_halo_unpack")
+           "gbfd_fp64_fma_rate", "gbfd_halo_bytes", "gbfd_halo_pack", "gbfd_halo_unpack",
+           "gbfd_batch_get_option")
 GBFD_CNN_OPT_CONV_GRID, GBFD_CNN_OPT_WGRAD_PARTS = 1, 2
 GBFD_BATCH_OPT_GRAPH, GBFD_BATCH_OPT_ZCHUNK, GBFD_BATCH_OPT_GRID = 1, 2, 3
+GBFD_BATCH_OPT_KERNEL, GBFD_BATCH_OPT_DATAFLOW, GBFD_BATCH_OPT_FAULT_STALL = 4, 5, 6
 
 
 class GbfdError(RuntimeError):
@@ -131,6 +133,7 @@ def load(path=None):
     L.gbfd_batch_diagnostics.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(gbfd_diag)]
     L.gbfd_batch_sync.argtypes = [_VP]
     L.gbfd_batch_set_option.argtypes = [_VP, ctypes.c_int, ctypes.c_int64]
+    L.gbfd_batch_get_option.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
     L.gbfd_batch_autotune.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP]
     L.gbfd_batch_launch_count.restype = ctypes.c_int64
     L.gbfd_batch_launch_count.argtypes = [_VP]
@@ -466,6 +469,11 @@ class Batch:
 
     def set_option(self, key, value):
         _bcheck(load().gbfd_batch_set_option(self.b, int(key), int(value)), self.b)
+
+    def get_option(self, key):
+        v = ctypes.c_int64()
+        _bcheck(load().gbfd_batch_get_option(self.b, int(key), ctypes.byref(v)), self.b)
+        return v.value
 
     def autotune(self, steps=2):
         zc = ctypes.c_int()

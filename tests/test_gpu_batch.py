@@ -116,6 +116,10 @@ def test_batch_graph_replay_equals_direct_launches_bitwise():
 
 
 def test_batch_autotune_keeps_state_and_chunks_agree():
+    """The autotuner times every column routine x z-chunk x launch mode on
+    dt = 0 steps, which leave the state unchanged; chunk lengths, launch
+    modes and the two-plane tile widths give the same bits (same arithmetic
+    per point), the lagged routine agrees to rounding."""
     from paper_1707_08900_gb300 import gbfd
     ns = [32, 64, 16]
     sts = _states(ns, 31, [2 * np.pi] * 3)
@@ -124,18 +128,65 @@ def test_batch_autotune_keeps_state_and_chunks_agree():
         b.set_state(i, st)
     zc, ms = b.autotune(steps=1)
     assert zc in (8, 16, 32, 64) and ms > 0
+    assert b.get_option(gbfd.GBFD_BATCH_OPT_KERNEL) in (0, 1, 2)
+    assert b.get_option(gbfd.GBFD_BATCH_OPT_DATAFLOW) in (0, 1)
     for i, st in enumerate(sts):
         assert np.array_equal(b.get_state(i, fp64=False), st)
     outs = {}
-    for z in (8, 32, 64):
-        b.set_option(gbfd.GBFD_BATCH_OPT_ZCHUNK, z)
-        for i, st in enumerate(sts):
-            b.set_state(i, st)
-        b.step([0.01] * 3, 1)
-        outs[z] = [b.get_state(i, fp64=False) for i in range(3)]
-    for z in (32, 64):
-        for a, c in zip(outs[8], outs[z]):
-            assert np.array_equal(a, c)
+    for kind in (0, 2, 1):
+        b.set_option(gbfd.GBFD_BATCH_OPT_KERNEL, kind)
+        for flow in (1, 0):
+            b.set_option(gbfd.GBFD_BATCH_OPT_DATAFLOW, flow)
+            for z in (8, 32, 64):
+                b.set_option(gbfd.GBFD_BATCH_OPT_ZCHUNK, z)
+                for i, st in enumerate(sts):
+                    b.set_state(i, st)
+                b.step([0.01] * 3, 2)
+                outs[(kind, flow, z)] = [b.get_state(i, fp64=False) for i in range(3)]
+    base = outs[(0, 1, 8)]
+    for key, out in outs.items():
+        for a, c in zip(base, out):
+            if key[0] == 1:
+                np.testing.assert_allclose(a, c, rtol=0, atol=2e-6 * np.abs(c).max())
+            else:
+                assert np.array_equal(a, c), key
+    # the lagged routine's chunk lengths and launch modes agree bitwise among themselves
+    for key, out in outs.items():
+        if key[0] == 1:
+            for a, c in zip(outs[(1, 1, 8)], out):
+                assert np.array_equal(a, c), key
+    b.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_dataflow_wait_times_out_and_batch_recovers(kind):
+    """A dataflow work item that is never counted as done (fault injection on
+    the host side: GBFD_BATCH_OPT_FAULT_STALL) makes its box's next substep
+    wait until the bounded wait gives up: gbfd_batch_sync reports
+    GBFD_ERR_TIMEOUT, and the batch steps correctly afterwards."""
+    from paper_1707_08900_gb300 import gbfd
+    ns = [16, 24]
+    sts = _states(ns, 5, [2 * np.pi] * 2)
+    b = gbfd.Batch(ns, [2 * np.pi] * 2, [5e-3] * 2)
+    b.set_option(gbfd.GBFD_BATCH_OPT_KERNEL, kind)
+    b.set_option(gbfd.GBFD_BATCH_OPT_DATAFLOW, 1)
+    for i, st in enumerate(sts):
+        b.set_state(i, st)
+    b.set_option(gbfd.GBFD_BATCH_OPT_FAULT_STALL, 0)  # box 0, first column, first substep
+    b.step([0.01, 0.01], 1)
+    with pytest.raises(gbfd.GbfdError) as err:
+        b.sync()
+    assert err.value.status == 4  # GBFD_ERR_TIMEOUT
+    b.set_option(gbfd.GBFD_BATCH_OPT_FAULT_STALL, -1)
+    b.sync()  # the error word was cleared
+    for i, st in enumerate(sts):
+        b.set_state(i, st)
+    b.step([0.01, 0.01], 1)
+    b.sync()
+    for i, (n, st) in enumerate(zip(ns, sts)):
+        g = fd.Grid(n, n, n)
+        ref = fd.rk3_step(st.astype(np.float64), 0.01, g, fd.Physics(cs=1.0, nu=5e-3))
+        assert np.all(rel_l2(b.get_state(i), ref) <= FP32_TOL)
     b.close()
 
 
