@@ -95,7 +95,7 @@ __device__ __forceinline__ bool run_item(const BoxDesc *__restrict__ B, const in
     const float beta = s == 0 ? (float)(1.0 / 3.0) : (s == 1 ? (float)(15.0 / 16.0)
                                                             : (float)(8.0 / 15.0));
     if constexpr (KIND == KIND_LAG) {
-        return tiled4::run_column<float, float, NF, TX, TY, NS, U, false, false, 1>(
+        return tiled4::run_column<float, float, NF, TX, TY, NS, U, false, false, true>(
             &B->tm_state[wi][parity], &B->tm_w[wi], B->state[parity ^ 1], B->w, L, L, scoef,
             alpha, beta, dt, s == 0, s == 2, item.y, item.z, item.w, nout, jrun, wrun, smem,
             dev_error, -1, nullptr, tmem);

@@ -35,10 +35,12 @@ constexpr int kZcChoices = 4;
 //      per iteration
 //   3  the same with one step per iteration
 //   4  the same as 2 with the pending right-hand sides in TMEM (default)
-//   5  the same as 4, shared loads free to move across the TMEM accesses
-//   6  the same as 4 compiled for three CTAs per SM (168 registers)
+//   5  the same as 4 compiled for three CTAs per SM (168 registers; slower:
+//      13.3 against 19.2 G updates/s at 256^3, spills and still two CTAs per
+//      SM, whose shared memory the ring fills; kept as the check that its
+//      TMEM accesses are right since the warps are reconverged before them)
 constexpr int kVarPx1 = 0, kVarPacked = 1, kVarLagReg = 2, kVarLagReg1 = 3, kVarLagTm = 4,
-              kVarLagTmFree = 5, kVarLagTmCap = 6;
+              kVarLagTmCap = 5;
 constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 
 // Default FP64 table entry (see tiled_f64.cu): the one-point kernel on

@@ -45,73 +45,43 @@ constexpr int kTmCols = 4 * kTmSlotCols;
 // Warp-collective 32x32b accesses of n consecutive columns of the thread's
 // own lane, each waiting for its own completion in the same statement.  They
 // are .sync.aligned: the warp is reconverged first, since the bounded
-// mbarrier spins before them exit lane by lane.  MC: with a "memory" clobber
-// (the compiler then keeps every shared-memory access on its side of the
-// statement); without it (TMEM is not generic memory) the compiler may move
-// shared loads across the statement.
-template <bool MC>
+// mbarrier spins before them exit lane by lane (without it, a register-capped
+// build of this kernel read back wrong values).
 __device__ __forceinline__ void tm_st8(uint32_t ta, const float2 *v)
 {
     __syncwarp();
-    if constexpr (MC)
-        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
-                     "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
-                     "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y),
-                     "f"(v[3].x), "f"(v[3].y)
-                     : "memory");
-    else
-        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
-                     "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
-                     "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y),
-                     "f"(v[3].x), "f"(v[3].y));
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n\t"
+                 "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
+                 "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y),
+                 "f"(v[3].x), "f"(v[3].y)
+                 : "memory");
 }
-template <bool MC>
 __device__ __forceinline__ void tm_st2(uint32_t ta, const float2 v)
 {
     __syncwarp();
-    if constexpr (MC)
-        asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n\t"
-                     "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
-                     "f"(v.x), "f"(v.y)
-                     : "memory");
-    else
-        asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n\t"
-                     "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
-                     "f"(v.x), "f"(v.y));
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};\n\t"
+                 "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
+                 "f"(v.x), "f"(v.y)
+                 : "memory");
 }
-template <bool MC>
 __device__ __forceinline__ void tm_ld8(uint32_t ta, float2 *v)
 {
     __syncwarp();
-    if constexpr (MC)
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
-                     "tcgen05.wait::ld.sync.aligned;"
-                     : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x),
-                       "=f"(v[2].y), "=f"(v[3].x), "=f"(v[3].y)
-                     : "r"(ta)
-                     : "memory");
-    else
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
-                     "tcgen05.wait::ld.sync.aligned;"
-                     : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x),
-                       "=f"(v[2].y), "=f"(v[3].x), "=f"(v[3].y)
-                     : "r"(ta));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x),
+                   "=f"(v[2].y), "=f"(v[3].x), "=f"(v[3].y)
+                 : "r"(ta)
+                 : "memory");
 }
-template <bool MC>
 __device__ __forceinline__ void tm_ld2(uint32_t ta, float2 &v)
 {
     __syncwarp();
-    if constexpr (MC)
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
-                     "tcgen05.wait::ld.sync.aligned;"
-                     : "=f"(v.x), "=f"(v.y)
-                     : "r"(ta)
-                     : "memory");
-    else
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
-                     "tcgen05.wait::ld.sync.aligned;"
-                     : "=f"(v.x), "=f"(v.y)
-                     : "r"(ta));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "r"(ta)
+                 : "memory");
 }
 
 // Shared-memory carve-up: NS state-plane slots, NW u-tilde slots, barriers.
@@ -125,7 +95,7 @@ struct RingL : tiled2::Ring<float, TW, NF, TX, TY, NS, U + 2> {
 // One z-chunk of one column; same contract as the two-point kernel's column
 // routine (barrier phases continue across calls through jrun / wrun; false
 // when a bounded wait gave up).
-template <class TW, class TA, int NF, int TX, int TY, int NS, int U, bool ICVT, bool FORCE, int TM,
+template <class TW, class TA, int NF, int TX, int TY, int NS, int U, bool ICVT, bool FORCE, bool TM,
           class CoefT>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            float *__restrict__ out, TW *__restrict__ w,
@@ -458,9 +428,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         V prv[NF];
         if constexpr (TM) {
             const uint32_t ta = trow + (uint32_t)((o & 3) * kTmSlotCols);
-            tm_ld8<TM == 1>(ta, prv);
+            tm_ld8(ta, prv);
             if constexpr (NF == 5)
-                tm_ld2<TM == 1>(ta + 8, prv[4]);
+                tm_ld2(ta + 8, prv[4]);
         } else {
 #pragma unroll
             for (int f = 0; f < NF; ++f)
@@ -566,9 +536,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         centre(cb, sc, prn);
         if constexpr (TM) {
             const uint32_t ta = trow + (uint32_t)(((s - R) & 3) * kTmSlotCols);
-            tm_st8<TM == 1>(ta, prn);
+            tm_st8(ta, prn);
             if constexpr (NF == 5)
-                tm_st2<TM == 1>(ta + 8, prn[4]);
+                tm_st2(ta + 8, prn[4]);
         } else {
 #pragma unroll
             for (int f = 0; f < NF; ++f)
@@ -686,7 +656,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 // every axis (10 stencil weights instead of 30, few enough to stay in uniform
 // registers).
 template <class TW, class TA, int NF, int TX, int TY, int NS, int U, int MINB, bool ICVT,
-          bool FORCE, int TM, class CoefT>
+          bool FORCE, bool TM, class CoefT>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     float *__restrict__ out, TW *__restrict__ w, const Layout Ls, const Layout Lw,
@@ -728,7 +698,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
 }  // namespace tiled4
 
 // Launch of the lagged-output kernel for the 55-point form (form 0 only).
-template <class TW, class TA, int TX, int TY, int NS, int U, int TM = 0, int MINB = 1,
+template <class TW, class TA, int TX, int TY, int NS, int U, bool TM = false, int MINB = 1,
           bool ICVT = false>
 cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKStage &st, int nf,
                            int zc, int cfg_key, int *dev_error, TmapCache *cache,

@@ -36,13 +36,10 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         e = launch_lag_cfg<TW, TA, 32, 8, 8, 1>(b, c, st, nf, t.zc, v, dev_error, cache, stream,
                                                  launches);
     } else if (v == kVarLagTm) {
-        e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, 1>(b, c, st, nf, t.zc, v, dev_error, cache,
-                                                    stream, launches);
-    } else if (v == kVarLagTmFree) {
-        e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, 2>(b, c, st, nf, t.zc, v, dev_error, cache,
+        e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, true>(b, c, st, nf, t.zc, v, dev_error, cache,
                                                     stream, launches);
     } else {
-        e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, 1, 3>(b, c, st, nf, t.zc, v, dev_error, cache,
+        e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, true, 3>(b, c, st, nf, t.zc, v, dev_error, cache,
                                                        stream, launches);
     }
     if (e != cudaSuccess || form == 0)

@@ -16,7 +16,7 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         return cudaErrorNotSupported;
     const int idx = cfg < 0 ? kDefaultF32 : cfg;
     const TileConfig t = tiled_config(4, idx);
-    return launch_lag_cfg<TW, TA, 32, 8, 8, 2, 1>(b, c, st, nf, t.zc, kVarLagTm, dev_error, cache,
+    return launch_lag_cfg<TW, TA, 32, 8, 8, 2, true>(b, c, st, nf, t.zc, kVarLagTm, dev_error, cache,
                                                    stream, launches);
 }
 
