@@ -177,6 +177,41 @@ def evaluate(net, seeds, n_fine, ratio, nsteps, nu=5e-3, k2=8, mach_range=(0.1, 
     return res
 
 
+def device_cost(net, n_fine, ratio, nsteps, nu=5e-3, k2=8):
+    """GPU time per step of the fine, plain coarse and corrected coarse runs,
+    each `nsteps` (fine: ratio x nsteps) steps back to back on one stream
+    after a warm-up: the device cost, without the host time between the
+    evaluation's timed segments."""
+    import torch
+    nc = n_fine // ratio
+    st, _ = _spectrum_state(n_fine, 1200, k2, (0.1, 0.3))
+    fine = gbfd.Solver((n_fine,) * 3, precision="fp32", nu=nu)
+    fine.set_state(st)
+    dt_f = fine.cfl_dt(0.4)
+    c0 = gbfd.box_filter(fine, ratio)
+    plain = gbfd.Solver((nc,) * 3, precision="fp32", nu=nu)
+    corr = gbfd.Solver((nc,) * 3, precision="fp32", nu=nu)
+    plain.set_state(c0)
+    corr.set_state(c0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, n):
+        fn(3)
+        torch.cuda.synchronize()
+        ev[0].record()
+        fn(n)
+        ev[1].record()
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) / n
+
+    out = {"fine": timed(lambda n: fine.rk3_step(dt_f, n), ratio * nsteps),
+           "plain": timed(lambda n: plain.rk3_step(ratio * dt_f, n), nsteps),
+           "corrected": timed(lambda n: net.step_corrected(corr, ratio * dt_f, n), nsteps)}
+    for s in (fine, plain, corr):
+        s.close()
+    return out
+
+
 def run(fine=256, ratio=4, train_seeds=200, eval_seeds=20, nsnap=10, gap=None, steps=200,
         train_steps=4000, batch=8, lr=3e-4, nu=5e-3, k2=8, seed=0, check_every=25, noise=1.0):
     """The full pipeline; returns a JSON-able summary."""
@@ -203,6 +238,7 @@ def run(fine=256, ratio=4, train_seeds=200, eval_seeds=20, nsnap=10, gap=None, s
     loss1 = set_loss()
     ev = evaluate(net, range(1200, 1200 + eval_seeds), fine, ratio, steps, nu, k2,
                   check_every=check_every)
+    dev = device_cost(net, fine, ratio, steps, nu, k2)
     mean = lambda v: float(np.mean(v)) if v else None
     return {
         "fine": fine, "coarse": nc, "ratio": ratio, "train_pairs": int(xs.shape[0]),
@@ -216,6 +252,7 @@ def run(fine=256, ratio=4, train_seeds=200, eval_seeds=20, nsnap=10, gap=None, s
         "rel_l2_lnrho_corrected": mean(ev["corrected_lnrho"]),
         "ms_fine_total": ev["ms_fine"], "ms_plain_total": ev["ms_plain"],
         "ms_corrected_total": ev["ms_corrected"], "error_curves": ev["curve"],
+        "device_ms_per_step": dev,
     }
 
 
