@@ -274,20 +274,23 @@ bool write_cache(const char *path, const std::map<std::string, std::pair<int, do
 // planes falling from 15% to 9%); else 40 when that still makes at least
 // four waves (fewest halo planes, and 7 chunks of a 256 column fill 5.9
 // waves where 8 chunks of 32 fill 6.7); else 32 when that fills at least
-// half a wave; else 16, so that small grids keep their SMs busy.  Measured
-// best at 64^3 (16), 128^3 (32), 256^3 (40) and 512^3 (64).
+// half a wave; else 16 when that fills a quarter; else 8, so that small grids
+// (64^3: 128 CTAs of 8 planes) keep more SMs busy and each CTA's plane
+// pipeline short.  Measured best at 128^3 (32), 256^3 (40) and 512^3 (64).
 int fp32_default_cfg(const gbfd_ctx *c)
 {
     const long long slots = 2LL * c->sms;
     const long long tiles = (long long)((c->p.nx + 31) / 32) * ((c->p.ny + 7) / 8);
-    // positions of 40, 32, 64 and 16 in the tile table's chunk list
+    // positions of 40, 32, 64, 16 and 8 in the tile table's chunk list
     if (tiles * ((c->p.nz + 63) / 64) >= 16 * slots)
         return kDefaultF32 + 2;
     if (tiles * ((c->p.nz + 39) / 40) >= 4 * slots)
         return kDefaultF32;
     if (2 * tiles * ((c->p.nz + 31) / 32) >= slots)
         return kDefaultF32 + 1;
-    return kDefaultF32 + 3;
+    if (4 * tiles * ((c->p.nz + 15) / 16) >= slots)
+        return kDefaultF32 + 3;
+    return kDefaultF32 + 4;
 }
 
 gbfd_status do_substep(gbfd_ctx *c, int s, double dt)

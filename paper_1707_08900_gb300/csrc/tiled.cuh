@@ -22,7 +22,7 @@ struct TileConfig {
 
 // Number of z-chunk lengths offered per (tx, ty, ns) variant; table index
 // i is variant i / kZcChoices with the (i % kZcChoices)-th chunk length.
-constexpr int kZcChoices = 4;
+constexpr int kZcChoices = 5;
 
 // FP32 tile table (55-point form; the 19-point form runs the two-plane
 // packed kernel for variants 1-4):
@@ -46,7 +46,7 @@ constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 // Default FP64 table entry (see tiled_f64.cu): the one-point kernel on
 // 16 x 8 tiles, z-chunks of 40 (2% faster than 32 x 4 at 256^3; the FP64
 // pipe is the bound, about 80% busy).
-constexpr int kDefaultF64 = 4;
+constexpr int kDefaultF64 = 1 * kZcChoices;
 
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);

@@ -19,7 +19,7 @@ const TileConfig kVariants4[] = {{32, 8, 0, 9, 1},
                                  {32, 8, 0, 8, 2, 2, 1, 1}};
 const TileConfig kVariants8[] = {{32, 4, 0, 8, 1}, {16, 8, 0, 8, 1}, {32, 4, 0, 6, 2, 1},
                                  {32, 4, 0, 5, 2, 2}, {32, 8, 0, 5, 2, 1}};
-const int kZc[kZcChoices] = {40, 32, 64, 16};
+const int kZc[kZcChoices] = {40, 32, 64, 16, 8};
 constexpr int kNz = kZcChoices;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()

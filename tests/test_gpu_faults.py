@@ -22,8 +22,8 @@ def _gpu():
     build.build()
 
 
-@pytest.mark.parametrize("cfg,report", [(-1, "sync"), (-1, "get_state"), (8, "sync"),
-                                        (16, "get_state")])
+@pytest.mark.parametrize("cfg,report", [(-1, "sync"), (-1, "get_state"), (10, "sync"),
+                                        (20, "get_state")])
 def test_bounded_wait_times_out_and_context_recovers(cfg, report):
     """The default kernel and the lagged-output kernels (registers, tensor
     memory); the timeout is reported by gbfd_sync or by gbfd_get_state to

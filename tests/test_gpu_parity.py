@@ -213,8 +213,8 @@ def test_diagnostics_match_oracle():
     s.close()
 
 
-@pytest.mark.parametrize("cfg,iso", [(-1, False), (-1, True), (4, False), (8, False),
-                                     (13, False), (16, False), (16, True)])
+@pytest.mark.parametrize("cfg,iso", [(-1, False), (-1, True), (5, False), (10, False),
+                                     (16, False), (20, False), (20, True), (24, True)])
 def test_roll_equivariance_bitwise_fp32(cfg, iso):
     """Rolling the input rolls the output bit for bit: every point runs the
     same arithmetic whatever tile, chunk or periodic edge it falls in (the
@@ -240,8 +240,9 @@ def test_roll_equivariance_bitwise_fp32(cfg, iso):
                                        "fp32_accff"])
 def test_every_tile_config_matches_oracle(precision):
     """Every entry of the tile table (one and two points per thread, all
-    z-chunk lengths) reproduces the oracle on a ragged grid; the precision
-    forms have two kernels (packed two-point, one-point) x 4 chunk lengths."""
+    z-chunk lengths) reproduces the oracle on a ragged grid; the FP64-update
+    precision forms have three kernels x 5 chunk lengths, the float-float
+    form one kernel x 5."""
     from paper_1707_08900_gb300 import gbfd
     shape = (20, 44, 36)
     g = _grid(shape)
@@ -253,7 +254,7 @@ def test_every_tile_config_matches_oracle(precision):
     ref = fd.rk3_step(st, dt, g, ph)
     tol = FP64_TOL if precision == "fp64" else FP32_TOL
     n = 0
-    for cfg in range({"fp32_acc64": 12, "fp32_acc64_w64": 12, "fp32_accff": 4}.get(precision, 256)):
+    for cfg in range({"fp32_acc64": 15, "fp32_acc64_w64": 15, "fp32_accff": 5}.get(precision, 256)):
         s = _solver(shape, precision=precision, nu=0.01)
         try:
             s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
@@ -270,7 +271,7 @@ def test_every_tile_config_matches_oracle(precision):
         else:
             _check_fp32(got, ref, st, f"cfg {cfg}")
         n += 1
-    assert n >= {"fp64": 20, "fp32": 20, "fp32_accff": 4}.get(precision, 12)
+    assert n >= {"fp64": 25, "fp32": 30, "fp32_accff": 5}.get(precision, 15)
 
 
 @pytest.mark.parametrize("iso", [False, True])
@@ -297,9 +298,9 @@ def test_lagged_output_kernel_on_ragged_chunks(shape, iso):
         dt = fd.cfl_dt(st, g, ph, 0.4)
         ref = fd.rk3_step(st, dt, g, ph)
         for v in (2, 3, 4, 5):
-            for zi in range(4):
+            for zi in range(5):
                 s = _solver(shape, precision="fp32", nu=0.01, entropy_mode=em, lengths=lengths)
-                s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, 4 * v + zi)
+                s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, 5 * v + zi)
                 s.set_state(st)
                 s.rk3_step(dt, 1)
                 got = s.get_state()
@@ -310,7 +311,7 @@ def test_lagged_output_kernel_on_ragged_chunks(shape, iso):
 @pytest.mark.parametrize("iso", [False, True])
 def test_lagged_kernel_tmem_and_isotropic_paths_are_bit_identical(iso):
     """The lagged-output kernel keeps its pending right-hand sides in
-    registers (table 8) or in TMEM (table 16, which on equal spacings also
+    registers (table 10) or in TMEM (table 20, which on equal spacings also
     takes the isotropic weights): storage does not round and the weights
     are the same values, so the two give the same bits."""
     from paper_1707_08900_gb300 import gbfd
@@ -318,7 +319,7 @@ def test_lagged_kernel_tmem_and_isotropic_paths_are_bit_identical(iso):
     lengths = (64 * 0.1, 40 * 0.1, 24 * 0.1) if iso else (2 * np.pi,) * 3
     st = inputs.spectrum(shape, 14, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
     outs = []
-    for cfg in (8, 16):
+    for cfg in (10, 20):
         s = _solver(shape, precision="fp32", nu=5e-3, lengths=lengths)
         s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
         s.set_state(st)

@@ -76,7 +76,7 @@ def test_every_fp32_tile_entry_runs_forced_on_the_default_kernel():
     st = inputs.spectrum(shape, 8, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
     ks, phis, es = inputs.forcing_sequence(9, 2)
     outs = []
-    for cfg in (-1, 0, 4, 8, 12):
+    for cfg in (-1, 0, 5, 10, 15):
         s = gbfd.Solver(shape, precision="fp32", nu=5e-3)
         s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
         s.set_state(st)
