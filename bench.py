@@ -372,8 +372,21 @@ def run_ours(args):
         errs[prec] = [float(np.linalg.norm((x[f] - ref64[f]).ravel())
                             / np.linalg.norm(ref64[f].ravel())) for f in range(4)]
     del ref64
+    # the 19-point form the same way: FP32 against FP64, both 19-point
+    s19 = make("fp64", "19p")
+    s19.rk3_step(dt, nerr)
+    ref19 = s19.get_state()
+    s19.close()
+    s2 = make("fp32", "19p")
+    s2.rk3_step(dt, nerr)
+    x = s2.get_state()
+    s2.close()
+    errs19 = [float(np.linalg.norm((x[f] - ref19[f]).ravel()) / np.linalg.norm(ref19[f].ravel()))
+              for f in range(4)]
+    del ref19, x
     extra["error_vs_fp64"] = {"steps": nerr, "grid": "256^3",
-                              "rel_l2_lnrho_ux_uy_uz": errs}
+                              "rel_l2_lnrho_ux_uy_uz": errs,
+                              "rel_l2_lnrho_ux_uy_uz_19p": {"fp32": errs19}}
     extra["fp32_vs_fp64_speedup"] = round(value / world / v64, 2)
 
     # ---- FP32, 19-point two-pass form
