@@ -180,11 +180,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait that also gives up when another role has raised the CTA's
-// abort flag; a wait that runs out (about 2 s) raises it.  BACKOFF: sleep
-// briefly between polls (the epilogue warps, so that their polling leaves
-// the issue slots to the loading and MMA-issuing warps on the same
-// scheduler).
-template <bool BACKOFF = false>
+// abort flag; a wait that runs out (about 2 s) raises it.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
 {
     if (tiled::mbar_try_wait(bar, parity))
@@ -199,8 +195,6 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
             *abort = 1;
             return false;
         }
-        if constexpr (BACKOFF)
-            __nanosleep(64);
     }
 }
 
@@ -305,24 +299,20 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 tc::fence_after_sync();
                 const uint64_t adst = ad0 + (uint64_t)((s * SM::A_PITCH) >> 4);
                 const uint32_t dt0 = tmem + acc * SM::ACC_COLS;
-                // taps in a short loop (a fully unrolled issue sequence of
-                // 27 ZB KSTEPS MMAs made the kernel's code large enough to
-                // miss in the instruction cache); the per-tap offset is a few
-                // integer operations
-#pragma unroll 1
-                for (int tap = 0; tap < TAPS; ++tap) {
-                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // offset + 1
-                    const uint64_t at = adst + (uint64_t)((((dz * HY + dy) * HX + dx) * 16) >> 4);
-                    const uint64_t bt = bd0 + (uint64_t)(tap * KSTEPS * 16);
 #pragma unroll
-                    for (int zb = 0; zb < ZB; ++zb)
+                for (int zb = 0; zb < ZB; ++zb)
 #pragma unroll
-                        for (int k = 0; k < KSTEPS; ++k)
-                            tc::mma_bf16(dt0 + zb * N,
-                                         at + (uint64_t)(((zb * HY * HX) * 16 + 2 * k * SM::CS) >> 4),
-                                         bt + (uint64_t)(k * 16), idesc,
+                    for (int tap = 0; tap < TAPS; ++tap) {
+                        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // offset + 1
+#pragma unroll
+                        for (int k = 0; k < KSTEPS; ++k) {
+                            const int aoff =
+                                ((((zb + dz) * HY + dy) * HX + dx) * 16 + 2 * k * SM::CS) >> 4;
+                            tc::mma_bf16(dt0 + zb * N, adst + (uint64_t)aoff,
+                                         bd0 + (uint64_t)((tap * KSTEPS + k) * 16), idesc,
                                          (tap > 0 || k > 0) ? 1u : 0u);
-                }
+                        }
+                    }
                 tc::commit(&empty[s]);
                 tc::commit(&accf[acc]);
                 cnt[2] = i + 1;
@@ -338,11 +328,6 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         const int r = q * 32 + lane;  // row of the M block = TMEM lane
         const int lx = r % TXT, ly = r / TXT;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + c0;
-        // this warp's biases, loaded once
-        float bias[NH];
-#pragma unroll
-        for (int j = 0; j < NH; ++j)
-            bias[j] = (EPI == EPI_DGELU || c0 + j >= N) ? 0.f : __ldg(a.bias + c0 + j);
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int acc = i % NACC;
@@ -350,7 +335,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             // warp-collective)
             int ok = 0;
             if (lane == 0)
-                ok = wait_or_abort<true>(&accf[acc], (i / NACC) & 1, abort);
+                ok = wait_or_abort(&accf[acc], (i / NACC) & 1, abort);
             if (!__shfl_sync(0xffffffffu, ok, 0))
                 break;
             // the other lanes observe the completed phase too (it cannot
@@ -385,9 +370,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     // five real output channels, all in the first half
                     if (c0 == 0) {
                         float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
-                        yo[0] = make_float4(v[zb][0] + bias[0], v[zb][1] + bias[1],
-                                            v[zb][2] + bias[2], v[zb][3] + bias[3]);
-                        yo[1] = make_float4(v[zb][4] + bias[4], 0.f, 0.f, 0.f);
+                        yo[0] = make_float4(v[zb][0] + __ldg(a.bias + 0), v[zb][1] + __ldg(a.bias + 1),
+                                            v[zb][2] + __ldg(a.bias + 2), v[zb][3] + __ldg(a.bias + 3));
+                        yo[1] = make_float4(v[zb][4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
                     }
                 } else {
                     uint4 out[NH / 8];
@@ -397,7 +382,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                         if constexpr (EPI == EPI_GELU) {
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
-                                h[j] = v[zb][c + j] + bias[c + j];
+                                h[j] = v[zb][c + j] + __ldg(a.bias + c0 + c + j);
                             if (a.hsave) {
                                 float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * N + c0 + c);
                                 hs[0] = make_float4(h[0], h[1], h[2], h[3]);

@@ -526,7 +526,7 @@ def test_integer_conversions_match_hardware_bitwise(precision, form):
     flat[idx] = np.resize(special, 60)
     for st in (base, salted):
         outs = []
-        for cfg in (0, 8):
+        for cfg in (0, 10):
             s = _solver(shape, precision=precision, form=form, nu=5e-3)
             s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
             s.set_state(st)
