@@ -460,6 +460,21 @@ def run_ours(args):
                                       "after every substep"}
     s.close()
 
+    # ---- the headline kernel with its x neighbours exchanged by warp shuffles
+    # (tile table entry 30: the same kernel, z-chunk and grid as the default
+    # entry, paired shared loads replaced by shuffles and halo quads)
+    ksh = max(3, args.steps // 8)
+    s = make("fp32", "55p")
+    s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, 30)
+    s.rk3_step(dt, 2)
+    torch.cuda.synchronize()
+    mssh, _ = timed_steps(s, dt, ksh, stream, torch)
+    extra["fp32_55p_shfl"] = {"value": world * npts * ksh / (max_over_ranks_(mssh) * 1e-3),
+                              "steps": ksh, "ms_per_step": mssh / ksh,
+                              "what": "default kernel with warp-shuffle x neighbours "
+                                      "(tile table entry 30)"}
+    s.close()
+
     # ---- precision form: FP32 stencil, FP64 RK3 registers
     kacc = max(3, args.steps // 4)
     s = make("fp32_acc64", "55p")

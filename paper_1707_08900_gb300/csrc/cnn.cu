@@ -8,8 +8,8 @@
 //   shared memory as K-major core matrices, FP32 accumulators in TMEM.
 // * A persistent, warp-specialised CTA per SM: one warp loads each tile's
 //   input plus its periodic one-point halo with ONE TMA box into a
-//   double-buffered ring, one thread issues the tile's 27 taps as MMAs from
-//   shifted descriptors into one of two TMEM accumulator buffers, and four
+//   three-stage ring, one thread issues the tile's 27 taps as MMAs from
+//   shifted descriptors into one of two TMEM accumulator buffers, and eight
 //   epilogue warps read the other buffer (bias, GELU or GELU', BF16 stores),
 //   so loads, MMAs and epilogues of consecutive tiles overlap.  The weights
 //   (B operand) stay in shared memory.  Activations are kept in a padded,
@@ -48,7 +48,6 @@ using bf16 = __nv_bfloat16;
 
 constexpr int TAPS = 27;
 constexpr int MT = 128;    // points per tile (MMA M)
-constexpr int NTHR = 128;  // threads per conv CTA (4 warps = 128 TMEM lanes)
 constexpr int NC = 5;      // physical channels (lnrho, u_x, u_y, u_z, s)
 constexpr int C0 = 16;     // padded input channels of layer 1
 constexpr int CH = 32;     // hidden channels

@@ -39,8 +39,11 @@ constexpr int kZcChoices = 5;
 //      13.3 against 19.2 G updates/s at 256^3, spills and still two CTAs per
 //      SM, whose shared memory the ring fills; kept as the check that its
 //      TMEM accesses are right since the warps are reconverged before them)
+//   6  the same as 4 with the x-neighbour pairs of the x arms taken from the
+//      neighbouring lanes by warp shuffles instead of paired shared loads
+//      (tiled_shfl.cu)
 constexpr int kVarPx1 = 0, kVarPacked = 1, kVarLagReg = 2, kVarLagReg1 = 3, kVarLagTm = 4,
-              kVarLagTmCap = 5;
+              kVarLagTmCap = 5, kVarLagTmShfl = 6;
 constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 
 // Default FP64 table entry (see tiled_f64.cu): the one-point kernel on
@@ -64,6 +67,11 @@ struct TmapCache {
     } e[kEntries];
     int next;
 };
+
+// Table variant 6 (FP32 storage and arithmetic, 55-point form).
+cudaError_t launch_lag_shfl(const StateBufs &b, const Coef<float> &c, const RKStage &st, int nf,
+                            int zc, int cfg_key, int *dev_error, TmapCache *cache,
+                            cudaStream_t stream, int *launches);
 
 template <class TS, class TW, class TA>
 cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RKStage &st, int nf,

@@ -96,7 +96,7 @@ struct RingL : tiled2::Ring<float, TW, NF, TX, TY, NS, U + 2> {
 // routine (barrier phases continue across calls through jrun / wrun; false
 // when a bounded wait gave up).
 template <class TW, class TA, int NF, int TX, int TY, int NS, int U, bool ICVT, bool FORCE, bool TM,
-          class CoefT>
+          class CoefT, bool SHFL = false>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            float *__restrict__ out, TW *__restrict__ w,
                                            const Layout &Ls, const Layout &Lw, const CoefT &c,
@@ -210,11 +210,55 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         }
     };
     // x-differences h_k (k = 1..3) of both points from the pairs of a row at
-    // x offsets -4, -2, +2, +4 and the centre pair
+    // x offsets -4, -2, +2, +4 and the centre pair (of the outer pairs only
+    // m4.y and p4.x enter, here and in the second derivative)
     auto xdiff = [&](V m4, V m2, V cc, V p2, V p4, V *h) {
         h[0] = P::mk(cc.y - m2.y, p2.x - cc.x);
         h[1] = P::fma(m2, NEG1, p2);
         h[2] = P::mk(p2.y - m4.y, p4.x - m2.x);
+    };
+    // the x-neighbour pairs of the centre pair cc at shared-memory index fb
+    // (the pair's own element): SHFL takes them from the lanes that hold them
+    // (a row is NTX consecutive lanes), and the two lanes at each end of the
+    // row the missing ones from one 16-byte load of the four halo values on
+    // their side; otherwise four paired shared loads
+    auto xnb = [&](int fb, V cc, V &m4, V &m2, V &p2, V &p4) {
+        if constexpr (SHFL) {
+            static_assert(NTX == 16 || NTX == 32, "a row within one warp");
+            static_assert(GX == 4 && RG::BX % 4 == 0 && RG::FSTRIDE % 4 == 0 &&
+                              RG::SLOT_ELEMS % 4 == 0,
+                          "16-byte aligned halo quads");
+            constexpr unsigned ALL = 0xffffffffu;
+            m2.x = __shfl_up_sync(ALL, cc.x, 1, NTX);
+            m2.y = __shfl_up_sync(ALL, cc.y, 1, NTX);
+            m4.y = __shfl_up_sync(ALL, cc.y, 2, NTX);
+            p2.x = __shfl_down_sync(ALL, cc.x, 1, NTX);
+            p2.y = __shfl_down_sync(ALL, cc.y, 1, NTX);
+            p4.x = __shfl_down_sync(ALL, cc.x, 2, NTX);
+            m4.x = p4.y = 0.f;
+            const bool lo = tx < 2, hi = tx >= NTX - 2;
+            if (lo || hi) {
+                // the row's halo columns: x offsets -4..-1 or TX..TX+3 of the tile
+                const int rb = fb - 2 * tx - GX + (lo ? 0 : GX + TX);
+                const float4 e = *reinterpret_cast<const float4 *>(sm + rb);
+                if (tx == 0) {
+                    m4.y = e.y;
+                    m2 = make_float2(e.z, e.w);
+                } else if (tx == 1) {
+                    m4.y = e.w;
+                } else if (tx == NTX - 1) {
+                    p2 = make_float2(e.x, e.y);
+                    p4.x = e.z;
+                } else {
+                    p4.x = e.x;
+                }
+            }
+        } else {
+            m4 = *reinterpret_cast<const V *>(sm + fb - 4);
+            m2 = *reinterpret_cast<const V *>(sm + fb - 2);
+            p2 = *reinterpret_cast<const V *>(sm + fb + 2);
+            p4 = *reinterpret_cast<const V *>(sm + fb + 4);
+        }
     };
     // a plane that is not a centre (the halo planes of the chunk): its arm
     // differences alone, from its own loads; centre pairs from colv[.][MC]
@@ -223,9 +267,10 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         auto at = [&](int f, int dy, int dx) -> V {
             return *reinterpret_cast<const V *>(sm + base + f * FSTRIDE + dy * BX + dx);
         };
-        V h[3], gd[3];
+        V h[3], gd[3], m4, m2, p2, p4;
         // u_x: x-differences -> z component
-        xdiff(at(1, 0, -4), at(1, 0, -2), colv[1][MC], at(1, 0, 2), at(1, 0, 4), h);
+        xnb(base + FSTRIDE, colv[1][MC], m4, m2, p2, p4);
+        xdiff(m4, m2, colv[1][MC], p2, p4, h);
         spread(acz, h, 1, mcc);
         // u_y: y-differences -> z component
 #pragma unroll
@@ -233,7 +278,8 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
             gd[k - 1] = P::fma(at(2, -k, 0), NEG1, at(2, k, 0));
         spread(acz, gd, 2, mcc);
         // u_z: x-differences -> x component, y-differences -> y component
-        xdiff(at(3, 0, -4), at(3, 0, -2), colv[3][MC], at(3, 0, 2), at(3, 0, 4), h);
+        xnb(base + 3 * FSTRIDE, colv[3][MC], m4, m2, p2, p4);
+        xdiff(m4, m2, colv[3][MC], p2, p4, h);
         spread(acx, h, 1, mcc);
 #pragma unroll
         for (int k = 1; k <= 3; ++k)
@@ -287,8 +333,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
         };
         V g[3], d2[3], h[3], gd[3], y1p, y1m;
         auto axial = [&](int f, bool second) {
-            const V m4 = ld2(f, 0, -4), m2 = ld2(f, 0, -2), p2 = ld2(f, 0, 2), p4 = ld2(f, 0, 4);
             const V cc = C(f, 3);
+            V m4, m2, p2, p4;
+            xnb(cb + f * FSTRIDE, cc, m4, m2, p2, p4);
             xdiff(m4, m2, cc, p2, p4, h);
             g[0] = P::fma(P::bc(c.D1(0, 3)), h[2],
                           P::fma(P::bc(c.D1(0, 2)), h[1], P::mul(P::bc(c.D1(0, 1)), h[0])));
@@ -656,7 +703,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 // every axis (10 stencil weights instead of 30, few enough to stay in uniform
 // registers).
 template <class TW, class TA, int NF, int TX, int TY, int NS, int U, int MINB, bool ICVT,
-          bool FORCE, bool TM, class CoefT>
+          bool FORCE, bool TM, class CoefT, bool SHFL>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     float *__restrict__ out, TW *__restrict__ w, const Layout Ls, const Layout Lw,
@@ -682,7 +729,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TW, TA, NF, TX, TY, NS, U, ICVT, FORCE, TM>(
+    run_column<TW, TA, NF, TX, TY, NS, U, ICVT, FORCE, TM, CoefT, SHFL>(
         &tmap, &wmap, out, w, Ls, Lw, c, (TA)st.alpha, (TA)st.beta, (TA)st.dt, st.first != 0,
         st.last != 0, x0, y0, z0, nout, jrun, wrun, smem, dev_error,
         blockIdx.x == 0 && blockIdx.y == 0 ? skip_plane : -1, &st.fo, tmem);
@@ -699,7 +746,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
 
 // Launch of the lagged-output kernel for the 55-point form (form 0 only).
 template <class TW, class TA, int TX, int TY, int NS, int U, bool TM = false, int MINB = 1,
-          bool ICVT = false>
+          bool ICVT = false, bool SHFL = false>
 cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKStage &st, int nf,
                            int zc, int cfg_key, int *dev_error, TmapCache *cache,
                            cudaStream_t stream, int *launches)
@@ -722,7 +769,8 @@ cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKSta
     const CubicCoef<float> cc = cubic_of(c);
 #define GBFD_LAUNCH_LAG_C(NFV, FRC, CT, CV)                                                       \
     do {                                                                                          \
-        auto kern = tiled4::k_substep_lag<TW, TA, NFV, TX, TY, NS, U, MINB, ICVT, FRC, TM, CT>;   \
+        auto kern = tiled4::k_substep_lag<TW, TA, NFV, TX, TY, NS, U, MINB, ICVT, FRC, TM, CT,    \
+                                          SHFL>;                                                  \
         constexpr int sm = tiled4::RingL<TW, NFV, TX, TY, NS, U>::BYTES;                          \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \

@@ -3,7 +3,7 @@
 // kernel, the two-plane packed two-point kernel, and the kernel that
 // finishes output planes three planes behind the in-plane work (pending
 // right-hand sides in registers, two or one steps per iteration, or in TMEM:
-// the default).  The z-chunk length comes from the table entry; the API picks
+// the default; its warp-shuffle variant is compiled in tiled_shfl.cu).  The z-chunk length comes from the table entry; the API picks
 // the default entry's chunk per grid (fp32_default_cfg in api.cu).
 #include "tiled4_impl.cuh"
 
@@ -38,9 +38,11 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     } else if (v == kVarLagTm) {
         e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, true>(b, c, st, nf, t.zc, v, dev_error, cache,
                                                     stream, launches);
-    } else {
+    } else if (v == kVarLagTmCap) {
         e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, true, 3>(b, c, st, nf, t.zc, v, dev_error, cache,
                                                        stream, launches);
+    } else {
+        e = launch_lag_shfl(b, c, st, nf, t.zc, v, dev_error, cache, stream, launches);
     }
     if (e != cudaSuccess || form == 0)
         return e;
