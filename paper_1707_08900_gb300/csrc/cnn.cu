@@ -298,20 +298,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 tc::fence_after_sync();
                 const uint64_t adst = ad0 + (uint64_t)((s * SM::A_PITCH) >> 4);
                 const uint32_t dt0 = tmem + acc * SM::ACC_COLS;
+                // consecutive MMAs go to the ZB planes' accumulators in
+                // turn, so that each waits less on the one before it
 #pragma unroll
-                for (int zb = 0; zb < ZB; ++zb)
+                for (int tap = 0; tap < TAPS; ++tap) {
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // offset + 1
 #pragma unroll
-                    for (int tap = 0; tap < TAPS; ++tap) {
-                        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // offset + 1
+                    for (int k = 0; k < KSTEPS; ++k)
 #pragma unroll
-                        for (int k = 0; k < KSTEPS; ++k) {
+                        for (int zb = 0; zb < ZB; ++zb) {
                             const int aoff =
                                 ((((zb + dz) * HY + dy) * HX + dx) * 16 + 2 * k * SM::CS) >> 4;
                             tc::mma_bf16(dt0 + zb * N, adst + (uint64_t)aoff,
                                          bd0 + (uint64_t)((tap * KSTEPS + k) * 16), idesc,
                                          (tap > 0 || k > 0) ? 1u : 0u);
                         }
-                    }
+                }
                 tc::commit(&empty[s]);
                 tc::commit(&accf[acc]);
                 cnt[2] = i + 1;

@@ -46,11 +46,12 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     }
     if (e != cudaSuccess || form == 0)
         return e;
-    // the 19-point form's second pass: one thread per point (a z-streaming
+    // the 19-point form's second pass: one thread per column of the entry's
+    // z-chunk, the divergence sliding along z in registers (a z-streaming
     // TMA-tiled version measured slower at 256^3: 10.2 against 11.6 G
     // updates/s for the form, its per-plane work being too small to hide the
-    // ring's latency; the one-point kernel is within 15% of its own bytes)
-    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
+    // ring's latency)
+    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches, t.zc);
 }
 
 template cudaError_t launch_substep_tiled<float, float, float>(const StateBufs &,
