@@ -63,11 +63,10 @@ cudaError_t launch_substep_simple(const StateBufs &b, const Coef<TS> &c, const R
                                   int nf, int form, cudaStream_t stream, int *launches);
 
 // Second pass of the 19-point form (Algorithm 3): w += dt (nu/3) grad div,
-// out += beta dt (nu/3) grad div, from the stored divergence field; one
-// thread per point (zc = 0) or per column of zc planes.
+// out += beta dt (nu/3) grad div, from the stored divergence field.
 template <class TS, class TW, class TA>
 cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKStage &st,
-                                cudaStream_t stream, int *launches, int zc = 0);
+                                cudaStream_t stream, int *launches);
 
 // State copies between a compact [f][z][y][x] staging buffer (FP64 or FP32)
 // and the padded layout (ghosts filled on the way in).

@@ -109,58 +109,6 @@ __global__ void __launch_bounds__(128) k_pass2_simple(const TS *__restrict__ div
     }
 }
 
-// The same second pass walking a column of zc planes per thread: the
-// divergence values along z slide through a register window, so each plane
-// is loaded once per column instead of by seven threads; the x and y arms
-// are read as in the one-point kernel.  Same arithmetic in the same order.
-template <class T>
-struct ColAcc {
-    const T *__restrict__ p;  // divergence at this thread's (x, y) in plane z
-    int P;
-    const T (&win)[7];        // divergence at z - 3 .. z + 3
-    __device__ __forceinline__ T operator()(int, int dz, int dy, int dx) const
-    {
-        return dz ? win[dz + 3] : __ldg(p + dy * P + dx);
-    }
-};
-
-template <class TS, class TW, class TA>
-__global__ void __launch_bounds__(128) k_pass2_col(const TS *__restrict__ divf,
-                                                   TS *__restrict__ out, TW *__restrict__ w,
-                                                   Layout Ls, Layout Lw, Coef<TS> c,
-                                                   RKStage st, int zc)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z0 = blockIdx.z * zc;
-    if (x >= Ls.nx || y >= Ls.ny)
-        return;
-    const int z1 = min(z0 + zc, Ls.nz);
-    const TS *col = divf + (long long)(y + GY) * Ls.P + (x + GX);
-    TS win[7];
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-        win[k] = __ldg(col + (long long)zplane(Ls, z0 - 3 + k) * Ls.plane);
-    const TA dt = (TA)st.dt, beta = (TA)st.beta, nu3 = (TA)st.nu3;
-#pragma unroll 1
-    for (int z = z0; z < z1; ++z) {
-        win[6] = __ldg(col + (long long)zplane(Ls, z + 3) * Ls.plane);
-        const ColAcc<TS> A{col + (long long)z * Ls.plane, Ls.P, win};
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const TA g = (TA)d1_axis(A, 0, i, c);
-            const long long iw = lidx(Lw, 1 + i, z, y, x);
-            const long long io = lidx(Ls, 1 + i, z, y, x);
-            if (!st.last)
-                w[iw] = (TW)((TA)w[iw] + dt * nu3 * g);
-            store_ghosted(out, Ls, 1 + i, z, y, x, (TS)((TA)out[io] + beta * dt * nu3 * g));
-        }
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            win[k] = win[k + 1];
-    }
-}
-
 }  // namespace
 
 template <class TS, class TW, class TA>
@@ -202,7 +150,7 @@ cudaError_t launch_substep_simple(const StateBufs &b, const Coef<TS> &c, const R
 
 template <class TS, class TW, class TA>
 cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKStage &st,
-                                cudaStream_t stream, int *launches, int zc)
+                                cudaStream_t stream, int *launches)
 {
     // walls in z: the stored divergence is even about a wall; its ghost
     // planes are filled between the passes
@@ -210,15 +158,9 @@ cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKS
     if (e != cudaSuccess)
         return e;
     const dim3 block(32, 4, 1);
-    if (zc > 0) {
-        const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, (b.Ls.nz + zc - 1) / zc);
-        k_pass2_col<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,
-                                                            (TW *)b.w, b.Ls, b.Lw, c, st, zc);
-    } else {
-        const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
-        k_pass2_simple<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,
-                                                               (TW *)b.w, b.Ls, b.Lw, c, st);
-    }
+    const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
+    k_pass2_simple<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,
+                                                           (TW *)b.w, b.Ls, b.Lw, c, st);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -246,15 +188,15 @@ template cudaError_t launch_substep_simple<float, double, double>(const StateBuf
 
 template cudaError_t launch_pass2_simple<double, double, double>(const StateBufs &,
                                                               const Coef<double> &, const RKStage &,
-                                                              cudaStream_t, int *, int);
+                                                              cudaStream_t, int *);
 template cudaError_t launch_pass2_simple<float, float, float>(const StateBufs &,
                                                               const Coef<float> &, const RKStage &,
-                                                              cudaStream_t, int *, int);
+                                                              cudaStream_t, int *);
 template cudaError_t launch_pass2_simple<float, float, double>(const StateBufs &,
                                                               const Coef<float> &, const RKStage &,
-                                                              cudaStream_t, int *, int);
+                                                              cudaStream_t, int *);
 template cudaError_t launch_pass2_simple<float, double, double>(const StateBufs &,
                                                               const Coef<float> &, const RKStage &,
-                                                              cudaStream_t, int *, int);
+                                                              cudaStream_t, int *);
 
 }  // namespace gbfd

@@ -35,7 +35,7 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
             b, c, st, nf, form, t.zc, 2, dev_error, cache, stream, launches);
     if (e != cudaSuccess || form == 0)
         return e;
-    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches, t.zc);
+    return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
 }
 
 template cudaError_t launch_substep_tiled<float, float, double>(const StateBufs &,
