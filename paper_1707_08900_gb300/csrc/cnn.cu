@@ -4,12 +4,13 @@
 //
 // * Convolutions (forward, and the input gradient of the backward pass) are
 //   implicit GEMMs on the tcgen05 tensor cores: M = 128 grid points per MMA,
-//   N = output channels, K = 27 taps x input channels; BF16 operands in
-//   shared memory as K-major core matrices, FP32 accumulators in TMEM.
+//   N = the output channels of the three z taps of one (dy, dx) tap (they
+//   share the A window), K = 9 (dy, dx) taps x input channels; BF16 operands
+//   in shared memory as K-major core matrices, FP32 accumulators in TMEM.
 // * A persistent, warp-specialised CTA per SM: one warp loads each tile's
-//   input plus its periodic one-point halo with ONE TMA box into a
-//   three-stage ring, one thread issues the tile's 27 taps as MMAs from
-//   shifted descriptors into one of two TMEM accumulator buffers, and eight
+//   input plus its periodic one-point halo with ONE TMA box into a two- or
+//   three-stage ring, one thread issues the tile's MMAs from shifted
+//   descriptors into one of two TMEM accumulator buffers, and eight
 //   epilogue warps read the other buffer (bias, GELU or GELU', BF16 stores),
 //   so loads, MMAs and epilogues of consecutive tiles overlap.  The weights
 //   (B operand) stay in shared memory.  Activations are kept in a padded,
@@ -133,14 +134,28 @@ struct ConvArgs {
 // Its input plus the one-point halo, HX x HY x HZ points of CIN channels, is
 // ONE TMA box of the padded chunk-major input, (8 channels, HX, HY, HZ,
 // CIN / 8 chunks): in shared memory chunk c of halo point (hx, hy, hz) sits at
-// c * CS + ((hz * HY + hy) * HX + hx) * 16.  For tap (dx, dy, dz) the A
-// operand of plane zb is then the same buffer at a shifted start: core
-// matrices of 8 x-consecutive rows (16-byte row stride), row groups one halo
-// row apart (SBO = HX * 16), K chunks CS apart (LBO), so the 27 taps are
-// issued back to back without any further data movement.
-constexpr int TXT = 8, TYT = 16, ZB = 2;
+// c * CS + ((hz * HY + hy) * HX + hx) * 16.  The A operand of halo plane hz
+// and in-plane tap (dy, dx) is that buffer at a shifted start: core matrices
+// of 8 x-consecutive rows (16-byte row stride), row groups one halo row apart
+// (SBO = HX * 16), K chunks CS apart (LBO).
+//
+// The three z taps of one (dy, dx) read the same A window (halo plane hz
+// feeds output planes hz - dz for dz = 0, 1, 2), so they are ONE MMA with
+// their weights stacked along N (N = 3 NO for NO output channels): a
+// tcgen05 MMA of M = 128, K = 16 costs about the same for N = 16 or 32 as for
+// 96 (measured on GB300: 45 cycles for N <= 32, 56 for N = 96, 64 for 128),
+// so merging the z taps cuts the MMA time per output plane by about 2.4 at
+// ZB = 4.  Column group dz of the MMA of halo plane hz lands on output plane
+// zo = hz - dz; placing plane zo's accumulator at column NO (ZB + 1 - zo)
+// makes the three groups of every MMA consecutive columns at
+// NO (ZB + 1 - hz).  Planes -2, -1, ZB and ZB + 1 catch the groups that fall
+// outside the tile (never read).  Every MMA accumulates, so the epilogue
+// zeroes the columns it has read (and the spill planes) before handing the
+// buffer back.
+constexpr int TXT = 8, TYT = 16, ZB = 4;
 constexpr int HX = TXT + 2, HY = TYT + 2, HZ = ZB + 2, HPTS = HX * HY * HZ;
 static_assert(TXT * TYT == MT, "one MMA row block per tile plane");
+constexpr int TAPS_XY = 9;  // (dy, dx) taps; dz is stacked along N
 
 // Warp roles of the convolution CTA (one per SM, persistent over tiles):
 // warp 0 issues the TMA halo loads, warp 1 the MMAs (and owns the TMEM
@@ -149,28 +164,30 @@ static_assert(TXT * TYT == MT, "one MMA row block per tile plane");
 // channels, 6-9 the second).
 constexpr int CONV_THREADS = 320;
 constexpr int EPI_WARPS = 8;
-constexpr int NSTAGE = 3;  // halo buffers
-constexpr int NACC = 2;    // TMEM accumulator buffers
+constexpr int NACC = 2;  // TMEM accumulator buffers
 
-template <int CIN, int N, int EPI>
+template <int CIN, int NO, int EPI>
 struct ConvSmem {
-    static constexpr int K = TAPS * CIN;
+    static constexpr int N = 3 * NO;          // MMA N: the three z taps' output channels
+    static constexpr int K = TAPS_XY * CIN;   // B operand K: (dy, dx) taps x input channels
     static constexpr int CH8 = CIN / 8;
     static constexpr int B_BYTES = N * K * 2;
     static constexpr int CS = HPTS * 16;  // chunk stride of the TMA box
     static constexpr int A_BYTES = CH8 * CS;
+    static constexpr int NSTAGE = CIN >= 32 ? 2 : 3;  // halo buffers
     static constexpr int A_OFF = (B_BYTES + 1023) / 1024 * 1024;
     static constexpr int A_PITCH = (A_BYTES + 1023) / 1024 * 1024;
     static constexpr int BAR_OFF = A_OFF + NSTAGE * A_PITCH;
-    // full[2], empty[2], acc_full[2], acc_empty[2], TMEM address, abort flag,
-    // issue / consume counts for the drain
-    static constexpr int BYTES = BAR_OFF + 8 * 8 + 32;
-    static constexpr int ACC_COLS = ZB * N;  // one accumulator buffer
-    static constexpr int TCOLS = NACC * ACC_COLS <= 32 ? 32 : (NACC * ACC_COLS <= 64 ? 64 : 128);
-    static_assert(CS % 16 == 0 && (CS >> 4) < (1 << 14), "descriptor offsets");
+    // full[NSTAGE], empty[NSTAGE], acc_full[NACC], acc_empty[NACC], then the
+    // TMEM address, the abort flag and four issue / consume counts
+    static constexpr int BYTES = BAR_OFF + (2 * NSTAGE + 2 * NACC) * 8 + 8 + 16;
+    static constexpr int ACC_COLS = (ZB + 4) * NO;  // one accumulator buffer
+    static constexpr int TCOLS = NACC * ACC_COLS <= 128 ? 128 : (NACC * ACC_COLS <= 256 ? 256 : 512);
+    static_assert(NACC * ACC_COLS <= 512, "TMEM columns");
+    static_assert(CS % 16 == 0 && (CS >> 4) < (1 << 14) && ((K * 16) >> 4) < (1 << 14),
+                  "descriptor offsets");
+    static_assert(BYTES <= 227 * 1024, "shared memory");
 };
-
-
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -209,12 +226,13 @@ __device__ __forceinline__ void tile_origin(int tile, int n, int &x0, int &y0, i
     b = r / tz_n;
 }
 
-template <int CIN, int N, int EPI>
+template <int CIN, int NO, int EPI>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap xmap, const ConvArgs a)
 {
-    using SM = ConvSmem<CIN, N, EPI>;
-    constexpr int KSTEPS = CIN / 16;  // MMAs per tap and plane
+    using SM = ConvSmem<CIN, NO, EPI>;
+    constexpr int NSTAGE = SM::NSTAGE;
+    constexpr int KSTEPS = CIN / 16;  // MMAs per (dy, dx) tap and halo plane
     constexpr int SBO_B = SM::K * 16;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sB = smem;
@@ -227,6 +245,19 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
     int *cnt = reinterpret_cast<int *>(tslot + 2);  // issued, consumed, committed, drained
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    // epilogue geometry: two warps per TMEM lane quarter, each taking half
+    // of the output channels
+    constexpr int NH = NO / 2;  // channels per epilogue warp
+    static_assert(NH == 16 || NH == 8, "epilogue column chunks");
+    const int e = warp - 2;
+    const int q = warp % 4, c0 = (e / 4) * NH;
+    auto zero_cols = [&](uint32_t taddr) {
+        if constexpr (NH == 16)
+            tc::tmem_zero16(taddr);
+        else
+            tc::tmem_zero8(taddr);
+    };
 
     // the weights (B operand) stay in shared memory for the whole launch
     for (int i = threadIdx.x; i < SM::B_BYTES / 16; i += CONV_THREADS)
@@ -251,6 +282,16 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tslot);
+    // every MMA accumulates: both accumulator buffers start at zero
+    if (warp >= 2) {
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + c0;
+#pragma unroll 1
+        for (int j = 0; j < NACC * (ZB + 4); ++j)
+            zero_cols(tl + j * NO);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
     const int n = a.n;
     const long long n3 = (long long)n * n * n;
     const int nb = (int)(a.npts / n3);
@@ -275,11 +316,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             }
         }
     } else if (warp == 1) {
-        // MMA issuer: 27 taps x ZB planes x KSTEPS per tile into one of two
-        // accumulator buffers; the commits free the halo stage and hand the
-        // accumulators to the epilogue
+        // MMA issuer: per halo plane, 9 (dy, dx) taps x KSTEPS MMAs of
+        // N = 3 NO into one of two accumulator buffers; the commits free the
+        // halo stage and hand the accumulators to the epilogue
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(MT, N);
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(MT, SM::N);
             // descriptors of the stage and weight bases; every tap's operand
             // is a compile-time byte offset from them (the start address is
             // the descriptor's low field, in 16-byte units, and shared
@@ -297,43 +338,42 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     break;
                 tc::fence_after_sync();
                 const uint64_t adst = ad0 + (uint64_t)((s * SM::A_PITCH) >> 4);
-                const uint32_t dt0 = tmem + acc * SM::ACC_COLS;
-                // consecutive MMAs go to the ZB planes' accumulators in
-                // turn, so that each waits less on the one before it
+                const uint32_t dbuf = tmem + acc * SM::ACC_COLS;
 #pragma unroll
-                for (int tap = 0; tap < TAPS; ++tap) {
-                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // offset + 1
+                for (int hz = 0; hz < HZ; ++hz)
 #pragma unroll
-                    for (int k = 0; k < KSTEPS; ++k)
+                    for (int t = 0; t < TAPS_XY; ++t) {
+                        const int dy = t / 3, dx = t % 3;  // offset + 1
 #pragma unroll
-                        for (int zb = 0; zb < ZB; ++zb) {
+                        for (int k = 0; k < KSTEPS; ++k) {
                             const int aoff =
-                                ((((zb + dz) * HY + dy) * HX + dx) * 16 + 2 * k * SM::CS) >> 4;
-                            tc::mma_bf16(dt0 + zb * N, adst + (uint64_t)aoff,
-                                         bd0 + (uint64_t)((tap * KSTEPS + k) * 16), idesc,
-                                         (tap > 0 || k > 0) ? 1u : 0u);
+                                (((hz * HY + dy) * HX + dx) * 16 + 2 * k * SM::CS) >> 4;
+                            tc::mma_bf16(dbuf + (uint32_t)(NO * (ZB + 1 - hz)),
+                                         adst + (uint64_t)aoff,
+                                         bd0 + (uint64_t)((t * KSTEPS + k) * 16), idesc, 1u);
                         }
-                }
+                    }
                 tc::commit(&empty[s]);
                 tc::commit(&accf[acc]);
                 cnt[2] = i + 1;
             }
         }
     } else {
-        // epilogue: TMEM -> registers, release the accumulators, then bias /
-        // GELU / GELU' and the stores (with the periodic copies).  Two warps
-        // per TMEM lane quarter, each taking half of the output channels.
-        constexpr int NH = N / 2;  // channels per epilogue warp
-        const int e = warp - 2;
-        const int q = warp % 4, c0 = (e / 4) * NH;
+        // epilogue, per tile plane: TMEM -> registers, zero those columns,
+        // then bias / GELU / GELU' and the stores (with the periodic
+        // copies); the spill planes are zeroed too before the buffer goes back
         const int r = q * 32 + lane;  // row of the M block = TMEM lane
         const int lx = r % TXT, ly = r / TXT;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + c0;
+        float bias[NH];
+#pragma unroll
+        for (int j = 0; j < NH; ++j)
+            bias[j] = (EPI == EPI_DGELU || c0 + j >= NO) ? 0.f : __ldg(a.bias + c0 + j);
         int i = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
             const int acc = i % NACC;
-            // one lane waits, the warp follows it (the TMEM loads below are
-            // warp-collective)
+            // one lane waits, the warp follows it (the TMEM accesses below
+            // are warp-collective)
             int ok = 0;
             if (lane == 0)
                 ok = wait_or_abort(&accf[acc], (i / NACC) & 1, abort);
@@ -344,26 +384,20 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
             if (lane != 0)
                 (void)tiled::mbar_try_wait(&accf[acc], (i / NACC) & 1);
             tc::fence_after_sync();
-            float v[ZB][NH];
-#pragma unroll
-            for (int zb = 0; zb < ZB; ++zb) {
-                if constexpr (NH == 16)
-                    tc::tmem_ld16(tl + acc * SM::ACC_COLS + zb * N, v[zb]);
-                else
-                    tc::tmem_ld8(tl + acc * SM::ACC_COLS + zb * N, v[zb]);
-            }
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&acce[acc]);
-            if (e == 0 && lane == 0)
-                cnt[3] = i + 1;
+            const uint32_t tb = tl + acc * SM::ACC_COLS;
             int x0, y0, z0, b;
             tile_origin(tile, n, x0, y0, z0, b);
             const int x = x0 + lx, y = y0 + ly;
-#pragma unroll
-            for (int zb = 0; zb < ZB; ++zb) {
-                const int z = z0 + zb;
+#pragma unroll 1
+            for (int zo = 0; zo < ZB; ++zo) {
+                const uint32_t tp = tb + (uint32_t)(NO * (ZB + 1 - zo));
+                float v[NH];
+                if constexpr (NH == 16)
+                    tc::tmem_ld16(tp, v);
+                else
+                    tc::tmem_ld8(tp, v);
+                zero_cols(tp);
+                const int z = z0 + zo;
                 if (x >= n || y >= n || z >= n)
                     continue;
                 const long long p = (long long)b * n3 + ((long long)z * n + y) * n + x;
@@ -371,9 +405,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     // five real output channels, all in the first half
                     if (c0 == 0) {
                         float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
-                        yo[0] = make_float4(v[zb][0] + __ldg(a.bias + 0), v[zb][1] + __ldg(a.bias + 1),
-                                            v[zb][2] + __ldg(a.bias + 2), v[zb][3] + __ldg(a.bias + 3));
-                        yo[1] = make_float4(v[zb][4] + __ldg(a.bias + 4), 0.f, 0.f, 0.f);
+                        yo[0] = make_float4(v[0] + bias[0], v[1] + bias[1], v[2] + bias[2],
+                                            v[3] + bias[3]);
+                        yo[1] = make_float4(v[4] + bias[4], 0.f, 0.f, 0.f);
                     }
                 } else {
                     uint4 out[NH / 8];
@@ -383,9 +417,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                         if constexpr (EPI == EPI_GELU) {
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
-                                h[j] = v[zb][c + j] + __ldg(a.bias + c0 + c + j);
+                                h[j] = v[c + j] + bias[c + j];
                             if (a.hsave) {
-                                float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * N + c0 + c);
+                                float4 *hs = reinterpret_cast<float4 *>(a.hsave + p * NO + c0 + c);
                                 hs[0] = make_float4(h[0], h[1], h[2], h[3]);
                                 hs[1] = make_float4(h[4], h[5], h[6], h[7]);
                             }
@@ -394,12 +428,12 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                                 h[j] = gelu(h[j]);
                         } else {
                             const float4 *hp =
-                                reinterpret_cast<const float4 *>(a.hprev + p * N + c0 + c);
+                                reinterpret_cast<const float4 *>(a.hprev + p * NO + c0 + c);
                             const float4 h0 = __ldg(hp), h1 = __ldg(hp + 1);
                             const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
-                                h[j] = v[zb][c + j] * gelu_grad(hv[j]);
+                                h[j] = v[c + j] * gelu_grad(hv[j]);
                         }
                         __nv_bfloat162 o[4];
 #pragma unroll
@@ -415,6 +449,17 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     });
                 }
             }
+            // the spill planes -2, -1, ZB, ZB + 1
+            zero_cols(tb);
+            zero_cols(tb + NO);
+            zero_cols(tb + NO * (ZB + 2));
+            zero_cols(tb + NO * (ZB + 3));
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&acce[acc]);
+            if (e == 0 && lane == 0)
+                cnt[3] = i + 1;
         }
     }
     __syncthreads();
@@ -670,14 +715,15 @@ struct PackArgs {
     float *w, *m, *v;  // FP32 master parameters and Adam moments [kParams]
     const float *g;    // gradients [kParams] (NULL: pack only)
     float lr, b1, b2, eps, bc1, bc2;
-    bf16 *fwd[3];      // forward B operands, layer l: [co][27*ci]
-    bf16 *bwd[3];      // input-gradient B operands (layers 2, 3): [ci][27*co]
+    bf16 *fwd[3];      // forward B operands, layer l: [dz][co][9*ci]
+    bf16 *bwd[3];      // input-gradient B operands (layers 2, 3): [dz][ci][9*co]
     float *bias[3];    // FP32 biases [co]
 };
 
 // Adam step (Kingma & Ba 2015) on the master weights, then the BF16 GEMM
-// copies: forward B[co][tap*CI + ci]; input-gradient B'[ci][(26-tap)*CO + co]
-// (channels transposed, taps flipped).
+// copies, tap = (dz, dy, dx) = 9 dz + t: forward B[dz CO + co][t CI + ci];
+// input-gradient B'[dz' CI + ci][t' CO + co] for the flipped tap
+// (dz', t') of 26 - tap (channels transposed).
 __global__ void k_adam_pack(PackArgs a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -701,9 +747,15 @@ __global__ void k_adam_pack(PackArgs a)
         return;
     }
     const int co = j / (TAPS * CI), tap = (j / CI) % TAPS, ci = j % CI;
-    a.fwd[l][core_idx(co, tap * CI + ci, TAPS * CI)] = __float2bfloat16_rn(w);
-    if (l > 0)
-        a.bwd[l][core_idx(ci, (TAPS - 1 - tap) * CO + co, TAPS * CO)] = __float2bfloat16_rn(w);
+    // rows: the three z taps' output channels stacked (dz * CO + co); K:
+    // the (dy, dx) tap, then the input channel
+    a.fwd[l][core_idx((tap / 9) * CO + co, (tap % 9) * CI + ci, TAPS_XY * CI)] =
+        __float2bfloat16_rn(w);
+    if (l > 0) {
+        const int tf = TAPS - 1 - tap;  // flipped tap
+        a.bwd[l][core_idx((tf / 9) * CI + ci, (tf % 9) * CO + co, TAPS_XY * CO)] =
+            __float2bfloat16_rn(w);
+    }
 }
 
 // Centred box filter: coarse vertex I sits on fine vertex r I; per axis the
