@@ -189,6 +189,31 @@ struct ConvSmem {
     static_assert(BYTES <= 227 * 1024, "shared memory");
 };
 
+// Zeroes 16 (or 8) consecutive FP32 columns of this warp's 32 TMEM lanes and
+// waits for the stores to complete.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr)
+{
+    const uint32_t z = 0;
+    __syncwarp();
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_zero8(uint32_t taddr)
+{
+    const uint32_t z = 0;
+    __syncwarp();
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tiled::smem_u32(bar))
@@ -254,9 +279,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     const int q = warp % 4, c0 = (e / 4) * NH;
     auto zero_cols = [&](uint32_t taddr) {
         if constexpr (NH == 16)
-            tc::tmem_zero16(taddr);
+            tmem_zero16(taddr);
         else
-            tc::tmem_zero8(taddr);
+            tmem_zero8(taddr);
     };
 
     // the weights (B operand) stay in shared memory for the whole launch

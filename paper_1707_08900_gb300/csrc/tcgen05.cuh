@@ -143,30 +143,5 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *r)
         r[i] = __uint_as_float(v[i]);
 }
 
-// Zeroes 16 (or 8) consecutive FP32 columns of this warp's 32 TMEM lanes and
-// waits for the stores to complete.
-__device__ __forceinline__ void tmem_zero16(uint32_t taddr)
-{
-    const uint32_t z = 0;
-    __syncwarp();
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};\n\t"
-        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
-        "r"(z)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_zero8(uint32_t taddr)
-{
-    const uint32_t z = 0;
-    __syncwarp();
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};\n\t"
-        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
-        "r"(z)
-        : "memory");
-}
-
 }  // namespace tc
 }  // namespace gbfd
