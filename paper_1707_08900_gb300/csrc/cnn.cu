@@ -214,6 +214,18 @@ __device__ __forceinline__ void tmem_zero8(uint32_t taddr)
         : "memory");
 }
 
+// Programmatic dependent launch (a kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream finishes):
+// pdl_wait blocks until the predecessor grid has completed and its memory
+// is visible; pdl_trigger lets this grid's dependant start once every CTA
+// of this grid has triggered or exited.  Both are no-ops for a kernel
+// launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tiled::smem_u32(bar))
@@ -317,6 +329,12 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    // everything above (weights, barriers, TMEM) may overlap the tail of the
+    // kernel before this one in the stream, which never writes the weights
+    // (the input staging kernel, another convolution or the gradient
+    // reduction); the activations it writes are read only below
+    pdl_wait();
+    pdl_trigger();
     const int n = a.n;
     const long long n3 = (long long)n * n * n;
     const int nb = (int)(a.npts / n3);
@@ -624,6 +642,7 @@ __global__ void k_input_compact(const float *__restrict__ xs, int nf, int n, int
                                 const float *__restrict__ mean, const float *__restrict__ stdv,
                                 bf16 *__restrict__ x0)
 {
+    pdl_trigger();  // the first convolution may start its prologue
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts)
         return;
@@ -641,6 +660,7 @@ __global__ void k_input_state(const float *__restrict__ st, Layout L, int nf, in
                               const float *__restrict__ mean, const float *__restrict__ stdv,
                               bf16 *__restrict__ x0)
 {
+    pdl_trigger();  // the first convolution may start its prologue
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = L.nx;
     if (p >= n * n * n)
@@ -657,6 +677,7 @@ __global__ void k_input_state(const float *__restrict__ st, Layout L, int nf, in
 __global__ void k_apply(float *__restrict__ st, Layout L, int nf, const float *__restrict__ y,
                         const float *__restrict__ sout)
 {
+    pdl_wait();  // launched to overlap the last convolution's tail
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = L.nx;
     if (p >= n * n * n)
@@ -910,11 +931,21 @@ cudaError_t conv(gbfd_cnn *c, const CUtensorMap &xmap, const ConvArgs &a)
     const int n = a.n;
     const long long ntiles = (long long)(a.npts / ((long long)n * n * n)) * ((n + ZB - 1) / ZB) *
                              ((n + TYT - 1) / TYT) * ((n + TXT - 1) / TXT);
-    // persistent: one CTA per SM walking the tiles (fewer on request)
-    k<<<(int)std::min<long long>(ntiles, c->grid_conv), CONV_THREADS, SM::BYTES, c->stream>>>(xmap,
-                                                                                             a);
+    // persistent: one CTA per SM walking the tiles (fewer on request),
+    // launched so that its prologue overlaps the previous kernel's tail
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<long long>(ntiles, c->grid_conv));
+    cfg.blockDim = dim3(CONV_THREADS);
+    cfg.dynamicSmemBytes = SM::BYTES;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k, xmap, a);
     c->launches++;
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -1409,8 +1440,19 @@ gbfd_status gbfd_cnn_apply(gbfd_cnn *c, gbfd_ctx *ctx)
     if (e == cudaSuccess)
         e = forward(c, n3, false);
     if (e == cudaSuccess) {
-        k_apply<<<(n3 + 255) / 256, 256, 0, s>>>(st, L, nf, c->y3, c->norm + 10);
-        e = cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((n3 + 255) / 256);
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_apply, st, L, nf, (const float *)c->y3,
+                               (const float *)(c->norm + 10));
+        if (e == cudaSuccess)
+            e = cudaGetLastError();
     }
     c->stream = saved;
     c->launches += 2;

@@ -50,9 +50,11 @@ def _net(n, batch, p):
 @pytest.mark.parametrize("n,batch,grid", [(8, 2, 0), (12, 1, 0), (8, 2, 1), (12, 1, 2),
                                           (32, 2, 0), (32, 2, 7)])
 def test_forward_matches_oracle(n, batch, grid):
-    """`grid` caps the CTAs of each convolution launch (0: the default three
-    per SM), so that every CTA walks several tiles (8^3 x 2 has 8 tiles of
-    256 points, 32^3 x 2 has 256; 7 CTAs give 36-37 tiles each)."""
+    """`grid` caps the CTAs of each convolution launch (0: the default, one
+    per SM), so that every CTA walks several tiles (tiles of 8 x 16 x 4
+    points: 8^3 x 2 has 4, 32^3 x 2 has 128; 7 CTAs give 18-19 tiles each),
+    reusing its halo stages, barrier phases and both TMEM accumulator
+    buffers."""
     from paper_1707_08900_gb300 import gbfd
     p = _params(3)
     rng = np.random.default_rng(4)
