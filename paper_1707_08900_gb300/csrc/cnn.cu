@@ -149,9 +149,9 @@ struct ConvArgs {
 // zo = hz - dz; placing plane zo's accumulator at column NO (ZB + 1 - zo)
 // makes the three groups of every MMA consecutive columns at
 // NO (ZB + 1 - hz).  Planes -2, -1, ZB and ZB + 1 catch the groups that fall
-// outside the tile (never read).  Every MMA accumulates, so the epilogue
-// zeroes the columns it has read (and the spill planes) before handing the
-// buffer back.
+// outside the tile (never read).  Every MMA accumulates, so the buffers
+// start at zero and the epilogue zeroes the columns it has read before
+// handing the buffer back.
 constexpr int TXT = 8, TYT = 16, ZB = 4;
 constexpr int HX = TXT + 2, HY = TYT + 2, HZ = ZB + 2, HPTS = HX * HY * HZ;
 static_assert(TXT * TYT == MT, "one MMA row block per tile plane");
@@ -403,8 +403,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         }
     } else {
         // epilogue, per tile plane: TMEM -> registers, zero those columns,
-        // then bias / GELU / GELU' and the stores (with the periodic
-        // copies); the spill planes are zeroed too before the buffer goes back
+        // then bias / GELU / GELU' and the stores (with the periodic copies)
         const int r = q * 32 + lane;  // row of the M block = TMEM lane
         const int lx = r % TXT, ly = r / TXT;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + c0;
@@ -492,11 +491,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                     });
                 }
             }
-            // the spill planes -2, -1, ZB, ZB + 1
-            zero_cols(tb);
-            zero_cols(tb + NO);
-            zero_cols(tb + NO * (ZB + 2));
-            zero_cols(tb + NO * (ZB + 3));
+            // (the spill planes -2, -1, ZB, ZB + 1 keep accumulating: they are
+            // never read, and their columns are no other plane's)
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0)
