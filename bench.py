@@ -562,6 +562,10 @@ def run_ours(args):
         "network_ms_per_application": ms_corr - ms_plain,
         "network_tensor_tflops": cnn_flop / ((ms_corr - ms_plain) * 1e-3) / 1e12,
         "value_corrected": world * nc ** 3 / (ms_corr * 1e-3), "steps": csteps,
+        # SM cycles per tcgen05 MMA (M = 128, K = 16) against N: the
+        # convolutions stack their three z taps along N (96 / 48 columns)
+        "tc_mma_cycles": {str(nn): round(gbfd.gbfd_tc_mma_cycles(nn, stream.cuda_stream), 1)
+                          for nn in (32, 48, 96, 128, 256)},
     }
     net.close()
     cs_.close()

@@ -255,6 +255,17 @@ gbfd_status gbfd_diagnostics_noalloc(const void *state, int state_is_fp64, int n
  * INVALID_ARG (NULL output), CUDA. */
 gbfd_status gbfd_fp64_fma_rate(void *stream, double *tflops);
 
+/* Measured cost of one tcgen05 MMA (M = 128, K = 16, BF16 operands from
+ * shared memory, FP32 accumulation in TMEM) with n columns, n in {16, 32,
+ * 48, 64, 96, 128, 256}: one thread per SM issues 1,024 MMAs back to back
+ * with the convolutions' operand strides; *cycles = SM clock cycles per MMA,
+ * averaged over the SMs (synchronises `stream`; results in fixed device
+ * arrays, no allocation).  It is the measurement behind the network
+ * convolutions' MMA shape (their z taps stacked along N); no counterpart in
+ * the paper.  Errors: INVALID_ARG (NULL output, unsupported n), TIMEOUT (a
+ * bounded completion wait gave up), CUDA. */
+gbfd_status gbfd_tc_mma_cycles(int n, void *stream, double *cycles);
+
 /* Tuning options (no counterpart in the paper; used by the tests and the
  * autotuner).  GBFD_OPT_KERNEL_PATH: 0 = tiled kernels (TMA-staged shared
  * memory, the default), 1 = simple one-thread-per-point kernels reading

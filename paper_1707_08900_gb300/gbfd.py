@@ -43,7 +43,7 @@ EXPORTS = ("gbfd_workspace_bytes", "gbfd_init", "gbfd_destroy", "gbfd_set_state"
            "gbfd_cnn_set_norm", "gbfd_cnn_forward", "gbfd_cnn_gradients",
            "gbfd_cnn_train_step", "gbfd_cnn_apply", "gbfd_step_corrected", "gbfd_box_filter",
            "gbfd_cnn_launch_count", "gbfd_cnn_last_error", "gbfd_cnn_set_option",
-           "gbfd_fp64_fma_rate", "gbfd_halo_bytes", "gbfd_halo_pack", "gbfd_halo_unpack",
+           "gbfd_fp64_fma_rate", "gbfd_tc_mma_cycles", "gbfd_halo_bytes", "gbfd_halo_pack", "gbfd_halo_unpack",
            "gbfd_batch_get_option")
 GBFD_CNN_OPT_CONV_GRID, GBFD_CNN_OPT_WGRAD_PARTS = 1, 2
 GBFD_BATCH_OPT_GRAPH, GBFD_BATCH_OPT_ZCHUNK, GBFD_BATCH_OPT_GRID = 1, 2, 3
@@ -162,6 +162,7 @@ def load(path=None):
     L.gbfd_cnn_last_error.argtypes = [_VP]
     L.gbfd_cnn_set_option.argtypes = [_VP, ctypes.c_int, ctypes.c_int64]
     L.gbfd_fp64_fma_rate.argtypes = [_VP, _DP]
+    L.gbfd_tc_mma_cycles.argtypes = [ctypes.c_int, _VP, _DP]
     L.gbfd_halo_bytes.restype = ctypes.c_size_t
     L.gbfd_halo_bytes.argtypes = [_VP]
     L.gbfd_halo_pack.argtypes = [_VP, ctypes.c_int, _VP]
@@ -276,6 +277,17 @@ def gbfd_fp64_fma_rate(stream_ptr=None):
         stream_ptr = torch.cuda.current_stream().cuda_stream
     r = ctypes.c_double()
     _check(load().gbfd_fp64_fma_rate(_VP(stream_ptr), ctypes.byref(r)))
+    return r.value
+
+
+def gbfd_tc_mma_cycles(n, stream_ptr=None):
+    """SM clock cycles per tcgen05 MMA of M = 128, K = 16 and N = n columns
+    (BF16 from shared memory), measured on the current device."""
+    if stream_ptr is None:
+        import torch
+        stream_ptr = torch.cuda.current_stream().cuda_stream
+    r = ctypes.c_double()
+    _check(load().gbfd_tc_mma_cycles(int(n), _VP(stream_ptr), ctypes.byref(r)))
     return r.value
 
 
