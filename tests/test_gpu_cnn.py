@@ -144,6 +144,44 @@ def test_zero_network_leaves_the_coarse_step_unchanged():
     net.close()
 
 
+@pytest.mark.parametrize("n,grid", [(16, 0), (24, 3)])
+def test_apply_matches_oracle_correct(n, grid):
+    """gbfd_cnn_apply on a solver's state (normalise, three convolutions,
+    de-normalise, add to the state with its ghost copies) against the
+    oracle's state + std_out * net((state - mean_in) / std_in): the
+    increment within the BF16 bound; `grid` caps the convolution CTAs so
+    that each walks several tiles.  A step afterwards must read the
+    updated ghosts: it is compared with a fresh context holding the same
+    state."""
+    from paper_1707_08900_gb300 import gbfd
+    p = _params(11)
+    st = inputs.spectrum((n, n, n), 12, mach=0.3, lnrho_rms=5e-2).astype(np.float32)
+    st[4] = 0.02 * np.random.default_rng(13).standard_normal((n, n, n)).astype(np.float32)
+    mean_in = np.array([0.01, 0.02, -0.01, 0.0, 0.005])
+    std_in = np.array([0.05, 0.3, 0.25, 0.3, 0.02])
+    std_out = np.array([1e-3, 2e-3, 3e-3, 2.5e-3, 1e-3])
+    s = gbfd.Solver((n, n, n), precision="fp32", nu=5e-3)
+    s.set_state(st)
+    net = gbfd.CNN(n, batch=1)
+    net.set_params(p)
+    net.set_norm(mean_in, std_in, std_out)
+    net.set_option(gbfd.GBFD_CNN_OPT_CONV_GRID, grid)
+    net.apply(s)
+    got = s.get_state()
+    st64 = st.astype(np.float64)
+    ref = ocnn.correct(st64, p, mean_in, std_in, std_out)
+    assert _rel(got - st64, ref - st64) < BF16_FWD_TOL
+    # the ghost copies were updated with the interior: one step from the
+    # corrected context equals one step from a fresh copy of its state
+    fresh = gbfd.Solver((n, n, n), precision="fp32", nu=5e-3)
+    fresh.set_state(s.get_state(fp64=False))
+    s.rk3_step(0.01, 1)
+    fresh.rk3_step(0.01, 1)
+    assert np.array_equal(s.get_state(fp64=False), fresh.get_state(fp64=False))
+    for x in (s, fresh, net):
+        x.close()
+
+
 def test_training_beats_the_plain_coarse_solver():
     """64^3 fine runs filtered to 16^3: after a short GPU training the
     corrected coarse solver is closer to the filtered fine solution than the
