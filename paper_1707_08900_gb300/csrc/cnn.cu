@@ -54,7 +54,7 @@ constexpr int C0 = 16;     // padded input channels of layer 1
 constexpr int CH = 32;     // hidden channels
 constexpr int C3 = 16;     // padded output channels of layer 3
 
-enum { EPI_GELU = 0, EPI_LINEAR = 1, EPI_DGELU = 2, EPI_APPLY = 3 };
+enum { EPI_GELU = 0, EPI_LINEAR = 1, EPI_DGELU = 2 };
 
 // Packed FP32 parameters: W[co_pad][tap][ci_pad] then b[co_pad], per layer;
 // padded channel counts per layer: (32, 16), (32, 32), (16, 32).
@@ -118,15 +118,11 @@ __device__ __forceinline__ void each_copy(int x, int y, int z, int n, F &&f)
 
 struct ConvArgs {
     const bf16 *wB;      // [N][27*CIN] in core-matrix order
-    const float *bias;   // [N]                      (EPI_GELU, EPI_LINEAR, EPI_APPLY)
+    const float *bias;   // [N]                      (EPI_GELU, EPI_LINEAR)
     float *hsave;        // [npts][N] pre-activation (EPI_GELU; NULL: not kept)
     bf16 *yb;            // padded chunk-major output (EPI_GELU: GELU(h), EPI_DGELU: dh)
     float *yf;           // [npts][8]                (EPI_LINEAR)
     const float *hprev;  // [npts][N]                (EPI_DGELU)
-    float *st;           // solver state, padded FP32 (EPI_APPLY: st += sout * y)
-    Layout L;            //   its layout
-    const float *sout;   //   per-field output scale (std of the residual)
-    int nf;              //   fields present
     int n;               // grid side
     int npts;            // batch * n^3
     int B;               // samples allocated in the padded arrays
@@ -447,21 +443,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
                 if (x >= n || y >= n || z >= n)
                     continue;
                 const long long p = (long long)b * n3 + ((long long)z * n + y) * n + x;
-                if constexpr (EPI == EPI_APPLY) {
-                    // the de-normalised residual straight into the solver's
-                    // state, with its ghost copies (five real output
-                    // channels, all in the first half)
-                    if (c0 == 0) {
-#pragma unroll
-                        for (int f = 0; f < NC; ++f) {
-                            if (f < a.nf) {
-                                const float yv = v[f] + bias[f];
-                                store_ghosted(a.st, a.L, f, z, y, x,
-                                              a.st[lidx(a.L, f, z, y, x)] + a.sout[f] * yv);
-                            }
-                        }
-                    }
-                } else if constexpr (EPI == EPI_LINEAR) {
+                if constexpr (EPI == EPI_LINEAR) {
                     // five real output channels, all in the first half
                     if (c0 == 0) {
                         float4 *yo = reinterpret_cast<float4 *>(a.yf + p * 8);
@@ -685,6 +667,22 @@ __global__ void k_input_state(const float *__restrict__ st, Layout L, int nf, in
     for (int c = 0; c < C0; ++c)
         v[c] = (c < nf) ? (st[lidx(L, c, z, y, x)] - mean[c]) / stdv[c] : 0.f;
     put_input(x0, v, 0, x, y, z, n, B);
+}
+
+// state += std_out * y (the de-normalised predicted residual), ghosts kept.
+__global__ void k_apply(float *__restrict__ st, Layout L, int nf, const float *__restrict__ y,
+                        const float *__restrict__ sout)
+{
+    pdl_wait();  // launched to overlap the last convolution's tail
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = L.nx;
+    if (p >= n * n * n)
+        return;
+    const int z = p / (n * n), yy = (p / n) % n, x = p % n;
+    for (int f = 0; f < nf; ++f) {
+        const float v = st[lidx(L, f, z, yy, x)] + sout[f] * y[(long long)p * 8 + f];
+        store_ghosted(st, L, f, z, yy, x, v);
+    }
 }
 
 // Normalised output [batch][5][n^3] from the layer-3 rows (tests, inference).
@@ -1003,11 +1001,8 @@ cudaError_t pack(gbfd_cnn *c, const float *g, float lr)
 }
 
 // forward of `npts` points whose layer-1 input is already in x0; `keep`
-// saves the pre-activations for the backward pass (training only).  With
-// `st` (one box, the apply path) the last layer adds its de-normalised
-// output to that padded FP32 state instead of writing y3.
-cudaError_t forward(gbfd_cnn *c, int npts, bool keep, float *st = nullptr,
-                    const Layout *L = nullptr, int nf = 0)
+// saves the pre-activations for the backward pass (training only)
+cudaError_t forward(gbfd_cnn *c, int npts, bool keep)
 {
     ConvArgs a;
     memset(&a, 0, sizeof a);
@@ -1033,13 +1028,6 @@ cudaError_t forward(gbfd_cnn *c, int npts, bool keep, float *st = nullptr,
     a.bias = c->bias[2];
     a.hsave = nullptr;
     a.yb = nullptr;
-    if (st) {
-        a.st = st;
-        a.L = *L;
-        a.sout = c->norm + 10;
-        a.nf = nf;
-        return conv<CH, C3, EPI_APPLY>(c, c->map_a2, a);
-    }
     a.yf = c->y3;
     return conv<CH, C3, EPI_LINEAR>(c, c->map_a2, a);
 }
@@ -1446,9 +1434,24 @@ gbfd_status gbfd_cnn_apply(gbfd_cnn *c, gbfd_ctx *ctx)
                                                    c->x0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = forward(c, n3, false, st, &L, nf);  // the last layer updates the state
+        e = forward(c, n3, false);
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((n3 + 255) / 256);
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_apply, st, L, nf, (const float *)c->y3,
+                               (const float *)(c->norm + 10));
+        if (e == cudaSuccess)
+            e = cudaGetLastError();
+    }
     c->stream = saved;
-    c->launches += 1;
+    c->launches += 2;
     return e == cudaSuccess ? GBFD_OK : ccuda(c, e, "cnn apply");
 }
 
