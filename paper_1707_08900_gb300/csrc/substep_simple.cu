@@ -83,8 +83,23 @@ __global__ void __launch_bounds__(128) k_substep_simple(const TS *__restrict__ i
     }
 }
 
+// The divergence around one point for the second pass: the point's address
+// once, its z neighbours by precomputed plane offsets (periodic wrap or
+// ghost planes), the x and y neighbours by constant offsets.
+template <class T>
+struct DivAcc {
+    const T *__restrict__ p;  // divergence at (x, y, z)
+    long long P;              // row pitch
+    long long dz[7];          // offset of plane z + k - 3 from plane z
+    __device__ __forceinline__ T operator()(int, int kz, int ky, int kx) const
+    {
+        return __ldg(p + dz[kz + 3] + ky * P + kx);
+    }
+};
+
 // Second pass of Algorithm 3: w += dt (nu/3) grad(div u),
 // out += beta dt (nu/3) grad(div u), grad by Eq. 6 on the stored divergence.
+// Every load is issued before the first store.
 template <class TS, class TW, class TA>
 __global__ void __launch_bounds__(128) k_pass2_simple(const TS *__restrict__ divf,
                                                       TS *__restrict__ out, TW *__restrict__ w,
@@ -96,16 +111,33 @@ __global__ void __launch_bounds__(128) k_pass2_simple(const TS *__restrict__ div
     const int z = blockIdx.z;
     if (x >= Ls.nx || y >= Ls.ny)
         return;
-    GlobalAcc<TS> A = make_acc(divf, Ls, x, y, z);
+    const long long cs = (long long)z * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+    const long long cw = (long long)z * Lw.plane + (long long)(y + GY) * Lw.P + (x + GX);
+    DivAcc<TS> A;
+    A.p = divf + cs;
+    A.P = Ls.P;
+#pragma unroll
+    for (int k = -3; k <= 3; ++k)
+        A.dz[k + 3] = (long long)(zplane(Ls, z + k) - z) * Ls.plane;
+    TA g[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        g[i] = (TA)d1_axis(A, 0, i, c);
+    TS ov[3];
+    TW wv[3];
+    const bool keep_w = !st.last;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ov[i] = out[cs + (1 + i) * Ls.fpitch];
+        if (keep_w)
+            wv[i] = w[cw + (1 + i) * Lw.fpitch];
+    }
     const TA dt = (TA)st.dt, beta = (TA)st.beta, nu3 = (TA)st.nu3;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const TA g = (TA)d1_axis(A, 0, i, c);
-        const long long iw = lidx(Lw, 1 + i, z, y, x);
-        const long long io = lidx(Ls, 1 + i, z, y, x);
-        if (!st.last)
-            w[iw] = (TW)((TA)w[iw] + dt * nu3 * g);
-        store_ghosted(out, Ls, 1 + i, z, y, x, (TS)((TA)out[io] + beta * dt * nu3 * g));
+        if (keep_w)
+            w[cw + (1 + i) * Lw.fpitch] = (TW)((TA)wv[i] + dt * nu3 * g[i]);
+        store_ghosted(out, Ls, 1 + i, z, y, x, (TS)((TA)ov[i] + beta * dt * nu3 * g[i]));
     }
 }
 
