@@ -141,6 +141,130 @@ __global__ void __launch_bounds__(128) k_pass2_simple(const TS *__restrict__ div
     }
 }
 
+// Two x-adjacent points (x even, x + 1) per thread of the second pass, with
+// 8- or 16-byte pair accesses.  x and x + 1 fall on the same side of every
+// periodic edge (nx even), so their ghost copies are one pair too.  Each
+// point's arithmetic is the one-point kernel's, in the same order.
+template <class T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using t = float2;
+};
+template <>
+struct Pair<double> {
+    using t = double2;
+};
+
+template <class T>
+__device__ __forceinline__ typename Pair<T>::t ldg_pair(const T *p)
+{
+    return __ldg(reinterpret_cast<const typename Pair<T>::t *>(p));
+}
+
+// The divergence around point x + J of the pair, from preloaded pairs: the
+// x row at x - 4 .. x + 5, and the y and z arms (pairs at the same x).
+template <class T, int J>
+struct PairDivAcc {
+    using V = typename Pair<T>::t;
+    const V *xrow;    // 5 pairs: x - 4, x - 2, x, x + 2, x + 4
+    const V *yarm;    // 6 pairs: dy = -3..-1, 1..3
+    const V *zarm;    // 6 pairs: dz = -3..-1, 1..3
+    __device__ __forceinline__ T operator()(int, int kz, int ky, int kx) const
+    {
+        if (kz)
+            return J ? zarm[kz < 0 ? kz + 3 : kz + 2].y : zarm[kz < 0 ? kz + 3 : kz + 2].x;
+        if (ky)
+            return J ? yarm[ky < 0 ? ky + 3 : ky + 2].y : yarm[ky < 0 ? ky + 3 : ky + 2].x;
+        const int e = J + kx + 4;  // element index in the x row
+        return (e & 1) ? xrow[e >> 1].y : xrow[e >> 1].x;
+    }
+};
+
+template <class T>
+__device__ __forceinline__ void store_pair_ghosted(T *base, const Layout &L, int f, int z, int y,
+                                                   int x, typename Pair<T>::t v)
+{
+    using V = typename Pair<T>::t;
+    const long long i0 = lidx(L, f, z, y, x);
+    *reinterpret_cast<V *>(base + i0) = v;
+    long long dx = 0, dy = 0;
+    if (x < GX)
+        dx = L.nx;
+    else if (x >= L.nx - GX)
+        dx = -L.nx;
+    if (y < GY)
+        dy = (long long)L.ny * L.P;
+    else if (y >= L.ny - GY)
+        dy = -(long long)L.ny * L.P;
+    if (dx)
+        *reinterpret_cast<V *>(base + i0 + dx) = v;
+    if (dy) {
+        *reinterpret_cast<V *>(base + i0 + dy) = v;
+        if (dx)
+            *reinterpret_cast<V *>(base + i0 + dy + dx) = v;
+    }
+}
+
+template <class TS, class TW, class TA>
+__global__ void __launch_bounds__(128) k_pass2_pair(const TS *__restrict__ divf,
+                                                    TS *__restrict__ out, TW *__restrict__ w,
+                                                    Layout Ls, Layout Lw, Coef<TS> c, RKStage st)
+{
+    using V = typename Pair<TS>::t;
+    using VW = typename Pair<TW>::t;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= Ls.nx || y >= Ls.ny)
+        return;
+    const long long cs = (long long)z * Ls.plane + (long long)(y + GY) * Ls.P + (x + GX);
+    const long long cw = (long long)z * Lw.plane + (long long)(y + GY) * Lw.P + (x + GX);
+    const TS *p = divf + cs;
+    V xrow[5], yarm[6], zarm[6];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+        xrow[k] = ldg_pair(p + 2 * k - 4);
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) {
+        yarm[3 - k] = ldg_pair(p - k * Ls.P);
+        yarm[2 + k] = ldg_pair(p + k * Ls.P);
+        zarm[3 - k] = ldg_pair(p + (long long)(zplane(Ls, z - k) - z) * Ls.plane);
+        zarm[2 + k] = ldg_pair(p + (long long)(zplane(Ls, z + k) - z) * Ls.plane);
+    }
+    const PairDivAcc<TS, 0> A0{xrow, yarm, zarm};
+    const PairDivAcc<TS, 1> A1{xrow, yarm, zarm};
+    TA g0[3], g1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g0[i] = (TA)d1_axis(A0, 0, i, c);
+        g1[i] = (TA)d1_axis(A1, 0, i, c);
+    }
+    V ov[3];
+    VW wv[3];
+    const bool keep_w = !st.last;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ov[i] = *reinterpret_cast<const V *>(out + cs + (1 + i) * Ls.fpitch);
+        if (keep_w)
+            wv[i] = *reinterpret_cast<const VW *>(w + cw + (1 + i) * Lw.fpitch);
+    }
+    const TA dt = (TA)st.dt, beta = (TA)st.beta, nu3 = (TA)st.nu3;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (keep_w) {
+            VW nw;
+            nw.x = (TW)((TA)wv[i].x + dt * nu3 * g0[i]);
+            nw.y = (TW)((TA)wv[i].y + dt * nu3 * g1[i]);
+            *reinterpret_cast<VW *>(w + cw + (1 + i) * Lw.fpitch) = nw;
+        }
+        V no;
+        no.x = (TS)((TA)ov[i].x + beta * dt * nu3 * g0[i]);
+        no.y = (TS)((TA)ov[i].y + beta * dt * nu3 * g1[i]);
+        store_pair_ghosted(out, Ls, 1 + i, z, y, x, no);
+    }
+}
+
 }  // namespace
 
 template <class TS, class TW, class TA>
@@ -190,9 +314,22 @@ cudaError_t launch_pass2_simple(const StateBufs &b, const Coef<TS> &c, const RKS
     if (e != cudaSuccess)
         return e;
     const dim3 block(32, 4, 1);
-    const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
-    k_pass2_simple<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,
-                                                           (TW *)b.w, b.Ls, b.Lw, c, st);
+    // pairs of x points with 8- or 16-byte accesses when every row start
+    // and field pitch keeps an even x on a pair boundary
+    auto even = [](const void *q, size_t bytes) { return ((uintptr_t)q % bytes) == 0; };
+    const bool pairs = b.Ls.nx % 2 == 0 && b.Ls.P % 2 == 0 && b.Ls.plane % 2 == 0 &&
+                       b.Ls.fpitch % 2 == 0 && b.Lw.P % 2 == 0 && b.Lw.plane % 2 == 0 &&
+                       b.Lw.fpitch % 2 == 0 && GX % 2 == 0 && even(b.div, 2 * sizeof(TS)) &&
+                       even(b.out, 2 * sizeof(TS)) && even(b.w, 2 * sizeof(TW));
+    if (pairs) {
+        const dim3 grid((b.Ls.nx / 2 + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
+        k_pass2_pair<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,
+                                                             (TW *)b.w, b.Ls, b.Lw, c, st);
+    } else {
+        const dim3 grid((b.Ls.nx + 31) / 32, (b.Ls.ny + 3) / 4, b.Ls.nz);
+        k_pass2_simple<TS, TW, TA><<<grid, block, 0, stream>>>((const TS *)b.div, (TS *)b.out,
+                                                               (TW *)b.w, b.Ls, b.Lw, c, st);
+    }
     *launches += 1;
     return cudaGetLastError();
 }
