@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -921,9 +922,21 @@ cudaError_t conv(gbfd_cnn *c, const CUtensorMap &xmap, const ConvArgs &a)
 {
     using SM = ConvSmem<CIN, N, EPI>;
     auto k = k_conv_tc<CIN, N, EPI>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
+    // the shared-memory opt-in once per device (it is a per-device attribute
+    // of the kernel; the call costs host time on every launch otherwise)
+    static std::atomic<unsigned long long> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (dev >= 64 || !(opted.load() & bit)) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SM::BYTES);
+        if (e != cudaSuccess)
+            return e;
+        if (dev < 64)
+            opted.fetch_or(bit);
+    }
     const int n = a.n;
     const long long ntiles = (long long)(a.npts / ((long long)n * n * n)) * ((n + ZB - 1) / ZB) *
                              ((n + TYT - 1) / TYT) * ((n + TXT - 1) / TXT);
