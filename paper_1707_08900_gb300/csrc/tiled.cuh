@@ -42,10 +42,8 @@ constexpr int kZcChoices = 5;
 //   6  the same as 4 with the x-neighbour pairs of the x arms taken from the
 //      neighbouring lanes by warp shuffles instead of paired shared loads
 //      (tiled_shfl.cu)
-//   7  the same as 4 on 32 x 16 tiles: one CTA of eight warps per SM, 22%
-//      less halo per point (tiled_tall.cu)
 constexpr int kVarPx1 = 0, kVarPacked = 1, kVarLagReg = 2, kVarLagReg1 = 3, kVarLagTm = 4,
-              kVarLagTmCap = 5, kVarLagTmShfl = 6, kVarLagTmTall = 7;
+              kVarLagTmCap = 5, kVarLagTmShfl = 6;
 constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 
 // Default FP64 table entry (see tiled_f64.cu): the one-point kernel on
@@ -70,10 +68,7 @@ struct TmapCache {
     int next;
 };
 
-// Table variants 6 and 7 (FP32 storage and arithmetic, 55-point form).
-cudaError_t launch_lag_tall(const StateBufs &b, const Coef<float> &c, const RKStage &st, int nf,
-                            int zc, int cfg_key, int *dev_error, TmapCache *cache,
-                            cudaStream_t stream, int *launches);
+// Table variant 6 (FP32 storage and arithmetic, 55-point form).
 cudaError_t launch_lag_shfl(const StateBufs &b, const Coef<float> &c, const RKStage &st, int nf,
                             int zc, int cfg_key, int *dev_error, TmapCache *cache,
                             cudaStream_t stream, int *launches);

@@ -188,10 +188,8 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     V colv[NF][W];
     V acx[W], acy[W], acz[W];
     V pr[NF][TM ? 1 : 3 + U];
-    // this thread's TMEM lane (the warp's 32-lane quarter), column 0; warps
-    // 4-7 of an 8-warp CTA take the same lanes, kTmCols columns further
-    const uint32_t trow = tmem + ((uint32_t)(((threadIdx.x / 32) % 4) * 32) << 16) +
-                          (uint32_t)((threadIdx.x / 128) * kTmCols);
+    // this thread's TMEM lane (the warp's 32-lane quarter), column 0
+    const uint32_t trow = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
     (void)trow;
 #pragma unroll
     for (int m = 0; m < W; ++m)
@@ -713,9 +711,6 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
     int *__restrict__ dev_error, const int skip_plane)
 {
     using RG = RingL<TW, NF, TX, TY, NS, U>;
-    // TMEM columns: kTmCols per group of four warps (a power of two)
-    constexpr int TMC = kTmCols * (((TX / 2) * TY + 127) / 128);
-    static_assert(TMC == 64 || TMC == 128, "TMEM allocation");
     extern __shared__ __align__(128) unsigned char smem[];
     tiled2::init_barriers(reinterpret_cast<uint64_t *>(smem + RG::BAR_OFF), NS + RG::NW);
     uint32_t tmem = 0;
@@ -723,7 +718,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
         // warp 0 allocates the CTA's columns; every thread reads the address
         uint32_t *slot = reinterpret_cast<uint32_t *>(smem + RG::TM_OFF);
         if (threadIdx.x < 32)
-            tc::tmem_alloc(slot, TMC);
+            tc::tmem_alloc(slot, kTmCols);
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
@@ -743,7 +738,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
         __syncthreads();
         tc::fence_after_sync();
         if (threadIdx.x < 32)
-            tc::tmem_dealloc(tmem, TMC);
+            tc::tmem_dealloc(tmem, kTmCols);
     }
 }
 

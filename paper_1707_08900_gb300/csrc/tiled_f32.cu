@@ -41,10 +41,8 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     } else if (v == kVarLagTmCap) {
         e = launch_lag_cfg<TW, TA, 32, 8, 8, 2, true, 3>(b, c, st, nf, t.zc, v, dev_error, cache,
                                                        stream, launches);
-    } else if (v == kVarLagTmShfl) {
-        e = launch_lag_shfl(b, c, st, nf, t.zc, v, dev_error, cache, stream, launches);
     } else {
-        e = launch_lag_tall(b, c, st, nf, t.zc, v, dev_error, cache, stream, launches);
+        e = launch_lag_shfl(b, c, st, nf, t.zc, v, dev_error, cache, stream, launches);
     }
     if (e != cudaSuccess || form == 0)
         return e;

@@ -215,7 +215,7 @@ def test_diagnostics_match_oracle():
 
 @pytest.mark.parametrize("cfg,iso", [(-1, False), (-1, True), (5, False), (10, False),
                                      (16, False), (20, False), (20, True), (24, True),
-                                     (30, True), (34, False), (35, True), (38, False)])
+                                     (30, True), (34, False)])
 def test_roll_equivariance_bitwise_fp32(cfg, iso):
     """Rolling the input rolls the output bit for bit: every point runs the
     same arithmetic whatever tile, chunk or periodic edge it falls in (the
@@ -273,7 +273,7 @@ def test_every_tile_config_matches_oracle(precision):
         else:
             _check_fp32(got, ref, st, f"cfg {cfg}")
         n += 1
-    assert n >= {"fp64": 25, "fp32": 40, "fp32_accff": 5}.get(precision, 15)
+    assert n >= {"fp64": 25, "fp32": 35, "fp32_accff": 5}.get(precision, 15)
 
 
 @pytest.mark.parametrize("iso", [False, True])
@@ -284,8 +284,7 @@ def test_lagged_output_kernel_on_ragged_chunks(shape, iso):
     iteration; 4: pending right-hand sides in tensor memory; 5: the same
     capped at 168 registers for three CTAs per SM, whose TMEM accesses once
     returned wrong values before the warps were reconverged ahead of them;
-    6: x neighbours by warp shuffles, halo quads at the row ends; 7: 32 x 16
-    tiles, eight warps sharing the TMEM lane quarters) on z-chunks of
+    6: x neighbours by warp shuffles, halo quads at the row ends) on z-chunks of
     odd length and of length 1, where its epilogue steps (the halo planes
     above the chunk) fall on either step of an iteration; both entropy
     modes; unequal spacings, and equal ones (`iso`), where variant 4 runs
@@ -301,7 +300,7 @@ def test_lagged_output_kernel_on_ragged_chunks(shape, iso):
             st = np.ascontiguousarray(st[:4])
         dt = fd.cfl_dt(st, g, ph, 0.4)
         ref = fd.rk3_step(st, dt, g, ph)
-        for v in (2, 3, 4, 5, 6, 7):
+        for v in (2, 3, 4, 5, 6):
             for zi in range(5):
                 s = _solver(shape, precision="fp32", nu=0.01, entropy_mode=em, lengths=lengths)
                 s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, 5 * v + zi)
@@ -317,16 +316,15 @@ def test_lagged_kernel_tmem_and_isotropic_paths_are_bit_identical(iso):
     """The lagged-output kernel keeps its pending right-hand sides in
     registers (table 10) or in TMEM (table 20, which on equal spacings also
     takes the isotropic weights; table 30 the same with the x neighbours
-    exchanged by warp shuffles; table 35 on 32 x 16 tiles): storage does not
-    round, the weights are the same values, a shuffle moves the same bits a
-    shared load reads and the tile shape changes no point's arithmetic, so
-    all give the same bits."""
+    exchanged by warp shuffles): storage does not round, the weights are the
+    same values and a shuffle moves the same bits a shared load reads, so the
+    three give the same bits."""
     from paper_1707_08900_gb300 import gbfd
     shape = (24, 40, 64)
     lengths = (64 * 0.1, 40 * 0.1, 24 * 0.1) if iso else (2 * np.pi,) * 3
     st = inputs.spectrum(shape, 14, mach=0.2, lnrho_rms=1e-2).astype(np.float32)
     outs = []
-    for cfg in (10, 20, 30, 35):
+    for cfg in (10, 20, 30):
         s = _solver(shape, precision="fp32", nu=5e-3, lengths=lengths)
         s.set_option(gbfd.GBFD_OPT_TILE_CONFIG, cfg)
         s.set_state(st)
