@@ -46,10 +46,13 @@ constexpr int kVarPx1 = 0, kVarPacked = 1, kVarLagReg = 2, kVarLagReg1 = 3, kVar
               kVarLagTmCap = 5, kVarLagTmShfl = 6;
 constexpr int kDefaultF32 = kVarLagTm * kZcChoices;
 
-// Default FP64 table entry (see tiled_f64.cu): the one-point kernel on
-// 16 x 8 tiles, z-chunks of 40 (2% faster than 32 x 4 at 256^3; the FP64
-// pipe is the bound, about 80% busy).
-constexpr int kDefaultF64 = 1 * kZcChoices;
+// Default FP64 table entry (see tiled_f64.cu): the one-point kernel with the
+// output lagged three planes behind the in-plane work (z-paired Eq. 8 terms
+// from each centre plane's own differences), 16 x 8 tiles, a 5-slot ring for
+// three CTAs per SM, z-chunks of 40: 0.622 against 0.554 G updates/s for the
+// one-point kernel that reads every stencil point (entry 5) at 256^3; the
+// FP64 pipe is the bound.
+constexpr int kDefaultF64 = 5 * kZcChoices;
 
 // Tile tables per storage width (4 = FP32 storage, 8 = FP64 storage).
 int tiled_config_count(int sbytes);

@@ -18,8 +18,9 @@ const TileConfig kVariants4[] = {{32, 8, 0, 9, 1},
                                  {32, 8, 0, 8, 2, 2, 1, 1},
                                  {32, 8, 0, 8, 2, 2, 1, 1},
                                  {32, 8, 0, 8, 2, 2, 1, 1}};
-const TileConfig kVariants8[] = {{32, 4, 0, 8, 1}, {16, 8, 0, 8, 1}, {32, 4, 0, 6, 2, 1},
-                                 {32, 4, 0, 5, 2, 2}, {32, 8, 0, 5, 2, 1}};
+const TileConfig kVariants8[] = {{32, 4, 0, 8, 1},       {16, 8, 0, 8, 1},
+                                 {32, 4, 0, 6, 2, 1},    {32, 4, 0, 5, 2, 2},
+                                 {32, 8, 0, 5, 2, 1},    {16, 8, 0, 5, 1, 0, 1, 1}};
 const int kZc[kZcChoices] = {40, 32, 64, 16, 8};
 constexpr int kNz = kZcChoices;
 

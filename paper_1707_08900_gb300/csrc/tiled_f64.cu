@@ -2,9 +2,13 @@
 // table): 0, 1 the one-point-per-thread kernel on 32 x 4 and 16 x 8 tiles;
 // 2-4 the two-point kernel on point pairs (scalar FP64 operations in pairs)
 // with the z-paired Eq. 8 terms accumulated forward from each arriving plane,
-// on 32 x 4 tiles with one or two output planes per iteration and on 32 x 8.
-// Forced steps (Sect. 6 forcing) run the one-point kernel.
-#include "tiled2_impl.cuh"
+// on 32 x 4 tiles with one or two output planes per iteration and on 32 x 8;
+// 5 (the default) the one-point kernel with output planes finished three
+// planes behind the in-plane work (tiled6_impl.cuh) on 16 x 8 tiles, a
+// 5-slot ring, three CTAs per SM.  Forced steps (Sect. 6 forcing) of
+// variants 1-4 run variant 0 (which has the forcing term); the 19-point form
+// of variant 5 runs variant 1.
+#include "tiled6_impl.cuh"
 
 namespace gbfd {
 
@@ -15,7 +19,11 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
 {
     const int idx = cfg < 0 ? kDefaultF64 : cfg;
     const TileConfig t = tiled_config(8, idx);
-    const int v = st.fo.on ? 0 : idx / kZcChoices;
+    int v = idx / kZcChoices;
+    if (form != 0 && v == 5)
+        v = 1;
+    if (st.fo.on && v != 5)
+        v = 0;
     cudaError_t e;
     switch (v) {
     case 0:
@@ -34,9 +42,13 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
         e = launch_px2_cfg<TS, TW, TA, 32, 4, 5, true, 2, 1, false, false, false, 3>(
             b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
         break;
-    default:
+    case 4:
         e = launch_px2_cfg<TS, TW, TA, 32, 8, 5, true, 1, 1, false, false, false, 3>(
             b, c, st, nf, form, t.zc, v, dev_error, cache, stream, launches);
+        break;
+    default:
+        e = launch_lag64_cfg<16, 8, 5, 3>(b, c, st, nf, t.zc, v, dev_error, cache, stream,
+                                          launches);
         break;
     }
     if (e != cudaSuccess || form == 0)
