@@ -305,7 +305,7 @@ def run_ours(args):
                 "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": "k_substep_lag<float,5,55p,32x8,packed,U=2,TMEM> (3 launches per step)",
+                "kernel": "k_substep_lag<float,5,55p,32x8,packed,U=2,TMEM,substep s,whole tiles> (3 launches per step, one instantiation per RK3 substep)",
                 "alg_bytes_per_launch": alg_per_launch,
                 "frac_of_8TBs_nominal": round(achieved / 8000.0, 4),
                 # each field read and written once per substep (12 F w per

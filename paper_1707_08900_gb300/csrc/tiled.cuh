@@ -34,7 +34,10 @@ constexpr int kZcChoices = 5;
 //      planes around it, pending right-hand sides in registers, two steps
 //      per iteration
 //   3  the same with one step per iteration
-//   4  the same as 2 with the pending right-hand sides in TMEM (default)
+//   4  the same as 2 with the pending right-hand sides in TMEM (default;
+//      on whole tiles with equal spacing and five unforced fields it runs an
+//      instantiation per RK3 substep, the substep and the grid-extent test
+//      fixed at compile time)
 //   5  the same as 4 compiled for three CTAs per SM (168 registers; slower:
 //      13.3 against 19.2 G updates/s at 256^3, spills and still two CTAs per
 //      SM, whose shared memory the ring fills; kept as the check that its

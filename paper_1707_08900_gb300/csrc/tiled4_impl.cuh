@@ -95,13 +95,15 @@ struct RingL : tiled2::Ring<float, TW, NF, TX, TY, NS, U + 2> {
 // One z-chunk of one column; same contract as the two-point kernel's column
 // routine (barrier phases continue across calls through jrun / wrun; false
 // when a bounded wait gave up).
+// STG >= 0 fixes the RK3 substep (0, 1, 2) at compile time, FULL says that
+// every tile lies inside the grid; both only drop run-time tests.
 template <class TW, class TA, int NF, int TX, int TY, int NS, int U, bool ICVT, bool FORCE, bool TM,
-          class CoefT, bool SHFL = false>
+          class CoefT, bool SHFL = false, int STG = -1, bool FULL = false>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            float *__restrict__ out, TW *__restrict__ w,
                                            const Layout &Ls, const Layout &Lw, const CoefT &c,
                                            const TA alpha, const TA beta, const TA dt,
-                                           const bool first, const bool last, const int x0,
+                                           const bool first_arg, const bool last_arg, const int x0,
                                            const int y0, const int z0, const int nout, int &jrun,
                                            int &wrun, unsigned char *smem, int *dev_error,
                                            const int skip_plane, const Forcing *fo,
@@ -129,7 +131,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     const int nz = Ls.nz;
     const int nplanes = nout + 2 * R;
     const int x = x0 + 2 * tx, y = y0 + ty;
-    const bool valid0 = (x < Ls.nx) && (y < Ls.ny);  // nx % 4 == 0: x+1 valid with x
+    const bool first = STG >= 0 ? STG == 0 : first_arg;
+    const bool last = STG >= 0 ? STG == 2 : last_arg;
+    const bool valid0 = FULL || ((x < Ls.nx) && (y < Ls.ny));  // nx % 4 == 0: x+1 valid with x
     const int toff = (ty + GY) * BX + (2 * tx + GX);
     const bool need_w = !first;
     float2 fxy0 = make_float2(0.f, 0.f), fxy1 = make_float2(0.f, 0.f);
@@ -703,7 +707,7 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 // every axis (10 stencil weights instead of 30, few enough to stay in uniform
 // registers).
 template <class TW, class TA, int NF, int TX, int TY, int NS, int U, int MINB, bool ICVT,
-          bool FORCE, bool TM, class CoefT, bool SHFL>
+          bool FORCE, bool TM, class CoefT, bool SHFL, int STG = -1, bool FULL = false>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     float *__restrict__ out, TW *__restrict__ w, const Layout Ls, const Layout Lw,
@@ -729,7 +733,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_lag(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TW, TA, NF, TX, TY, NS, U, ICVT, FORCE, TM, CoefT, SHFL>(
+    run_column<TW, TA, NF, TX, TY, NS, U, ICVT, FORCE, TM, CoefT, SHFL, STG, FULL>(
         &tmap, &wmap, out, w, Ls, Lw, c, (TA)st.alpha, (TA)st.beta, (TA)st.dt, st.first != 0,
         st.last != 0, x0, y0, z0, nout, jrun, wrun, smem, dev_error,
         blockIdx.x == 0 && blockIdx.y == 0 ? skip_plane : -1, &st.fo, tmem);
@@ -788,6 +792,35 @@ cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKSta
         }                                                                                         \
         GBFD_LAUNCH_LAG_C(NFV, FRC, Coef<float>, c);                                              \
     } while (0)
+    // the unforced five-field isotropic case on whole tiles: the substep is a
+    // template argument and the grid-extent test goes
+    constexpr bool SPEC = TM && MINB == 1 && !ICVT && !SHFL && std::is_same<TW, float>::value &&
+                          (std::is_same<TA, float>::value || std::is_same<TA, ffloat>::value);
+    const bool full = b.Ls.nx % TX == 0 && b.Ls.ny % TY == 0;
+    if constexpr (SPEC) {
+        if (nf == 5 && !st.fo.on && iso && full && st.s >= 0 && st.s <= 2) {
+#define GBFD_LAUNCH_LAG_S(SV)                                                                     \
+    do {                                                                                          \
+        auto kern = tiled4::k_substep_lag<TW, TA, 5, TX, TY, NS, U, MINB, ICVT, false, TM,        \
+                                          CubicCoef<float>, SHFL, SV, true>;                      \
+        constexpr int sm = tiled4::RingL<TW, 5, TX, TY, NS, U>::BYTES;                            \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
+        if (e != cudaSuccess)                                                                     \
+            return e;                                                                             \
+        kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, b.Ls, b.Lw, cc, st, zc, tiles_x,   \
+                                          dev_error, skip_plane);                                 \
+    } while (0)
+            if (st.s == 0)
+                GBFD_LAUNCH_LAG_S(0);
+            else if (st.s == 1)
+                GBFD_LAUNCH_LAG_S(1);
+            else
+                GBFD_LAUNCH_LAG_S(2);
+#undef GBFD_LAUNCH_LAG_S
+            *launches += 1;
+            return cudaGetLastError();
+        }
+    }
     if (nf == 5) {
         if (st.fo.on)
             GBFD_LAUNCH_LAG(5, true);
