@@ -46,12 +46,14 @@ cudaError_t launch_substep_tiled(const StateBufs &b, const Coef<TS> &c, const RK
     }
     if (e != cudaSuccess || form == 0)
         return e;
-    // the 19-point form's second pass: one thread per point.  Measured
-    // slower at 256^3 for the form: a z-streaming TMA-tiled version (10.2
-    // against 11.6 G updates/s, its per-plane work too small to hide the
-    // ring's latency) and one thread per z-column with the divergence
-    // sliding through registers (10.55 against 11.3 G with 40-plane columns,
-    // 10.54 with 16: fewer independent loads in flight per thread)
+    // the 19-point form's second pass: two x-adjacent points per thread
+    // with pair accesses where the layout keeps pairs aligned, else one
+    // point per thread.  Measured slower at 256^3 for the form: a
+    // z-streaming TMA-tiled version (10.2 against 11.6 G updates/s, its
+    // per-plane work too small to hide the ring's latency) and one thread
+    // per z-column with the divergence sliding through registers (10.55
+    // against 11.3 G with 40-plane columns, 10.54 with 16: fewer
+    // independent loads in flight per thread)
     return launch_pass2_simple<TS, TW, TA>(b, c, st, stream, launches);
 }
 

@@ -69,15 +69,19 @@ def test_batch_matches_oracle_and_single_box(graph):
     b.close()
 
 
-def test_batch_one_step_elementwise_against_oracle():
+@pytest.mark.parametrize("kind", [0, 1])
+def test_batch_one_step_elementwise_against_oracle(kind):
     """One batched RK3 step of uneven boxes on the term-exposing state (nu
     0.02): every box within the FP32 bars, relative L2 and the element-wise
-    increment bar."""
+    increment bar, for the two-plane routine (kind 0) and the lagged routine
+    (kind 1; its 32^3 and 64^3 boxes are whole tiles and take the
+    per-substep instantiations, the others the general one)."""
     from paper_1707_08900_gb300 import gbfd
-    ns = [16, 32, 24, 40]
-    lengths = [2 * np.pi, 3.0, 2 * np.pi, 5.0]
+    ns = [16, 32, 24, 40, 64]
+    lengths = [2 * np.pi, 3.0, 2 * np.pi, 5.0, 2 * np.pi]
     sts = [term_exposing_state((n, n, n), 50 + i, inputs) for i, n in enumerate(ns)]
     b = gbfd.Batch(ns, lengths, [TERM_NU] * len(ns))
+    b.set_option(gbfd.GBFD_BATCH_OPT_KERNEL, kind)
     dts = []
     for i, (n, L, st) in enumerate(zip(ns, lengths, sts)):
         b.set_state(i, st.astype(np.float32))
