@@ -802,16 +802,20 @@ cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKSta
         }                                                                                         \
         GBFD_LAUNCH_LAG_C(NFV, FRC, Coef<float>, c);                                              \
     } while (0)
-    // the unforced five-field isotropic case on whole tiles: the substep is a
-    // template argument and the grid-extent test goes
+    // the five-field isotropic case on whole tiles (forced steps in FP32
+    // arithmetic included): the substep is a template argument and the
+    // grid-extent test goes
     constexpr bool SPEC = TM && MINB == 1 && !ICVT && !SHFL && std::is_same<TW, float>::value &&
                           (std::is_same<TA, float>::value || std::is_same<TA, ffloat>::value);
     const bool full = b.Ls.nx % TX == 0 && b.Ls.ny % TY == 0;
     if constexpr (SPEC) {
-        if (nf == 5 && !st.fo.on && iso && full && st.s >= 0 && st.s <= 2) {
-#define GBFD_LAUNCH_LAG_S(SV)                                                                     \
+        // forced steps too, in FP32 arithmetic (the forcing is a compile-time
+        // switch of the same kernel)
+        const bool frc_ok = !st.fo.on || std::is_same<TA, float>::value;
+        if (nf == 5 && frc_ok && iso && full && st.s >= 0 && st.s <= 2) {
+#define GBFD_LAUNCH_LAG_S(FRC, SV)                                                                \
     do {                                                                                          \
-        auto kern = tiled4::k_substep_lag<TW, TA, 5, TX, TY, NS, U, MINB, ICVT, false, TM,        \
+        auto kern = tiled4::k_substep_lag<TW, TA, 5, TX, TY, NS, U, MINB, ICVT, FRC, TM,          \
                                           CubicCoef<float>, SHFL, SV, true>;                      \
         constexpr int sm = tiled4::RingL<TW, 5, TX, TY, NS, U>::BYTES;                            \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
@@ -820,12 +824,22 @@ cudaError_t launch_lag_cfg(const StateBufs &b, const Coef<float> &c, const RKSta
         kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, b.Ls, b.Lw, cc, st, zc, tiles_x,   \
                                           dev_error, skip_plane);                                 \
     } while (0)
-            if (st.s == 0)
-                GBFD_LAUNCH_LAG_S(0);
-            else if (st.s == 1)
-                GBFD_LAUNCH_LAG_S(1);
-            else
-                GBFD_LAUNCH_LAG_S(2);
+#define GBFD_LAUNCH_LAG_SS(FRC)                                                                   \
+    do {                                                                                          \
+        if (st.s == 0)                                                                            \
+            GBFD_LAUNCH_LAG_S(FRC, 0);                                                            \
+        else if (st.s == 1)                                                                       \
+            GBFD_LAUNCH_LAG_S(FRC, 1);                                                            \
+        else                                                                                      \
+            GBFD_LAUNCH_LAG_S(FRC, 2);                                                            \
+    } while (0)
+            if (!st.fo.on) {
+                GBFD_LAUNCH_LAG_SS(false);
+            } else {
+                if constexpr (std::is_same<TA, float>::value)
+                    GBFD_LAUNCH_LAG_SS(true);
+            }
+#undef GBFD_LAUNCH_LAG_SS
 #undef GBFD_LAUNCH_LAG_S
             *launches += 1;
             return cudaGetLastError();

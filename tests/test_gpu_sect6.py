@@ -70,6 +70,45 @@ def test_forced_steps_match_oracle(precision, form, path):
     assert np.all(err[:4] <= tol), err
 
 
+def test_forced_fp32_steps_on_whole_tiles_match_oracle():
+    """Forced FP32 steps where the default kernel runs its per-substep
+    instantiations with the forcing compiled in (whole 32 x 8 tiles, equal
+    spacing on every axis): one forced step on the term-exposing state within
+    the FP32 bars (relative L2 and the element-wise increment bar), then
+    three steps with new k, phi and e each within 3 x the per-step bar."""
+    from bars import inc_bar, inc_err, max_abs, term_exposing_state
+    from paper_1707_08900_gb300 import gbfd
+    shape = (24, 16, 64)  # (nz, ny, nx)
+    h = 2 * np.pi / 64
+    lengths = (64 * h, 16 * h, 24 * h)  # (lx, ly, lz)
+    g = fd.Grid(shape[2], shape[1], shape[0], *lengths)
+    nu = 0.02
+    ph = fd.Physics(cs=1.0, nu=nu, entropy_mode=1)
+    st = term_exposing_state(shape, 17, inputs)
+    ks, phis, es = inputs.forcing_sequence(11, 3, kmin=1.0, kmax=3.0)
+    dt, f0 = fd.cfl_dt(st, g, ph, 0.4), 0.2
+    s = gbfd.Solver(shape, lengths=lengths, nu=nu, precision="fp32")
+    s.set_state(st)
+    s.rk3_step_forced(dt, f0, ks[:1], phis[:1], es[:1])
+    got = s.get_state()
+    ref = fd.rk3_step_forced(st, dt, g, ph, f0, ks[:1], phis[:1], es[:1])
+    base = fd.rk3_step(st, dt, g, ph)
+    # the forcing must have acted on this step
+    assert np.linalg.norm((ref[1:4] - base[1:4]).ravel()) > 1e-2 * np.linalg.norm(
+        (base[1:4] - st[1:4]).ravel())
+    err, inc, bar = _rel(got, ref), inc_err(got, ref, st), inc_bar(ref, st)
+    print(f"one forced step: relL2 {err} inc {inc} bar {bar} maxabs {max_abs(got, ref)}")
+    assert np.all(err <= FP32_TOL), err
+    assert np.all(inc <= bar), (inc, bar)
+    s.set_state(st)
+    s.rk3_step_forced(dt, f0, ks, phis, es)
+    got3 = s.get_state()
+    s.close()
+    ref3 = fd.rk3_step_forced(st, dt, g, ph, f0, ks, phis, es)
+    err3 = _rel(got3, ref3)
+    assert np.all(err3 <= 3 * FP32_TOL), err3
+
+
 def test_every_fp32_tile_entry_runs_forced_on_the_default_kernel():
     from paper_1707_08900_gb300 import gbfd
     shape = (16, 24, 32)
