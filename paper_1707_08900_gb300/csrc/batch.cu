@@ -79,7 +79,10 @@ constexpr int smem_bytes()
 
 // One column of one box at substep s (parity: which state buffer is the
 // input).  Returns false when a bounded wait gave up.
-template <int KIND, int NF>
+// SPEC: boxes on whole tiles take one instantiation of the column routine
+// per RK3 substep (two-plane routine, five fields), as the single-box kernels
+// do; the substep and the grid-extent test then leave the per-plane code.
+template <int KIND, int NF, bool SPEC = false>
 __device__ __forceinline__ bool run_item(const BoxDesc *__restrict__ B, const int4 item,
                                          const int s, const int parity, const float dt,
                                          const int zc, const CubicCoef<float> &scoef, int &jrun,
@@ -101,6 +104,23 @@ __device__ __forceinline__ bool run_item(const BoxDesc *__restrict__ B, const in
             dev_error, -1, nullptr, tmem);
     } else {
         const CubicCoef<float> c = B->coef;
+        if constexpr (SPEC && NF == 5) {
+            if (L.nx % TX == 0 && L.ny % TY == 0) {
+                auto run = [&](auto stg) {
+                    constexpr int S = decltype(stg)::value;
+                    return tiled2::run_column<float, float, float, NF, true, TX, TY, NS, true, U,
+                                              false, false, false, CubicCoef<float>, S, true>(
+                        &B->tm_state[wi][parity], &B->tm_w[wi], B->state[parity ^ 1], B->w,
+                        nullptr, L, L, c, alpha, beta, dt, S == 0, S == 2, item.y, item.z, item.w,
+                        nout, jrun, wrun, smem, dev_error);
+                };
+                if (s == 0)
+                    return run(std::integral_constant<int, 0>{});
+                if (s == 1)
+                    return run(std::integral_constant<int, 1>{});
+                return run(std::integral_constant<int, 2>{});
+            }
+        }
         return tiled2::run_column<float, float, float, NF, true, TX, TY, NS, true, U, false>(
             &B->tm_state[wi][parity], &B->tm_w[wi], B->state[parity ^ 1], B->w, nullptr, L, L, c,
             alpha, beta, dt, s == 0, s == 2, item.y, item.z, item.w, nout, jrun, wrun, smem,
@@ -245,8 +265,9 @@ __global__ void __launch_bounds__((kind_tx(KIND) / 2) * TY) k_batch_flow(
         const int k = q / nitems;
         const int4 item = items[q % nitems];
         const BoxDesc *B = boxes + item.x;
-        const bool ok = run_item<KIND, NF>(B, item, k % 3, (cur + k) & 1, dts[item.x], zc, scoef,
-                                           jrun, wrun, smem, dev_error, tmem);
+        const bool ok = run_item<KIND, NF, KIND == KIND_PACKED>(B, item, k % 3, (cur + k) & 1,
+                                                               dts[item.x], zc, scoef, jrun, wrun,
+                                                               smem, dev_error, tmem);
         __syncthreads();  // the column's stores are issued by every thread
         if (threadIdx.x == 0) {
             if (!ok)

@@ -109,14 +109,17 @@ __device__ __forceinline__ void init_barriers(uint64_t *bars, int n)
 // copies this CTA has made before (they continue the barrier phases) and are
 // advanced on return.  Returns false when a bounded wait gave up (after
 // recording it and draining the copies in flight).
+// STG >= 0 fixes the RK3 substep (0, 1, 2) at compile time, FULL says that
+// every tile lies inside the grid; both only drop run-time tests.
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK,
-          int U, bool WG, bool ICVT = false, bool FORCE = false, class CoefT>
+          int U, bool WG, bool ICVT = false, bool FORCE = false, class CoefT, int STG = -1,
+          bool FULL = false>
 __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtensorMap *wmap,
                                            TS *__restrict__ out, TW *__restrict__ w,
                                            TS *__restrict__ divf, const Layout &Ls,
                                            const Layout &Lw, const CoefT &c, const TA alpha,
-                                           const TA beta, const TA dt, const bool first,
-                                           const bool last, const int x0, const int y0,
+                                           const TA beta, const TA dt, const bool first_arg,
+                                           const bool last_arg, const int x0, const int y0,
                                            const int z0, const int nout, int &jrun, int &wrun,
                                            unsigned char *smem, int *dev_error,
                                            const int skip_plane = -1,
@@ -140,7 +143,9 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
     const int nz = Ls.nz;
     const int nplanes = nout + 2 * R;
     const int x = x0 + 2 * tx, y = y0 + ty;
-    const bool valid0 = (x < Ls.nx) && (y < Ls.ny);  // nx % 4 == 0: x+1 valid with x
+    const bool first = STG >= 0 ? STG == 0 : first_arg;
+    const bool last = STG >= 0 ? STG == 2 : last_arg;
+    const bool valid0 = FULL || ((x < Ls.nx) && (y < Ls.ny));  // nx % 4 == 0: x+1 valid with x
     // element offset of point (x, y) in a field of a slot; even, so pairs align
     const int toff = (ty + GY) * BX + (2 * tx + GX);
     const bool need_w = !first;
@@ -914,7 +919,8 @@ __device__ __forceinline__ bool run_column(const CUtensorMap *tmap, const CUtens
 
 // Single box: one CTA per (tile, z-chunk).
 template <class TS, class TW, class TA, int NF, bool MIXED, int TX, int TY, int NS, bool PK, int U,
-          int MINB, bool WG, bool ICVT, bool FORCE, class CoefT = Coef<TS>>
+          int MINB, bool WG, bool ICVT, bool FORCE, class CoefT = Coef<TS>, int STG = -1,
+          bool FULL = false>
 __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap wmap,
     TS *__restrict__ out, TW *__restrict__ w, TS *__restrict__ divf, const Layout Ls,
@@ -929,7 +935,8 @@ __global__ void __launch_bounds__((TX / 2) * TY, MINB) k_substep_px2(
     const int z0 = blockIdx.y * zc;
     const int nout = min(zc, Ls.nz - z0);
     int jrun = 0, wrun = 0;
-    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U, WG, ICVT, FORCE>(&tmap, &wmap, out, w, divf, Ls, Lw, c,
+    run_column<TS, TW, TA, NF, MIXED, TX, TY, NS, PK, U, WG, ICVT, FORCE, CoefT, STG, FULL>(
+        &tmap, &wmap, out, w, divf, Ls, Lw, c,
                                                   (TA)st.alpha, (TA)st.beta, (TA)st.dt,
                                                   st.first != 0, st.last != 0, x0, y0, z0, nout,
                                                   jrun, wrun, smem, dev_error,
@@ -998,6 +1005,37 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
         }                                                                                         \
         GBFD_LAUNCH2_K(NFV, MIX, false);                                                          \
     } while (0)
+    // the 19-point form's first pass in FP32, five unforced fields, equal
+    // spacing, whole tiles: the substep is a template argument and the
+    // grid-extent test goes (one instantiation per RK3 substep)
+    constexpr bool SPEC = PK && !WG && !ICVT && (ISO_OK & 1) != 0 &&
+                          std::is_same<TS, float>::value && std::is_same<TW, float>::value &&
+                          std::is_same<TA, float>::value;
+    if constexpr (SPEC) {
+        if (form == 1 && nf == 5 && !st.fo.on && iso && b.Ls.nx % TX == 0 &&
+            b.Ls.ny % TY == 0 && st.s >= 0 && st.s <= 2) {
+#define GBFD_LAUNCH2_S(SV)                                                                        \
+    do {                                                                                          \
+        auto kern = tiled2::k_substep_px2<TS, TW, TA, 5, false, TX, TY, NS, PK, U, MINB, WG,     \
+                                          ICVT, false, CubicCoef<TS>, SV, true>;                  \
+        constexpr int sm = tiled2::Ring<TS, TW, 5, TX, TY, NS, U + 2>::BYTES;                     \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
+        if (e != cudaSuccess)                                                                     \
+            return e;                                                                             \
+        kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, divf, b.Ls, b.Lw, cc, st, zc,      \
+                                          tiles_x, dev_error, skip_plane);                        \
+    } while (0)
+            if (st.s == 0)
+                GBFD_LAUNCH2_S(0);
+            else if (st.s == 1)
+                GBFD_LAUNCH2_S(1);
+            else
+                GBFD_LAUNCH2_S(2);
+#undef GBFD_LAUNCH2_S
+            *launches += 1;
+            return cudaGetLastError();
+        }
+    }
     if (form == 0) {
         if (nf == 5)
             GBFD_LAUNCH2(5, true);
