@@ -1005,19 +1005,19 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
         }                                                                                         \
         GBFD_LAUNCH2_K(NFV, MIX, false);                                                          \
     } while (0)
-    // the 19-point form's first pass in FP32, five unforced fields, equal
-    // spacing, whole tiles: the substep is a template argument and the
+    // the 19-point form's first pass in FP32, five fields (forced or not),
+    // equal spacing, whole tiles: the substep is a template argument and the
     // grid-extent test goes (one instantiation per RK3 substep)
     constexpr bool SPEC = PK && !WG && !ICVT && (ISO_OK & 1) != 0 &&
                           std::is_same<TS, float>::value && std::is_same<TW, float>::value &&
                           std::is_same<TA, float>::value;
     if constexpr (SPEC) {
-        if (form == 1 && nf == 5 && !st.fo.on && iso && b.Ls.nx % TX == 0 &&
-            b.Ls.ny % TY == 0 && st.s >= 0 && st.s <= 2) {
-#define GBFD_LAUNCH2_S(SV)                                                                        \
+        if (form == 1 && nf == 5 && iso && b.Ls.nx % TX == 0 && b.Ls.ny % TY == 0 &&
+            st.s >= 0 && st.s <= 2) {
+#define GBFD_LAUNCH2_S(FRC, SV)                                                                   \
     do {                                                                                          \
         auto kern = tiled2::k_substep_px2<TS, TW, TA, 5, false, TX, TY, NS, PK, U, MINB, WG,     \
-                                          ICVT, false, CubicCoef<TS>, SV, true>;                  \
+                                          ICVT, FRC, CubicCoef<TS>, SV, true>;                    \
         constexpr int sm = tiled2::Ring<TS, TW, 5, TX, TY, NS, U + 2>::BYTES;                     \
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);          \
         if (e != cudaSuccess)                                                                     \
@@ -1025,12 +1025,23 @@ cudaError_t launch_px2_cfg(const StateBufs &b, const Coef<TS> &c, const RKStage 
         kern<<<grid, block, sm, stream>>>(*map, *wmap, out, w, divf, b.Ls, b.Lw, cc, st, zc,      \
                                           tiles_x, dev_error, skip_plane);                        \
     } while (0)
-            if (st.s == 0)
-                GBFD_LAUNCH2_S(0);
-            else if (st.s == 1)
-                GBFD_LAUNCH2_S(1);
-            else
-                GBFD_LAUNCH2_S(2);
+#define GBFD_LAUNCH2_SS(FRC)                                                                      \
+    do {                                                                                          \
+        if (st.s == 0)                                                                            \
+            GBFD_LAUNCH2_S(FRC, 0);                                                               \
+        else if (st.s == 1)                                                                       \
+            GBFD_LAUNCH2_S(FRC, 1);                                                               \
+        else                                                                                      \
+            GBFD_LAUNCH2_S(FRC, 2);                                                               \
+    } while (0)
+            if (!st.fo.on) {
+                GBFD_LAUNCH2_SS(false);
+            } else {
+                // FORCE_OK: the forced step was accepted above
+                if constexpr (FORCE_OK)
+                    GBFD_LAUNCH2_SS(true);
+            }
+#undef GBFD_LAUNCH2_SS
 #undef GBFD_LAUNCH2_S
             *launches += 1;
             return cudaGetLastError();

@@ -70,12 +70,15 @@ def test_forced_steps_match_oracle(precision, form, path):
     assert np.all(err[:4] <= tol), err
 
 
-def test_forced_fp32_steps_on_whole_tiles_match_oracle():
-    """Forced FP32 steps where the default kernel runs its per-substep
+@pytest.mark.parametrize("form", ["55p", "19p"])
+def test_forced_fp32_steps_on_whole_tiles_match_oracle(form):
+    """Forced FP32 steps where the kernels run their per-substep
     instantiations with the forcing compiled in (whole 32 x 8 tiles, equal
-    spacing on every axis): one forced step on the term-exposing state within
-    the FP32 bars (relative L2 and the element-wise increment bar), then
-    three steps with new k, phi and e each within 3 x the per-step bar."""
+    spacing on every axis: the default 55-point kernel, the 19-point form's
+    first pass): one forced step on the term-exposing state within the FP32
+    bars (relative L2 and the element-wise increment bar), then three steps
+    with new k, phi and e each within 3 x the per-step bar."""
+    fm = fd.FORM_55P if form == "55p" else fd.FORM_19P
     from bars import inc_bar, inc_err, max_abs, term_exposing_state
     from paper_1707_08900_gb300 import gbfd
     shape = (24, 16, 64)  # (nz, ny, nx)
@@ -87,24 +90,24 @@ def test_forced_fp32_steps_on_whole_tiles_match_oracle():
     st = term_exposing_state(shape, 17, inputs)
     ks, phis, es = inputs.forcing_sequence(11, 3, kmin=1.0, kmax=3.0)
     dt, f0 = fd.cfl_dt(st, g, ph, 0.4), 0.2
-    s = gbfd.Solver(shape, lengths=lengths, nu=nu, precision="fp32")
+    s = gbfd.Solver(shape, lengths=lengths, nu=nu, precision="fp32", form=form)
     s.set_state(st)
     s.rk3_step_forced(dt, f0, ks[:1], phis[:1], es[:1])
     got = s.get_state()
-    ref = fd.rk3_step_forced(st, dt, g, ph, f0, ks[:1], phis[:1], es[:1])
-    base = fd.rk3_step(st, dt, g, ph)
+    ref = fd.rk3_step_forced(st, dt, g, ph, f0, ks[:1], phis[:1], es[:1], form=fm)
+    base = fd.rk3_step(st, dt, g, ph, form=fm)
     # the forcing must have acted on this step
     assert np.linalg.norm((ref[1:4] - base[1:4]).ravel()) > 1e-2 * np.linalg.norm(
         (base[1:4] - st[1:4]).ravel())
     err, inc, bar = _rel(got, ref), inc_err(got, ref, st), inc_bar(ref, st)
-    print(f"one forced step: relL2 {err} inc {inc} bar {bar} maxabs {max_abs(got, ref)}")
+    print(f"{form} one forced step: relL2 {err} inc {inc} bar {bar} maxabs {max_abs(got, ref)}")
     assert np.all(err <= FP32_TOL), err
     assert np.all(inc <= bar), (inc, bar)
     s.set_state(st)
     s.rk3_step_forced(dt, f0, ks, phis, es)
     got3 = s.get_state()
     s.close()
-    ref3 = fd.rk3_step_forced(st, dt, g, ph, f0, ks, phis, es)
+    ref3 = fd.rk3_step_forced(st, dt, g, ph, f0, ks, phis, es, form=fm)
     err3 = _rel(got3, ref3)
     assert np.all(err3 <= 3 * FP32_TOL), err3
 
