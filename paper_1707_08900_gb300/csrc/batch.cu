@@ -283,6 +283,40 @@ __global__ void __launch_bounds__((kind_tx(KIND) / 2) * TY) k_batch_flow(
     tmem_close<KIND>(tmem);
 }
 
+// CTAs of a kernel that fit on one SM by its registers, shared memory and
+// threads, and by the tensor-memory columns each CTA allocates (tm_cols of
+// the SM's 512; 0 = none).  The occupancy calculator gives a kernel that
+// allocates tensor memory one CTA per SM (the allocation's size is not part
+// of the kernel's attributes); the lagged routine takes 64 columns, so its
+// registers and shared memory decide.  The persistent grids need the true
+// figure: the dataflow launch is correct at any residency, but half-filled
+// SMs halve its throughput.
+int fit_per_sm(const void *kern, int threads, int dyn_smem, int dev, int tm_cols)
+{
+    cudaFuncAttributes fa;
+    int regs_sm = 0, smem_sm = 0, smem_res = 0, thr_sm = 0;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 0;
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in 256s
+    const int smem_cta = (dyn_smem + (int)fa.sharedSizeBytes + smem_res + 127) / 128 * 128;
+    int per = thr_sm / threads;
+    if (regs_warp > 0)
+        per = std::min(per, regs_sm / (regs_warp * warps));
+    if (smem_cta > 0)
+        per = std::min(per, smem_sm / smem_cta);
+    if (tm_cols > 0)
+        per = std::min(per, 512 / tm_cols);
+    return per;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -726,6 +760,9 @@ gbfd_status gbfd_batch_init(int nbox, const int32_t *n, const double *lengths, c
             e = cudaFuncSetAttribute(flowk, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, flowk, threads, smb);
+        if (e == cudaSuccess && kind == KIND_LAG)
+            per = std::max(per, fit_per_sm((const void *)flowk, threads, smb, dev,
+                                           tiled4::kTmCols));
         b->grid_kind[kind] = sms * std::max(per, 1);
     };
     if (b->nf == 5) {

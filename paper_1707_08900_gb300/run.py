@@ -5,6 +5,12 @@
 Draws the k^-2 spectrum initial state (rms Mach 0.1, lnrho 1e-3, seed 1),
 takes dt from CFL 0.4 once, advances `steps` RK3 steps, synchronises and
 prints the diagnostics.  Also the program profiled when a single kernel is captured.
+
+    python -m paper_1707_08900_gb300.run --n 128 --batch-boxes 4 --batch-kernel 0 --steps 1
+
+runs the batched form instead: that many n^3 boxes (seeds 100 + i, FP32),
+one dataflow launch per call with the chosen column routine and z-chunk, no
+graph (so each call is one launch of the dataflow kernel).
 """
 import argparse
 import json
@@ -22,7 +28,12 @@ def main():
     ap.add_argument("--entropy-mode", type=int, default=1)
     ap.add_argument("--tile-config", type=int, default=-1)
     ap.add_argument("--simple", action="store_true", help="one-thread-per-point kernels")
+    ap.add_argument("--batch-boxes", type=int, default=0, help="run the batched form")
+    ap.add_argument("--batch-kernel", type=int, default=0, help="column routine (batch)")
+    ap.add_argument("--batch-zchunk", type=int, default=64, help="planes per work item (batch)")
     args = ap.parse_args()
+    if args.batch_boxes:
+        return run_batch(args)
 
     import torch
 
@@ -49,6 +60,35 @@ def main():
                       "updates_per_s": args.n ** 3 * args.steps / el,
                       "mass": d["mass"], "ekin": d["ekin"], "nonfinite": d["nonfinite"]}))
     s.close()
+
+
+def run_batch(args):
+    import torch
+
+    from . import build, gbfd, inputs
+    build.build()
+    nb, n = args.batch_boxes, args.n
+    b = gbfd.Batch([n] * nb, [2 * np.pi] * nb, [5e-3] * nb)
+    b.set_option(gbfd.GBFD_BATCH_OPT_GRAPH, 0)
+    b.set_option(gbfd.GBFD_BATCH_OPT_DATAFLOW, 1)
+    b.set_option(gbfd.GBFD_BATCH_OPT_KERNEL, args.batch_kernel)
+    b.set_option(gbfd.GBFD_BATCH_OPT_ZCHUNK, args.batch_zchunk)
+    for i in range(nb):
+        st = inputs.spectrum((n,) * 3, 100 + i, p=-2.0, k1=1, k2=8, mach=0.1, lnrho_rms=1e-3)
+        b.set_state(i, st.astype(np.float32))
+    dts = [0.4 * (2 * np.pi / n) / (1.0 + b.diagnostics(i)["umax"]) for i in range(nb)]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        b.step(dts, 1)
+    b.sync()
+    el = time.perf_counter() - t
+    d = b.diagnostics(0)
+    print(json.dumps({"boxes": nb, "n": n, "kernel": args.batch_kernel, "zchunk": args.batch_zchunk,
+                      "steps": args.steps, "seconds": el,
+                      "updates_per_s": nb * n ** 3 * args.steps / el,
+                      "mass0": d["mass"], "nonfinite0": d["nonfinite"]}))
+    b.close()
 
 
 if __name__ == "__main__":
